@@ -1,0 +1,897 @@
+// FP64 CPU oracle of the two-colour (colour-gradient) lattice-Boltzmann time
+// step of Sedahmed & Coelho, "Wetting and pressure gradient performance in
+// lattice Boltzmann color gradient model" (arXiv:2407.10914).
+//
+// TEST INFRASTRUCTURE ONLY. Only the test-suite, __graft_entry__.smoke() and
+// the CPU-baseline leg of bench.py load this library. It shares no code,
+// header or table with the CUDA path under paper_2407_10914_gb300/.
+//
+// It is written to be read against the paper: one function per equation,
+// executed in the order of Eq. (1) and of the wetting summary at the end of
+// Sec. II.B.3, over plain loops, in double precision. OpenMP only splits the
+// node loops; nothing is blocked, fused or reordered.
+//
+// Layout (the public convention of this project, stated independently here):
+//   node n = x + nx*(y + ny*z), x fastest;
+//   populations f[(s*Q + i)*N + n], s = 0 red ("r"), s = 1 blue ("b");
+//   vectors v[a*N + n], a = 0,1,2 for x,y,z.
+//
+// Readings of the paper that this file takes (each repeated at its use):
+//   * collision: the single-rate (BGK) form of Eq. (2): rate S_nu (Eq. 13)
+//     for every non-conserved moment, rate 0 for rho and j, equilibrium of
+//     Eq. (A.4) and forcing of Eq. (A.5), written in velocity space;
+//   * D2Q9 = the z-free subset of the D3Q19 set of Eq. (A.1), in the same
+//     order, with weights 4/9, 1/9, 1/36;
+//   * out-of-domain neighbours on a non-periodic axis: halfway bounce-back
+//     for streaming, coordinate clamping (zero gradient) for every stencil;
+//   * thresholds: |C| <= 1e-8 -> n_c = 0; Scheme-II leaves n_c unchanged
+//     when sin(theta') < 1e-6; the Scheme-I secant stops early when the two
+//     last residuals differ by less than 1e-12.
+//
+// parity unpinned: none of the functions here is without a pin in tests/.
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+namespace {
+
+enum { CLS_SOLID = 0, CLS_SOLID_BND = 1, CLS_FLUID = 2, CLS_FLUID_BND = 3 };
+
+const double EPS_C = 1e-8;        // |C| below this: no interface, n_c = 0
+const double EPS_SIN = 1e-6;      // Scheme-II: n_c parallel to n_w
+const double EPS_SECANT = 1e-12;  // Scheme-I: secant denominator
+const double EPS_NW = 1e-12;      // |grad g| below this: no wall normal
+const double PI = 3.14159265358979323846;
+
+struct Lattice {
+  int D = 0, Q = 0;
+  int e[19][3];
+  double w[19];
+  int opp[19];
+};
+
+// Eq. (A.1) and Eq. (A.2): the D3Q19 velocities and weights in the order the
+// paper prints them (the columns of the matrix in Eq. A.1).
+const int E_D3Q19[19][3] = {
+    {0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0},
+    {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, 1, 0}, {1, -1, 0},
+    {-1, -1, 0}, {1, 0, 1},  {-1, 0, 1}, {1, 0, -1}, {-1, 0, -1},
+    {0, 1, 1},  {0, -1, 1},  {0, 1, -1}, {0, -1, -1}};
+
+Lattice make_lattice(int q) {
+  Lattice L;
+  if (q == 19) {
+    L.D = 3;
+    L.Q = 19;
+    for (int i = 0; i < 19; ++i) {
+      for (int a = 0; a < 3; ++a) L.e[i][a] = E_D3Q19[i][a];
+      L.w[i] = (i == 0) ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+    }
+  } else {
+    // D2Q9 (not in the paper): the members of Eq. (A.1) with e_z = 0, kept
+    // in the paper's order; standard D2Q9 weights.
+    const int pick[9] = {0, 1, 2, 3, 4, 7, 8, 9, 10};
+    L.D = 2;
+    L.Q = 9;
+    for (int k = 0; k < 9; ++k) {
+      for (int a = 0; a < 3; ++a) L.e[k][a] = E_D3Q19[pick[k]][a];
+      L.w[k] = (k == 0) ? 4.0 / 9.0 : (k <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+    }
+  }
+  for (int i = 0; i < L.Q; ++i)
+    for (int j = 0; j < L.Q; ++j)
+      if (L.e[j][0] == -L.e[i][0] && L.e[j][1] == -L.e[i][1] &&
+          L.e[j][2] == -L.e[i][2])
+        L.opp[i] = j;
+  return L;
+}
+
+}  // namespace
+
+extern "C" {
+
+// Parameters of one run. The oracle's own copy of the problem statement of
+// Sec. II; the field meanings follow the paper's symbols.
+typedef struct {
+  double tau_r, tau_b;  // relaxation times; nu^s = (tau^s - 1/2)/3, Eq. (13)
+  double gamma;         // interfacial tension, Eq. (5)
+  double beta;          // segregation parameter, Eq. (20)
+  double rho0;          // reference density of the equilibrium, Eq. (A.4)
+  double theta_deg;     // contact angle, measured through fluid b
+  int wetting;          // 0 none, 1 Scheme-I (Eqs. 28-31), 2 Scheme-II (32-33)
+  int zou_he;           // 1: Zou-He pressure inlet/outlet, Appendix B
+  int flow_axis;        // axis of the inlet (coordinate 0) and outlet planes
+  double rho_in, rho_out;  // Zou-He densities (B.1, B.9)
+  double zeta_r;        // injected red fraction zeta^r; zeta^b = 1 - zeta^r
+  double g[3];          // body acceleration (Type-II), Eq. (36)
+} orc_params;
+
+}  // extern "C"
+
+namespace {
+
+struct Oracle {
+  Lattice L;
+  int nx, ny, nz;
+  long N;
+  unsigned periodic;  // bit a set: axis a periodic
+  orc_params p;
+  std::vector<uint8_t> solid, cls;
+  std::vector<double> gsm;   // smoothed indicator g^(3), Eq. (25)
+  std::vector<double> nw;    // wall normal, Eq. (26), 3N
+  std::vector<double> f, ftmp;  // stored post-recolouring populations, 2QN
+  std::vector<double> rho_r, rho_b, phi;  // per node macros of the step
+  std::vector<double> C, nc;  // colour gradient and unit normal, 3N
+  std::vector<double> kappa, F;  // curvature and force (3N)
+  std::vector<double> u;         // velocity of Eq. (22), 3N
+  long n_fluid = 0;
+
+  int dim(int a) const { return a == 0 ? nx : (a == 1 ? ny : nz); }
+
+  void coords(long n, int c[3]) const {
+    c[0] = (int)(n % nx);
+    c[1] = (int)((n / nx) % ny);
+    c[2] = (int)(n / ((long)nx * ny));
+  }
+  long index(const int c[3]) const {
+    return c[0] + (long)nx * (c[1] + (long)ny * c[2]);
+  }
+
+  // Node reached from n by the displacement d. Periodic axes wrap. On a
+  // non-periodic axis a coordinate outside the box gives -1 (clamp = false)
+  // or is clamped to the box (clamp = true).
+  long neighbour(long n, const int d[3], bool clamp) const {
+    int c[3];
+    coords(n, c);
+    for (int a = 0; a < 3; ++a) {
+      int m = dim(a);
+      int v = c[a] + d[a];
+      if (v < 0 || v >= m) {
+        if (periodic & (1u << a)) {
+          v = ((v % m) + m) % m;
+        } else if (clamp) {
+          v = v < 0 ? 0 : m - 1;
+        } else {
+          return -1;
+        }
+      }
+      c[a] = v;
+    }
+    return index(c);
+  }
+
+  bool is_fluid(long n) const { return n >= 0 && !solid[n]; }
+  bool is_solid(long n) const { return n >= 0 && solid[n]; }
+  double &fp(int s, int i, long n) { return f[((long)s * L.Q + i) * N + n]; }
+
+  // ---------------------------------------------------------------- geometry
+  // Node classes from the solid image: a fluid node with a solid lattice
+  // neighbour is a fluid-boundary node (where the wetting schemes act, Sec.
+  // II.B); a solid node with a fluid lattice neighbour is a solid-boundary
+  // node (where Eqs. 34-35 extrapolate).
+  void classify() {
+    cls.assign(N, CLS_SOLID);
+    n_fluid = 0;
+    for (long n = 0; n < N; ++n) {
+      bool bnd = false;
+      for (int i = 1; i < L.Q; ++i) {
+        long m = neighbour(n, L.e[i], false);
+        if (m < 0) continue;
+        if (solid[n] ? !solid[m] : solid[m]) bnd = true;
+      }
+      if (solid[n]) {
+        cls[n] = bnd ? CLS_SOLID_BND : CLS_SOLID;
+      } else {
+        cls[n] = bnd ? CLS_FLUID_BND : CLS_FLUID;
+        ++n_fluid;
+      }
+    }
+  }
+
+  // Eq. (25): three passes of the 27-point smoothing kernel with weights
+  // w_s(0) = 8/27, w_s(1) = 2/27, w_s(2) = 1/54, w_s(3) = 1/216 indexed by
+  // i^2 + j^2 + k^2, applied to the fluid indicator g (1 fluid, 0 solid).
+  // In 2-D the kernel is the 9-point analogue 4/9, 1/9, 1/36 (reading).
+  // Off the box: wrap on periodic axes, clamp (replicate the edge) otherwise.
+  void smooth_indicator() {
+    const double ws3[4] = {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0};
+    const double ws2[3] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0};
+    std::vector<double> g(N), h(N);
+    for (long n = 0; n < N; ++n) g[n] = solid[n] ? 0.0 : 1.0;
+    const int kr = (L.D == 3) ? 1 : 0;
+    for (int itr = 1; itr <= 3; ++itr) {
+#pragma omp parallel for schedule(static)
+      for (long n = 0; n < N; ++n) {
+        double acc = 0.0;
+        for (int k = -kr; k <= kr; ++k)
+          for (int j = -1; j <= 1; ++j)
+            for (int i = -1; i <= 1; ++i) {
+              int d[3] = {i, j, k};
+              int r2 = i * i + j * j + k * k;
+              double wgt = (L.D == 3) ? ws3[r2] : ws2[r2];
+              acc += wgt * g[neighbour(n, d, true)];
+            }
+        h[n] = acc;
+      }
+      g.swap(h);
+    }
+    gsm = g;
+  }
+
+  // Eq. (26): n_w = grad g^(3), the gradient taken with the isotropic
+  // stencil of Eq. (6) and normalised, so that n_w points from the solid
+  // into the fluid. Zero where the gradient vanishes.
+  void wall_normal() {
+    nw.assign(3 * N, 0.0);
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < N; ++n) {
+      double G[3] = {0, 0, 0};
+      for (int i = 1; i < L.Q; ++i) {
+        double gi = gsm[neighbour(n, L.e[i], true)];
+        for (int a = 0; a < 3; ++a) G[a] += 3.0 * L.w[i] * L.e[i][a] * gi;
+      }
+      double m = std::sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
+      if (m > EPS_NW)
+        for (int a = 0; a < 3; ++a) nw[a * N + n] = G[a] / m;
+    }
+  }
+
+  // ------------------------------------------------------------------ step
+  // Eq. (1), propagation half: pull f^s_i(x) from x - e_i. Halfway
+  // bounce-back (Sec. II.B, first sentence) when x - e_i is solid or off a
+  // non-periodic axis: the population that left x along -e_i returns as i.
+  void stream() {
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < N; ++n) {
+      if (solid[n]) continue;
+      for (int i = 0; i < L.Q; ++i) {
+        int d[3] = {-L.e[i][0], -L.e[i][1], -L.e[i][2]};
+        long src = neighbour(n, d, false);
+        for (int s = 0; s < 2; ++s) {
+          double v = is_fluid(src) ? f[((long)s * L.Q + i) * N + src]
+                                   : f[((long)s * L.Q + L.opp[i]) * N + n];
+          ftmp[((long)s * L.Q + i) * N + n] = v;
+        }
+      }
+    }
+  }
+
+  // Eqs. (8), (9), (7): colour densities, total density and phase field.
+  void macros() {
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < N; ++n) {
+      if (solid[n]) continue;
+      double r = 0.0, b = 0.0;
+      for (int i = 0; i < L.Q; ++i) {
+        r += ftmp[(0L * L.Q + i) * N + n];
+        b += ftmp[(1L * L.Q + i) * N + n];
+      }
+      rho_r[n] = r;
+      rho_b[n] = b;
+      phi[n] = (r - b) / (r + b);
+    }
+  }
+
+  // Appendix B, generalised from the paper's z-axis form to a flow axis a:
+  // the unknown populations are those with e_i . a = +1 at the inlet plane
+  // (coordinate 0) and e_i . a = -1 at the outlet plane (last coordinate);
+  // 6 w_i equals the 1/3 and 1/6 of Eqs. (B.4)-(B.8) and (B.14)-(B.18).
+  //   inlet, per colour s (B.1-B.8):
+  //     j^s = rho_in zeta^s - [sum_{e.a=0} f^s + 2 sum_{e.a=-1} f^s]
+  //     f^s_i = f^s_opp(i) + 6 w_i j^s - sum_t (e_i.t) N^s_t
+  //   outlet, total j with the weights chi^s of Eqs. (B.12)-(B.13):
+  //     j^t = -rho_out + [sum_{e.a=0} f^t + 2 sum_{e.a=+1} f^t]   (B.9)
+  //     f^s_i = f^s_opp(i) - 6 w_i j^t chi^s - sum_t (e_i.t) N^s_t
+  //   N^s_t = 1/2 sum_{e.a=0} (e_j.t) f^s_j  (B.2-B.3, B.10-B.11).
+  // The outlet phase field is phi(x_out - a), Eq. (39), from the streamed
+  // populations of that node (the node's own value if that node is solid).
+  // Afterwards the inlet phase field is zeta^r - zeta^b (Sec. II.D.1).
+  void zou_he() {
+    const int a = p.flow_axis;
+    const int na = dim(a);
+    const double zeta[2] = {p.zeta_r, 1.0 - p.zeta_r};
+    std::vector<long> inlet, outlet;
+    for (long n = 0; n < N; ++n) {
+      if (solid[n]) continue;
+      int c[3];
+      coords(n, c);
+      if (c[a] == 0) inlet.push_back(n);
+      if (c[a] == na - 1) outlet.push_back(n);
+    }
+    auto F_ = [&](int s, int i, long n) -> double & {
+      return ftmp[((long)s * L.Q + i) * N + n];
+    };
+    auto transverse = [&](int s, long n, double Nt[3]) {
+      for (int t = 0; t < 3; ++t) Nt[t] = 0.0;
+      for (int j = 0; j < L.Q; ++j) {
+        if (L.e[j][a] != 0) continue;
+        for (int t = 0; t < 3; ++t)
+          if (t != a) Nt[t] += 0.5 * L.e[j][t] * F_(s, j, n);
+      }
+    };
+    // phase field of the outlet nodes from the plane behind them, Eq. (39)
+    std::vector<double> phi_out(outlet.size());
+    for (size_t k = 0; k < outlet.size(); ++k) {
+      long n = outlet[k];
+      int d[3] = {0, 0, 0};
+      d[a] = -1;
+      long m = neighbour(n, d, false);
+      phi_out[k] = is_fluid(m) ? phi[m] : phi[n];
+    }
+    for (long n : inlet) {
+      for (int s = 0; s < 2; ++s) {
+        double known = 0.0;
+        for (int i = 0; i < L.Q; ++i) {
+          if (L.e[i][a] == 0) known += F_(s, i, n);
+          if (L.e[i][a] == -1) known += 2.0 * F_(s, i, n);
+        }
+        double j = p.rho_in * zeta[s] - known;
+        double Nt[3];
+        transverse(s, n, Nt);
+        for (int i = 0; i < L.Q; ++i) {
+          if (L.e[i][a] != 1) continue;
+          double corr = 0.0;
+          for (int t = 0; t < 3; ++t)
+            if (t != a) corr += L.e[i][t] * Nt[t];
+          F_(s, i, n) = F_(s, L.opp[i], n) + 6.0 * L.w[i] * j - corr;
+        }
+      }
+    }
+    for (size_t k = 0; k < outlet.size(); ++k) {
+      long n = outlet[k];
+      double known = 0.0;
+      for (int i = 0; i < L.Q; ++i) {
+        double ft = F_(0, i, n) + F_(1, i, n);
+        if (L.e[i][a] == 0) known += ft;
+        if (L.e[i][a] == 1) known += 2.0 * ft;
+      }
+      double jt = -p.rho_out + known;
+      double chi[2] = {0.5 * (1.0 + phi_out[k]), 0.5 * (1.0 - phi_out[k])};
+      for (int s = 0; s < 2; ++s) {
+        double Nt[3];
+        transverse(s, n, Nt);
+        for (int i = 0; i < L.Q; ++i) {
+          if (L.e[i][a] != -1) continue;
+          double corr = 0.0;
+          for (int t = 0; t < 3; ++t)
+            if (t != a) corr += L.e[i][t] * Nt[t];
+          F_(s, i, n) = F_(s, L.opp[i], n) - 6.0 * L.w[i] * jt * chi[s] - corr;
+        }
+      }
+    }
+    // densities of the rebuilt nodes, then the phase-field overrides
+    auto resum = [&](long n) {
+      double r = 0.0, b = 0.0;
+      for (int i = 0; i < L.Q; ++i) {
+        r += F_(0, i, n);
+        b += F_(1, i, n);
+      }
+      rho_r[n] = r;
+      rho_b[n] = b;
+    };
+    for (long n : inlet) {
+      resum(n);
+      phi[n] = zeta[0] - zeta[1];
+    }
+    for (size_t k = 0; k < outlet.size(); ++k) {
+      resum(outlet[k]);
+      phi[outlet[k]] = phi_out[k];
+    }
+  }
+
+  // Eq. (34): phase field of a solid-boundary node, the w-weighted mean of
+  // phi over its fluid lattice neighbours.
+  void extrapolate_phi() {
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < N; ++n) {
+      if (cls[n] != CLS_SOLID_BND) continue;
+      double num = 0.0, den = 0.0;
+      for (int i = 1; i < L.Q; ++i) {
+        long m = neighbour(n, L.e[i], false);
+        if (!is_fluid(m)) continue;
+        num += L.w[i] * phi[m];
+        den += L.w[i];
+      }
+      phi[n] = num / den;
+    }
+  }
+
+  // Eq. (6) with c = dt = 1, and Eq. (11)/(27): C = 3 sum_i w_i e_i
+  // phi(x + e_i), n_c = C/|C| (zero when |C| <= EPS_C).
+  void colour_gradient() {
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < N; ++n) {
+      if (solid[n]) continue;
+      double G[3] = {0, 0, 0};
+      for (int i = 1; i < L.Q; ++i) {
+        double ph = phi[neighbour(n, L.e[i], true)];
+        for (int a = 0; a < 3; ++a) G[a] += 3.0 * L.w[i] * L.e[i][a] * ph;
+      }
+      double m = std::sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
+      for (int a = 0; a < 3; ++a) {
+        C[a * N + n] = G[a];
+        nc[a * N + n] = (m > EPS_C) ? G[a] / m : 0.0;
+      }
+    }
+  }
+
+  // Eq. (28): f(v) = v . n_w - |v| cos(theta)
+  static double secant_residual(const double v[3], const double w[3],
+                                double cth) {
+    double vn = v[0] * w[0] + v[1] * w[1] + v[2] * w[2];
+    double vv = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    return vn - vv * cth;
+  }
+
+ public:
+  // Scheme-I (Leclaire et al.), Eqs. (28)-(31): secant iterates
+  // v0 = n_c, v1 = n_c - lambda (n_c + n_w) with lambda = 1/2, then
+  // v_n = (v_{n-2} f(v_{n-1}) - v_{n-1} f(v_{n-2})) / (f(v_{n-1}) - f(v_{n-2}))
+  // for n = 2, 3, 4; v4 normalised replaces n_c. If the denominator is below
+  // EPS_SECANT the iteration stops and keeps v_{n-1}; if the final vector
+  // has zero length n_c is left unchanged (the degenerate cases of Sec.
+  // II.B.1, last paragraph).
+  static void scheme1(const double n_c[3], const double n_w[3], double theta,
+                      double out[3]) {
+    const double lambda = 0.5;
+    const double cth = std::cos(theta);
+    double vm2[3], vm1[3];
+    for (int a = 0; a < 3; ++a) {
+      vm2[a] = n_c[a];
+      vm1[a] = n_c[a] - lambda * (n_c[a] + n_w[a]);
+    }
+    for (int it = 2; it <= 4; ++it) {
+      double f1 = secant_residual(vm1, n_w, cth);
+      double f2 = secant_residual(vm2, n_w, cth);
+      double den = f1 - f2;
+      if (std::fabs(den) < EPS_SECANT) break;
+      double vn[3];
+      for (int a = 0; a < 3; ++a) vn[a] = (vm2[a] * f1 - vm1[a] * f2) / den;
+      for (int a = 0; a < 3; ++a) {
+        vm2[a] = vm1[a];
+        vm1[a] = vn[a];
+      }
+    }
+    double m = std::sqrt(vm1[0] * vm1[0] + vm1[1] * vm1[1] + vm1[2] * vm1[2]);
+    for (int a = 0; a < 3; ++a) out[a] = (m > 0.0) ? vm1[a] / m : n_c[a];
+  }
+
+  // Scheme-II (Akai et al.), Eqs. (32)-(33): theta' = arccos(n_w . n_c);
+  // n_+- = (cos(+-theta) - sin(+-theta) cos(theta')/sin(theta')) n_w
+  //        + sin(+-theta)/sin(theta') n_c;
+  // n_c is replaced by whichever of n_+ and n_- lies nearer to n_c (n_+ on a
+  // tie). Left unchanged when sin(theta') < EPS_SIN.
+  static void scheme2(const double n_c[3], const double n_w[3], double theta,
+                      double out[3]) {
+    double c = n_w[0] * n_c[0] + n_w[1] * n_c[1] + n_w[2] * n_c[2];
+    c = std::min(1.0, std::max(-1.0, c));
+    double thp = std::acos(c);
+    double sp = std::sin(thp);
+    if (sp < EPS_SIN) {
+      for (int a = 0; a < 3; ++a) out[a] = n_c[a];
+      return;
+    }
+    double cp = std::cos(thp);
+    double np[3], nm[3];
+    double dp = 0.0, dm = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      double sgn_p = std::sin(theta), sgn_m = std::sin(-theta);
+      np[a] = (std::cos(theta) - sgn_p * cp / sp) * n_w[a] + sgn_p / sp * n_c[a];
+      nm[a] = (std::cos(-theta) - sgn_m * cp / sp) * n_w[a] + sgn_m / sp * n_c[a];
+      dp += (np[a] - n_c[a]) * (np[a] - n_c[a]);
+      dm += (nm[a] - n_c[a]) * (nm[a] - n_c[a]);
+    }
+    for (int a = 0; a < 3; ++a) out[a] = (dp <= dm) ? np[a] : nm[a];
+  }
+
+ private:
+  // Sec. II.B.3, step 3: at fluid-boundary nodes, turn n_c to the contact
+  // angle with Scheme-I or Scheme-II; the magnitude |C| is kept, so the
+  // colour gradient becomes |C| n_c (Sec. II.B.1).
+  void wetting() {
+    const double theta = p.theta_deg * PI / 180.0;
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < N; ++n) {
+      if (cls[n] != CLS_FLUID_BND) continue;
+      double ncv[3], nwv[3], out[3];
+      double m2 = 0.0, w2 = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        ncv[a] = nc[a * N + n];
+        nwv[a] = nw[a * N + n];
+        m2 += ncv[a] * ncv[a];
+        w2 += nwv[a] * nwv[a];
+      }
+      if (m2 == 0.0 || w2 == 0.0) continue;  // no interface or no wall normal
+      if (p.wetting == 1)
+        scheme1(ncv, nwv, theta, out);
+      else
+        scheme2(ncv, nwv, theta, out);
+      double mag = 0.0;
+      for (int a = 0; a < 3; ++a) mag += C[a * N + n] * C[a * N + n];
+      mag = std::sqrt(mag);
+      for (int a = 0; a < 3; ++a) {
+        nc[a * N + n] = out[a];
+        C[a * N + n] = mag * out[a];
+      }
+    }
+  }
+
+  // Eq. (35): n_c of a solid-boundary node, the w-weighted mean of the
+  // (post-wetting) n_c of its fluid lattice neighbours, not renormalised.
+  void extrapolate_nc() {
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < N; ++n) {
+      if (cls[n] != CLS_SOLID_BND) continue;
+      double num[3] = {0, 0, 0}, den = 0.0;
+      for (int i = 1; i < L.Q; ++i) {
+        long m = neighbour(n, L.e[i], false);
+        if (!is_fluid(m)) continue;
+        for (int a = 0; a < 3; ++a) num[a] += L.w[i] * nc[a * N + m];
+        den += L.w[i];
+      }
+      for (int a = 0; a < 3; ++a) nc[a * N + n] = num[a] / den;
+    }
+  }
+
+  // Eq. (12): curvature from the derivatives d_b n_a, each taken with the
+  // stencil of Eq. (6) applied to the component n_a (reading). Eq. (5):
+  // F = 1/2 gamma kappa C, plus the Type-II body force rho g, Eq. (36).
+  void curvature_force() {
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < N; ++n) {
+      if (solid[n]) continue;
+      double dn[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // dn[a][b] = d_b n_a
+      for (int i = 1; i < L.Q; ++i) {
+        long m = neighbour(n, L.e[i], true);
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b)
+            dn[a][b] += 3.0 * L.w[i] * L.e[i][b] * nc[a * N + m];
+      }
+      double nx_ = nc[0 * N + n], ny_ = nc[1 * N + n], nz_ = nc[2 * N + n];
+      double k = (nx_ * nx_ - 1.0) * dn[0][0] + (ny_ * ny_ - 1.0) * dn[1][1] +
+                 (nz_ * nz_ - 1.0) * dn[2][2] +
+                 (dn[0][1] + dn[1][0]) * nx_ * ny_ +
+                 (dn[0][2] + dn[2][0]) * nx_ * nz_ +
+                 (dn[2][1] + dn[1][2]) * nz_ * ny_;
+      kappa[n] = k;
+      double rho = rho_r[n] + rho_b[n];
+      for (int a = 0; a < 3; ++a)
+        F[a * N + n] = 0.5 * p.gamma * k * C[a * N + n] + rho * p.g[a];
+    }
+  }
+
+ public:
+  // Single-node collision: Eq. (2) with one rate S for every non-conserved
+  // moment and rate 0 for the conserved ones (rho, j), i.e. the relaxation
+  // matrix of Eq. (4) with S_e = S_eps = S_q = S_nu = S_pi = S_m = S.
+  // Eq. (2) is read as f'' = f - M^-1 S (m - m_eq) + M^-1 S^F (the print
+  // multiplies S^F by S). Written in velocity space this is
+  //   f''_i = f_i - S (f_i - feq_i) + (1 - S/2) G_i
+  //           + S sum_a e_ia (j_a - rho0 u_a + F_a/2) / E2
+  //   feq_i = w_i [rho + rho0 (3 e_i.u + 9/2 (e_i.u)^2 - 3/2 u.u)]   (A.4)
+  //   G_i   = w_i [3 (e_i - u) + 9 (e_i.u) e_i] . F                  (A.5)
+  // where E2 = sum_i e_ix^2 and the last term gives back the part of the
+  // first two that would relax the conserved momentum: the post-collision
+  // momentum is exactly j + F and the mass is unchanged. u is Eq. (22):
+  // u = (sum_i e_i f_i + F/2) / rho.
+  static void collide(const Lattice &L, const double *ft, const double Fv[3],
+                      double S, double rho0, double *out, double u_out[3]) {
+    double rho = 0.0, j[3] = {0, 0, 0};
+    for (int i = 0; i < L.Q; ++i) {
+      rho += ft[i];
+      for (int a = 0; a < 3; ++a) j[a] += L.e[i][a] * ft[i];
+    }
+    double E2 = 0.0;
+    for (int i = 0; i < L.Q; ++i) E2 += L.e[i][0] * L.e[i][0];
+    double u[3], back[3];
+    for (int a = 0; a < 3; ++a) u[a] = (j[a] + 0.5 * Fv[a]) / rho;
+    for (int a = 0; a < 3; ++a)
+      back[a] = S * (j[a] - rho0 * u[a] + 0.5 * Fv[a]) / E2;
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    for (int i = 0; i < L.Q; ++i) {
+      double eu = L.e[i][0] * u[0] + L.e[i][1] * u[1] + L.e[i][2] * u[2];
+      double feq = L.w[i] * (rho + rho0 * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
+      double guo = 0.0, cons = 0.0;
+      for (int a = 0; a < 3; ++a) {
+        guo += (3.0 * (L.e[i][a] - u[a]) + 9.0 * eu * L.e[i][a]) * Fv[a];
+        cons += L.e[i][a] * back[a];
+      }
+      guo *= L.w[i];
+      out[i] = ft[i] - S * (ft[i] - feq) + (1.0 - 0.5 * S) * guo + cons;
+    }
+    if (u_out)
+      for (int a = 0; a < 3; ++a) u_out[a] = u[a];
+  }
+
+ private:
+  // Eqs. (13)-(14): harmonic-mean viscosity, S_nu = 1 / (3 nu + 1/2);
+  // phi is clamped to [-1, 1] here only.
+  double relaxation_rate(double ph) const {
+    double nur = (p.tau_r - 0.5) / 3.0, nub = (p.tau_b - 0.5) / 3.0;
+    double pc = std::min(1.0, std::max(-1.0, ph));
+    double inv_nu = (1.0 + pc) / (2.0 * nur) + (1.0 - pc) / (2.0 * nub);
+    double nu = 1.0 / inv_nu;
+    return 1.0 / (3.0 * nu + 0.5);
+  }
+
+  // Collision (Eq. 2, BGK reading) followed by recolouring, Eqs. (20)-(21):
+  //   f^r'_i = rho^r/rho f^t''_i + beta w_i rho^r rho^b / rho (e_i . n)
+  //   f^b'_i = f^t''_i - f^r'_i
+  // with n the post-wetting interface normal n_c (the i = 0 term vanishes
+  // because e_0 = 0).
+  void collide_recolour() {
+#pragma omp parallel for schedule(static)
+    for (long n = 0; n < N; ++n) {
+      if (solid[n]) continue;
+      double ft[19], fpp[19], Fv[3], uu[3];
+      for (int i = 0; i < L.Q; ++i)
+        ft[i] = ftmp[(0L * L.Q + i) * N + n] + ftmp[(1L * L.Q + i) * N + n];
+      for (int a = 0; a < 3; ++a) Fv[a] = F[a * N + n];
+      double S = relaxation_rate(phi[n]);
+      collide(L, ft, Fv, S, p.rho0, fpp, uu);
+      for (int a = 0; a < 3; ++a) u[a * N + n] = uu[a];
+      double r = rho_r[n], b = rho_b[n], rho = r + b;
+      double nv[3] = {nc[0 * N + n], nc[1 * N + n], nc[2 * N + n]};
+      for (int i = 0; i < L.Q; ++i) {
+        double en = L.e[i][0] * nv[0] + L.e[i][1] * nv[1] + L.e[i][2] * nv[2];
+        double fr = r / rho * fpp[i] + p.beta * L.w[i] * r * b / rho * en;
+        f[(0L * L.Q + i) * N + n] = fr;
+        f[(1L * L.Q + i) * N + n] = fpp[i] - fr;
+      }
+    }
+  }
+
+ public:
+  void init(int q, int nx_, int ny_, int nz_, const uint8_t *mask,
+            unsigned per) {
+    L = make_lattice(q);
+    nx = nx_;
+    ny = ny_;
+    nz = nz_;
+    N = (long)nx * ny * nz;
+    periodic = per;
+    solid.assign(mask, mask + N);
+    classify();
+    smooth_indicator();
+    wall_normal();
+    f.assign(2L * L.Q * N, 0.0);
+    ftmp.assign(2L * L.Q * N, 0.0);
+    rho_r.assign(N, 0.0);
+    rho_b.assign(N, 0.0);
+    phi.assign(N, 0.0);
+    C.assign(3 * N, 0.0);
+    nc.assign(3 * N, 0.0);
+    kappa.assign(N, 0.0);
+    F.assign(3 * N, 0.0);
+    u.assign(3 * N, 0.0);
+    std::memset(&p, 0, sizeof(p));
+  }
+
+  // Initial state: f^s_i = w_i rho^s with rho^r = rho0 (1 + phi0)/2 and
+  // rho^b = rho0 (1 - phi0)/2 (a fluid at rest).
+  void init_state(const double *phi0) {
+    std::fill(f.begin(), f.end(), 0.0);
+    for (long n = 0; n < N; ++n) {
+      if (solid[n]) continue;
+      double r = p.rho0 * 0.5 * (1.0 + phi0[n]);
+      double b = p.rho0 * 0.5 * (1.0 - phi0[n]);
+      for (int i = 0; i < L.Q; ++i) {
+        f[(0L * L.Q + i) * N + n] = L.w[i] * r;
+        f[(1L * L.Q + i) * N + n] = L.w[i] * b;
+      }
+      rho_r[n] = r;
+      rho_b[n] = b;
+      phi[n] = (r - b) / (r + b);
+    }
+    std::fill(u.begin(), u.end(), 0.0);
+  }
+
+  // One time step in the order of Eq. (1) and Sec. II.B.3: stream (with
+  // bounce-back), macros, Zou-He (which rebuilds the macros of its two
+  // planes), Eq. 34, Eqs. 6/27, wetting, Eq. 35, Eqs. 12 and 5, collision,
+  // recolouring.
+  void stream_part() {
+    stream();
+    macros();
+    if (p.zou_he) zou_he();
+  }
+
+  void step() {
+    stream_part();
+    extrapolate_phi();
+    colour_gradient();
+    if (p.wetting) wetting();
+    extrapolate_nc();
+    curvature_force();
+    collide_recolour();
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+void *orc_create(int lattice, int nx, int ny, int nz, const uint8_t *solid,
+                 unsigned periodic_mask) {
+  if (lattice != 9 && lattice != 19) return nullptr;
+  if (lattice == 9 && nz != 1) return nullptr;
+  Oracle *o = new Oracle();
+  o->init(lattice, nx, ny, nz, solid, periodic_mask);
+  return o;
+}
+
+void orc_destroy(void *h) { delete static_cast<Oracle *>(h); }
+
+void orc_set_params(void *h, const orc_params *p) {
+  static_cast<Oracle *>(h)->p = *p;
+}
+
+void orc_init_state(void *h, const double *phi0) {
+  static_cast<Oracle *>(h)->init_state(phi0);
+}
+
+void orc_set_pops(void *h, const double *src) {
+  Oracle *o = static_cast<Oracle *>(h);
+  std::memcpy(o->f.data(), src, sizeof(double) * o->f.size());
+}
+
+void orc_get_pops(void *h, double *dst) {
+  Oracle *o = static_cast<Oracle *>(h);
+  std::memcpy(dst, o->f.data(), sizeof(double) * o->f.size());
+}
+
+void orc_step(void *h, int nsteps) {
+  Oracle *o = static_cast<Oracle *>(h);
+  for (int s = 0; s < nsteps; ++s) o->step();
+}
+
+// The first half of a step only: streaming with bounce-back, the macros
+// and, when enabled, Zou-He; the streamed (and rebuilt) populations go to
+// dst (2QN). The stored state is not changed.
+void orc_stream_only(void *h, double *dst) {
+  Oracle *o = static_cast<Oracle *>(h);
+  o->stream_part();
+  std::memcpy(dst, o->ftmp.data(), sizeof(double) * o->ftmp.size());
+}
+
+// Classes (0 solid, 1 solid-boundary, 2 fluid, 3 fluid-boundary), the
+// smoothed indicator g^(3) and the wall normal (3N).
+void orc_geometry(void *h, uint8_t *cls, double *gsm, double *nw) {
+  Oracle *o = static_cast<Oracle *>(h);
+  if (cls) std::memcpy(cls, o->cls.data(), o->N);
+  if (gsm) std::memcpy(gsm, o->gsm.data(), sizeof(double) * o->N);
+  if (nw) std::memcpy(nw, o->nw.data(), sizeof(double) * 3 * o->N);
+}
+
+// Fields of the most recent step: rho = rho^r + rho^b, phi (with the
+// inlet/outlet overrides and the Eq. 34 values at solid-boundary nodes),
+// u (Eq. 22, 3N), n_c (3N, post-wetting and Eq. 35), kappa, F (3N).
+void orc_fields(void *h, double *rho, double *phi, double *u, double *nc,
+                double *kappa, double *F) {
+  Oracle *o = static_cast<Oracle *>(h);
+  const long N = o->N;
+  if (rho)
+    for (long n = 0; n < N; ++n) rho[n] = o->rho_r[n] + o->rho_b[n];
+  if (phi) std::memcpy(phi, o->phi.data(), sizeof(double) * N);
+  if (u) std::memcpy(u, o->u.data(), sizeof(double) * 3 * N);
+  if (nc) std::memcpy(nc, o->nc.data(), sizeof(double) * 3 * N);
+  if (kappa) std::memcpy(kappa, o->kappa.data(), sizeof(double) * N);
+  if (F) std::memcpy(F, o->F.data(), sizeof(double) * 3 * N);
+}
+
+// Diagnostics over the fluid nodes:
+//  0: red mass sum_x sum_i f^r_i of the stored state
+//  1: blue mass, likewise
+//  2: S_w, the fraction of fluid nodes with phi < 0 (Sec. IV.B)
+//  3: smooth S_w, mean of (1 - phi)/2
+//  4: pressure drop: mean rho/3 (Eq. 23) on the inlet plane minus the same
+//     on the outlet plane of the flow axis
+//  5: capillary number of fluid r: rho0 nu^r <u_a>_{phi>0} / gamma
+//  6: capillary number of fluid b: rho0 nu^b <u_a>_{phi<0} / gamma
+// Kinds 2-6 use the fields of the most recent step (orc_fields).
+double orc_reduce(void *h, int kind) {
+  Oracle *o = static_cast<Oracle *>(h);
+  const long N = o->N;
+  const int Q = o->L.Q;
+  if (kind == 0 || kind == 1) {
+    double s = 0.0;
+    for (long n = 0; n < N; ++n) {
+      if (o->solid[n]) continue;
+      for (int i = 0; i < Q; ++i) s += o->f[((long)kind * Q + i) * N + n];
+    }
+    return s;
+  }
+  if (kind == 2 || kind == 3) {
+    double s = 0.0;
+    for (long n = 0; n < N; ++n) {
+      if (o->solid[n]) continue;
+      if (kind == 2)
+        s += (o->phi[n] < 0.0) ? 1.0 : 0.0;
+      else
+        s += 0.5 * (1.0 - o->phi[n]);
+    }
+    return s / (double)o->n_fluid;
+  }
+  if (kind == 4) {
+    const int a = o->p.flow_axis, na = o->dim(a);
+    double si = 0.0, so = 0.0;
+    long ci = 0, co = 0;
+    for (long n = 0; n < N; ++n) {
+      if (o->solid[n]) continue;
+      int c[3];
+      o->coords(n, c);
+      double P = (o->rho_r[n] + o->rho_b[n]) / 3.0;
+      if (c[a] == 0) {
+        si += P;
+        ++ci;
+      }
+      if (c[a] == na - 1) {
+        so += P;
+        ++co;
+      }
+    }
+    return (ci ? si / ci : 0.0) - (co ? so / co : 0.0);
+  }
+  if (kind == 5 || kind == 6) {
+    const int a = o->p.flow_axis;
+    double s = 0.0;
+    long c = 0;
+    for (long n = 0; n < N; ++n) {
+      if (o->solid[n]) continue;
+      bool red = o->phi[n] > 0.0;
+      if ((kind == 5) != red) continue;
+      s += o->u[a * N + n];
+      ++c;
+    }
+    double tau = (kind == 5) ? o->p.tau_r : o->p.tau_b;
+    double mu = o->p.rho0 * (tau - 0.5) / 3.0;
+    return c ? mu * (s / c) / o->p.gamma : 0.0;
+  }
+  return NAN;
+}
+
+// ---- single-equation entry points for the tests --------------------------
+
+// Lattice tables: e (Q x 3 ints), w (Q), opposite index (Q). Returns Q.
+int orc_lattice(int lattice, int *e, double *w, int *opp) {
+  Lattice L = make_lattice(lattice);
+  for (int i = 0; i < L.Q; ++i) {
+    for (int a = 0; a < 3; ++a) e[3 * i + a] = L.e[i][a];
+    w[i] = L.w[i];
+    opp[i] = L.opp[i];
+  }
+  return L.Q;
+}
+
+void orc_scheme1(const double *n_c, const double *n_w, double theta,
+                 double *out) {
+  Oracle::scheme1(n_c, n_w, theta, out);
+}
+
+void orc_scheme2(const double *n_c, const double *n_w, double theta,
+                 double *out) {
+  Oracle::scheme2(n_c, n_w, theta, out);
+}
+
+// One node's collision (BGK reading of Eq. 2) on total populations ft (Q).
+void orc_collide(int lattice, const double *ft, const double *F, double S,
+                 double rho0, double *out, double *u) {
+  Lattice L = make_lattice(lattice);
+  Oracle::collide(L, ft, F, S, rho0, out, u);
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+}  // extern "C"

@@ -1,0 +1,209 @@
+"""Python handle on the FP64 CPU oracle (``lbm_oracle.cpp``).
+
+Test infrastructure only: the test-suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` use it; the product path never does.
+
+Arrays follow the project's layout: a field has numpy shape ``(nz, ny, nx)``
+(x fastest), populations ``(2, Q, nz, ny, nx)`` with colour 0 = red, 1 = blue,
+vector fields ``(3, nz, ny, nx)``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbm_oracle.cpp")
+_LIB = os.path.join(_HERE, "liblbm_oracle.so")
+
+MASS_R, MASS_B, SW_COUNT, SW_SMOOTH, DP, CA_R, CA_B = range(7)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with g++ (plain -O2, OpenMP) next to its source."""
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    subprocess.run(["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared",
+                    _SRC, "-o", tmp], check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Params(C.Structure):
+    _fields_ = [("tau_r", C.c_double), ("tau_b", C.c_double),
+                ("gamma", C.c_double), ("beta", C.c_double),
+                ("rho0", C.c_double), ("theta_deg", C.c_double),
+                ("wetting", C.c_int), ("zou_he", C.c_int),
+                ("flow_axis", C.c_int),
+                ("rho_in", C.c_double), ("rho_out", C.c_double),
+                ("zeta_r", C.c_double), ("g", C.c_double * 3)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        dp = C.POINTER(C.c_double)
+        L.orc_create.restype = C.c_void_p
+        L.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int,
+                                 C.c_void_p, C.c_uint]
+        L.orc_destroy.argtypes = [C.c_void_p]
+        L.orc_set_params.argtypes = [C.c_void_p, C.POINTER(_Params)]
+        L.orc_init_state.argtypes = [C.c_void_p, C.c_void_p]
+        L.orc_set_pops.argtypes = [C.c_void_p, C.c_void_p]
+        L.orc_get_pops.argtypes = [C.c_void_p, C.c_void_p]
+        L.orc_step.argtypes = [C.c_void_p, C.c_int]
+        L.orc_stream_only.argtypes = [C.c_void_p, C.c_void_p]
+        L.orc_geometry.argtypes = [C.c_void_p] + [C.c_void_p] * 3
+        L.orc_fields.argtypes = [C.c_void_p] + [C.c_void_p] * 6
+        L.orc_reduce.restype = C.c_double
+        L.orc_reduce.argtypes = [C.c_void_p, C.c_int]
+        L.orc_lattice.restype = C.c_int
+        L.orc_lattice.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]
+        L.orc_scheme1.argtypes = [dp, dp, C.c_double, dp]
+        L.orc_scheme2.argtypes = [dp, dp, C.c_double, dp]
+        L.orc_collide.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_double,
+                                  C.c_double, C.c_void_p, C.c_void_p]
+        L.orc_max_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _vec(v):
+    return (C.c_double * 3)(*[float(x) for x in v])
+
+
+def lattice(q: int):
+    """Velocities (Q, 3), weights (Q,), opposite index (Q,)."""
+    e = np.zeros((19, 3), np.int32)
+    w = np.zeros(19)
+    o = np.zeros(19, np.int32)
+    n = lib().orc_lattice(q, _ptr(e), _ptr(w), _ptr(o))
+    return e[:n].copy(), w[:n].copy(), o[:n].copy()
+
+
+def scheme1(n_c, n_w, theta_rad):
+    out = (C.c_double * 3)()
+    lib().orc_scheme1(_vec(n_c), _vec(n_w), float(theta_rad), out)
+    return np.array(out[:])
+
+
+def scheme2(n_c, n_w, theta_rad):
+    out = (C.c_double * 3)()
+    lib().orc_scheme2(_vec(n_c), _vec(n_w), float(theta_rad), out)
+    return np.array(out[:])
+
+
+def collide(q, ft, F, S, rho0=1.0):
+    ft = np.ascontiguousarray(ft, np.float64)
+    Fv = np.ascontiguousarray(F, np.float64)
+    out = np.zeros(q)
+    u = np.zeros(3)
+    lib().orc_collide(q, _ptr(ft), _ptr(Fv), float(S), float(rho0),
+                      _ptr(out), _ptr(u))
+    return out, u
+
+
+PARAM_DEFAULTS = dict(tau_r=1.0, tau_b=1.0, gamma=0.01, beta=0.7, rho0=1.0,
+                      theta_deg=90.0, wetting=0, zou_he=0, flow_axis=0,
+                      rho_in=1.0, rho_out=1.0, zeta_r=1.0, g=(0.0, 0.0, 0.0))
+
+
+class Oracle:
+    """One oracle domain: geometry, state and parameters."""
+
+    def __init__(self, lattice_q: int, solid: np.ndarray,
+                 periodic=(True, True, True)):
+        solid = np.ascontiguousarray(solid, dtype=np.uint8)
+        if solid.ndim == 2:
+            solid = solid[None]
+        self.q = lattice_q
+        self.shape = solid.shape  # (nz, ny, nx)
+        nz, ny, nx = self.shape
+        self.N = nx * ny * nz
+        self.solid = solid
+        mask = sum((1 << a) for a in range(3) if periodic[a])
+        self._h = lib().orc_create(lattice_q, nx, ny, nz, _ptr(solid), mask)
+        if not self._h:
+            raise ValueError("oracle: bad lattice/shape")
+        self.params = dict(PARAM_DEFAULTS)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.orc_destroy(h)
+            self._h = None
+
+    def set_params(self, **kw):
+        for k in kw:
+            if k not in PARAM_DEFAULTS:
+                raise KeyError(k)
+        self.params.update(kw)
+        p = self.params
+        st = _Params(p["tau_r"], p["tau_b"], p["gamma"], p["beta"], p["rho0"],
+                     p["theta_deg"], int(p["wetting"]), int(p["zou_he"]),
+                     int(p["flow_axis"]), p["rho_in"], p["rho_out"],
+                     p["zeta_r"], (C.c_double * 3)(*p["g"]))
+        lib().orc_set_params(self._h, C.byref(st))
+
+    def init_state(self, phi0: np.ndarray):
+        a = np.ascontiguousarray(np.broadcast_to(phi0, self.shape), np.float64)
+        lib().orc_init_state(self._h, _ptr(a))
+
+    @property
+    def pops(self) -> np.ndarray:
+        out = np.zeros((2, self.q) + self.shape)
+        lib().orc_get_pops(self._h, _ptr(out))
+        return out
+
+    @pops.setter
+    def pops(self, f: np.ndarray):
+        a = np.ascontiguousarray(f, np.float64).reshape((2, self.q) + self.shape)
+        lib().orc_set_pops(self._h, _ptr(a))
+
+    def step(self, n: int = 1):
+        lib().orc_step(self._h, int(n))
+
+    def stream_only(self) -> np.ndarray:
+        """Streamed (and Zou-He rebuilt) populations of the next step,
+        without changing the stored state."""
+        out = np.zeros((2, self.q) + self.shape)
+        lib().orc_stream_only(self._h, _ptr(out))
+        return out
+
+    def geometry(self):
+        cls = np.zeros(self.shape, np.uint8)
+        gsm = np.zeros(self.shape)
+        nw = np.zeros((3,) + self.shape)
+        lib().orc_geometry(self._h, _ptr(cls), _ptr(gsm), _ptr(nw))
+        return cls, gsm, nw
+
+    def fields(self):
+        rho = np.zeros(self.shape)
+        phi = np.zeros(self.shape)
+        u = np.zeros((3,) + self.shape)
+        nc = np.zeros((3,) + self.shape)
+        kap = np.zeros(self.shape)
+        F = np.zeros((3,) + self.shape)
+        lib().orc_fields(self._h, _ptr(rho), _ptr(phi), _ptr(u), _ptr(nc),
+                         _ptr(kap), _ptr(F))
+        return dict(rho=rho, phi=phi, u=u, nc=nc, kappa=kap, F=F)
+
+    def reduce(self, kind: int) -> float:
+        return lib().orc_reduce(self._h, int(kind))
+
+
+def max_threads() -> int:
+    return lib().orc_max_threads()
