@@ -1,0 +1,389 @@
+#!/usr/bin/env python
+"""Throughput of the two-colour LBM step on the synthetic 256^3 porous rock
+(primary drainage, Type-I Zou-He ends, Scheme-I wetting, FP32 storage).
+
+One JSON line on rank 0:
+  value      fluid-node updates per second / 1e6 (MLUPS), whole job over all
+             ranks, populations resident in HBM, CUDA events around K steps;
+  e2e        the same metric through the public API from host buffers: the
+             solid image and phi0 copied in from pinned memory, geometry set-up,
+             K steps each followed by the FP64 saturation read-back (8 bytes),
+             the final phase field copied out;
+  roofline   the collision pass (the dominant kernel) against the measured
+             HBM copy bandwidth, algorithmic bytes = 2 x 2Q x 4 B per fluid
+             node (populations read + written);
+  cpu_baseline  the FP64 oracle on a bounded slab of the same rock.
+
+`--impl reference` times the oracle (the reference arm of this build) on the
+host cores instead. Several GPUs (torchrun) run independent replicas.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import shutil
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % HBM roofline: plain FP32 vs FP16-storage/batched at stated error"
+BYTES_POP = {"fp32": 4, "fp16": 2, "bf16": 2}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="fp32", choices=["fp32", "fp16", "bf16"])
+    ap.add_argument("--drive", default="typeI", choices=["typeI", "typeII"])
+    ap.add_argument("--size", type=int, default=256)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2407_10914_gb300 import workloads as W
+    n = args.size
+    case = W.porous_3d(n=(n, n, n), drive=args.drive)
+    name = f"porous{n}_drainage_{args.drive}_{args.storage}"
+    return case, name
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.path = None
+        self.idx = gpu_index
+        exe = shutil.which("nvidia-smi")
+        if exe:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                [exe, f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(gpu_index), "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4)
+                          if r[5 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    return 6800.0, "fallback 6.8 TB/s"
+
+
+def kernel_source_hash():
+    h = hashlib.sha1()
+    for f in ("step.cu", "stencil.cuh", "lattice.cuh", "context.hpp"):
+        h.update(open(os.path.join(ROOT, "paper_2407_10914_gb300", "csrc", f),
+                      "rb").read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summary (profiles/dram_traffic.txt), if it was taken on the current
+    kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(p):
+        return None
+    want = kernel_source_hash()
+    for line in open(p):
+        parts = line.split()
+        if len(parts) >= 4 and not line.startswith("#"):
+            if parts[0] == kernel and parts[1] == workload and parts[3] == want:
+                return float(parts[2])
+    return None
+
+
+# --------------------------------------------------------- CPU oracle
+def oracle_sample(case, planes: int):
+    """A slab of the first `planes` x-planes of the rock (inlet reservoir +
+    rock), same parameters, as a bounded sample for the oracle."""
+    from paper_2407_10914_gb300 import workloads as W
+    solid = np.ascontiguousarray(case.solid[:, :, :planes])
+    phi0 = np.ascontiguousarray(case.phi0[:, :, :planes])
+    return W.Case(case.name + f"_slab{planes}", case.lattice, solid,
+                  case.periodic, phi0, dict(case.params))
+
+
+def time_oracle(case, planes: int, steps: int, warmup: int = 0):
+    from oracle import oracle as O
+    O.build()
+    sample = oracle_sample(case, planes)
+    o = O.Oracle(sample.lattice, sample.solid, sample.periodic)
+    o.set_params(**sample.params)
+    o.init_state(sample.phi0)
+    if warmup:
+        o.step(warmup)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    nf = int((sample.solid == 0).sum())
+    return dict(value=nf * steps / dt / 1e6, unit="MLUPS", cores=O.max_threads(),
+                kind="oracle",
+                sample=f"first {planes} x-planes of the {case.solid.shape[2]}^3 "
+                       f"rock ({nf} fluid nodes), {steps} steps, FP64 oracle",
+                seconds=dt)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_init(args)
+    if rank != 0:
+        return
+    case, name = workload(args)
+    # size the slab so that warm-up + timed steps take about 90 s
+    probe = time_oracle(case, 6, 1, 0)
+    per_plane = probe["seconds"] / 6.0
+    planes = int(90.0 / max(1, args.steps + args.warmup) / per_plane)
+    planes = max(3, min(case.solid.shape[2], planes))
+    res = time_oracle(case, planes, args.steps, args.warmup)
+    line = {"impl": "reference", "metric": METRIC, "value": round(res["value"], 3),
+            "unit": "MLUPS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * res["seconds"] / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "sample": res["sample"]},
+            "cpu_baseline": {k: res[k] for k in ("value", "unit", "cores", "kind",
+                                                  "sample")},
+            "e2e": {"value": round(res["value"], 3), "unit": "MLUPS",
+                    "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------- our arm
+def run_ours(args):
+    import torch
+    from paper_2407_10914_gb300 import build, lbm
+
+    ws, rank, local = dist_init(args)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    build.build()
+    case, name = workload(args)
+    Q = case.lattice
+    s = lbm.Session(Q, case.solid, case.periodic, args.storage)
+    s.set_params(**case.params)
+    s.init_state(case.phi0.astype(np.float32))
+    nf = s.n_fluid
+    n_sbnd = s.counts[2]
+    passes = 5 if n_sbnd > 0 else 3
+    stream = torch.cuda.current_stream()
+
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    ms_max = max_over_ranks(ms, ws)
+    value = ws * nf * args.steps / (ms_max * 1e-3) / 1e6
+
+    # per-pass times (events inside the library, on the same stream)
+    k2 = max(1, min(args.steps, 200))
+    pass_ms = s.step_timed(k2)
+    coll_ms = pass_ms["collide"] / k2
+    bpp = BYTES_POP[args.storage]
+    alg_bytes = 2 * 2 * Q * 4 * nf if args.storage == "fp32" else 2 * Q * 4 * nf
+    achieved = alg_bytes / (coll_ms * 1e-3) / 1e9
+    peak, peak_src = measured_peaks()
+    traffic = recorded_traffic("k_collide", name)
+    step_bytes = (2 * 2 * Q * bpp + 4) * nf  # populations read+written + link bits
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = end_to_end(args, case, torch, lbm)
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = time_oracle(case, 32, 6, 0)
+        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "MLUPS",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {
+                "workload": name, "grid": list(case.solid.shape[::-1]),
+                "fluid_nodes": nf, "nodes": case.n_nodes,
+                "rock_porosity": round(case.info.get("rock_porosity", 0), 4),
+                "storage": args.storage, "lattice": "D3Q19",
+                "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                "l2": "inputs larger than L2 (two population buffers of "
+                      f"{2 * Q * bpp * case.n_nodes / 1e9:.2f} GB)",
+            },
+            "roofline": {"bound": "hbm", "kernel": "k_collide",
+                         "achieved": round(achieved, 1), "peak": peak,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": traffic, "peak_source": peak_src,
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "avg_launch_ms": round(coll_ms, 5)},
+            "step_bandwidth": {"bytes_per_update": 2 * 2 * Q * bpp + 4,
+                               "GBps": round(step_bytes / (ms_max / args.steps
+                                                           * 1e-3) / 1e9, 1),
+                               "frac_of_measured_peak": round(
+                                   step_bytes / (ms_max / args.steps * 1e-3)
+                                   / 1e9 / peak, 4)},
+            "pass_ms_per_step": {k: round(v / k2, 5) for k, v in pass_ms.items()},
+            "gpu_launches": passes * args.steps,
+            "clocks": clk,
+            "total_node_MLUPS": round(ws * case.n_nodes * args.steps
+                                      / (ms_max * 1e-3) / 1e6, 1),
+        }
+        if e2e:
+            line["e2e"] = e2e
+        if cpu:
+            line["cpu_baseline"] = cpu
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def end_to_end(args, case, torch, lbm):
+    """The user's call sequence from host memory: workspace allocated
+    beforehand; timed: lbm_init_geometry (solid image H2D from pinned host
+    memory), phi0 H2D (pinned), K x (step + S_w read-back), final phi D2H."""
+    from paper_2407_10914_gb300.lbm import (STORAGE, lbm_init_geometry,
+                                            lbm_workspace_bytes)
+    import ctypes as C
+    nz, ny, nx = case.solid.shape
+    Q = case.lattice
+    solid_pin = torch.from_numpy(case.solid.reshape(-1)).pin_memory()
+    phi_pin = torch.from_numpy(case.phi0.astype(np.float32).reshape(-1)).pin_memory()
+    out_pin = torch.empty(case.n_nodes, dtype=torch.float32).pin_memory()
+    mask = sum((1 << a) for a in range(3) if case.periodic[a])
+    wsb = lbm_workspace_bytes(Q, nx, ny, nz, case.solid, STORAGE[args.storage])
+    work = torch.empty(wsb, dtype=torch.uint8, device="cuda")
+    phi_dev = torch.empty(case.n_nodes, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    sp = C.c_void_p(stream.cuda_stream)
+    L = lbm.load_library()
+    steps = args.steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h = C.c_void_p()
+    st = L.lbm_init_geometry(C.byref(h), Q, nx, ny, nz,
+                             C.c_void_p(solid_pin.data_ptr()), mask,
+                             STORAGE[args.storage], C.c_void_p(work.data_ptr()),
+                             wsb, sp)
+    assert st == 0, st
+    lbm.lbm_set_params(h, lbm.make_params(**case.params))
+    phi_dev.copy_(phi_pin, non_blocking=True)
+    lbm.lbm_init_state(h, phi_dev, sp)
+    sw = 0.0
+    for _ in range(steps):
+        lbm.lbm_step(h, 1, sp)
+        sw = lbm.lbm_reduce(h, lbm.LBM_SW_COUNT, sp)
+    lbm.lbm_macros(h, None, phi_dev, None, sp)
+    out_pin.copy_(phi_dev, non_blocking=True)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    lbm.lbm_destroy(h)
+    nf = int((case.solid == 0).sum())
+    return {"value": round(nf * steps / dt / 1e6, 2), "unit": "MLUPS",
+            "h2d_bytes_per_step": round((case.n_nodes * 5) / steps, 1),
+            "d2h_bytes_per_step": round(8 + case.n_nodes * 4 / steps, 1),
+            "final_sw": sw, "seconds": round(dt, 3),
+            "note": "geometry set-up, phi0 upload, per-step S_w read-back "
+                    "and the final phi download inside the timed region"}
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

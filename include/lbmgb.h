@@ -1,0 +1,180 @@
+/*
+ * lbmgb.h - C-ABI of the GB300 two-colour lattice-Boltzmann step.
+ *
+ * The method is the colour-gradient model studied in Sedahmed & Coelho,
+ * "Wetting and pressure gradient performance in lattice Boltzmann color
+ * gradient model" (arXiv:2407.10914), Sec. II: two populations f^r, f^b on a
+ * D3Q19 (Eq. A.1) or D2Q9 lattice; streaming with halfway bounce-back at
+ * solid nodes (Eq. 1); Zou-He pressure ends (Type-I, Sec. II.C.1 and App. B)
+ * or a uniform body force (Type-II, Eq. 36); phase field (Eq. 7), colour
+ * gradient (Eq. 6), wetting by Scheme-I (Eqs. 28-31) or Scheme-II (Eqs.
+ * 32-33) with the extrapolations of Eqs. 34-35, curvature (Eq. 12), CSF force
+ * (Eq. 5), the single-rate (BGK) form of the collision of Eq. 2 with the
+ * viscosity of Eqs. 13-14, and recolouring (Eqs. 20-21).
+ *
+ * Conventions shared by every call:
+ *  - Layout. A field over the box has N = nx*ny*nz entries, node
+ *    n = x + nx*(y + ny*z), x fastest. Populations exchanged with the caller
+ *    are float32 [2][Q][N] (colour 0 = red "r", 1 = blue "b"); vector fields
+ *    are [3][N]. For D2Q9, nz = 1 and the velocities are the z-free members
+ *    of Eq. (A.1) in that order: (0,0) (1,0) (-1,0) (0,1) (0,-1) (1,1)
+ *    (-1,1) (1,-1) (-1,-1).
+ *  - Memory. The caller owns all device memory. lbm_workspace_bytes() says
+ *    how much one domain needs; the caller allocates it (any allocator) and
+ *    passes it to lbm_init_geometry(); the library never calls cudaMalloc.
+ *    Host arrays are read during the call and not kept.
+ *  - Streams. `stream` is a cudaStream_t passed as void* (0 = legacy
+ *    default stream). Calls enqueue work and return, except lbm_reduce() and
+ *    lbm_workspace_bytes(), which synchronise the stream.
+ *  - Errors. Every call returns an lbm_status. Argument errors are found
+ *    before anything is enqueued; lbm_last_error() then holds a message.
+ *    A handle is used by one host thread and one stream at a time.
+ */
+#ifndef LBMGB_H
+#define LBMGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx *lbm_handle;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = -1,       /* invalid argument (nothing was enqueued)      */
+  LBM_ERR_CUDA = -2,      /* a CUDA call failed                            */
+  LBM_ERR_STATE = -3,     /* call order: params/state not set yet          */
+  LBM_ERR_NONFINITE = -4, /* a reduction met NaN/Inf                       */
+  LBM_ERR_TIMEOUT = -5,   /* a bounded device wait gave up                 */
+  LBM_ERR_NOMEM = -6      /* workspace smaller than lbm_workspace_bytes()  */
+} lbm_status;
+
+/* Node classes returned by lbm_get_geometry(). */
+enum {
+  LBM_CLS_SOLID = 0,     /* solid, no fluid lattice neighbour               */
+  LBM_CLS_SOLID_BND = 1, /* solid with a fluid neighbour (Eqs. 34-35 act)   */
+  LBM_CLS_FLUID = 2,     /* fluid, no solid neighbour                       */
+  LBM_CLS_FLUID_BND = 3  /* fluid with a solid neighbour (wetting acts)     */
+};
+
+/* Population storage (chosen at lbm_init_geometry). */
+enum {
+  LBM_STORAGE_FP32 = 0, /* f^r, f^b as float32                              */
+  LBM_STORAGE_FP16 = 1, /* T = f^r + f^b - w rho0 and D = f^r - f^b, fp16   */
+  LBM_STORAGE_BF16 = 2  /* the same offsets in bfloat16                     */
+};
+
+/* Reduction kinds of lbm_reduce(). */
+enum {
+  LBM_MASS_R = 0,    /* sum over fluid nodes of sum_i f^r_i (stored state)  */
+  LBM_MASS_B = 1,    /* the same for f^b                                    */
+  LBM_SW_COUNT = 2,  /* S_w: fraction of fluid nodes with phi < 0 (Sec.IV.B)*/
+  LBM_SW_SMOOTH = 3, /* mean over fluid nodes of (1 - phi)/2                */
+  LBM_DP = 4,        /* mean rho/3 (Eq. 23) on the inlet plane minus the
+                        same on the outlet plane of the flow axis           */
+  LBM_CA_R = 5,      /* rho0 nu^r <u_a>_{phi>0} / gamma (not in the paper)  */
+  LBM_CA_B = 6       /* rho0 nu^b <u_a>_{phi<0} / gamma (not in the paper)  */
+};
+
+typedef struct {
+  double tau_r, tau_b; /* relaxation times, > 1/2; nu^s = (tau^s-1/2)/3 (Eq.13)*/
+  double gamma;        /* interfacial tension (Eq. 5)                        */
+  double beta;         /* recolouring segregation parameter, [0,1] (Eq. 20) */
+  double rho0;         /* reference density of the equilibrium (Eq. A.4)    */
+  double theta_deg;    /* contact angle, degrees, measured through fluid b  */
+  int wetting;         /* 0 none, 1 Scheme-I (Leclaire), 2 Scheme-II (Akai) */
+  int zou_he;          /* 1: Zou-He inlet (coordinate 0) and outlet (last
+                          coordinate) on flow_axis, which must not be
+                          periodic (Type-I; or the ends of a Type-II run)   */
+  int flow_axis;       /* 0 = x, 1 = y, 2 = z                               */
+  double rho_in, rho_out; /* Zou-He densities (Eqs. B.1, B.9)               */
+  double zeta_r;       /* injected red fraction zeta^r in [0,1]; zeta^b =
+                          1 - zeta^r; the inlet phase field is zeta^r -
+                          zeta^b (Sec. II.D.1)                              */
+  double g[3];         /* body acceleration; force density rho*g (Eq. 36)  */
+} lbm_params;
+
+/* Device bytes one domain needs (populations A/B, phase field, normals,
+ * classes, wall normals, lists, macros, reduction scratch). solid_host may
+ * be NULL (the bound then assumes every node fluid). Returns 0 on a bad
+ * argument. */
+size_t lbm_workspace_bytes(int lattice, int nx, int ny, int nz,
+                           const uint8_t *solid_host, int storage);
+
+/* Create a domain. lattice = 9 (D2Q9, nz must be 1) or 19 (D3Q19).
+ * solid_host: N bytes, nonzero = solid (host memory, copied).
+ * periodic_mask: bit a set = axis a periodic; a non-periodic face that is
+ * not a Zou-He plane acts as a halfway bounce-back wall without wetting.
+ * Builds, on the device, the node classes, the three-pass smoothing of
+ * Eq. (25) and the wall normal of Eq. (26) (gradient of the smoothed fluid
+ * indicator by the Eq. 6 stencil, normalised; it points into the fluid).
+ * dev_workspace: caller-owned device memory of ws_bytes >=
+ * lbm_workspace_bytes(), 256-byte aligned, kept until lbm_destroy(). */
+lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
+                             int nz, const uint8_t *solid_host,
+                             unsigned periodic_mask, int storage,
+                             void *dev_workspace, size_t ws_bytes,
+                             void *stream);
+
+/* Set the parameters (host struct, copied). Validates them. */
+lbm_status lbm_set_params(lbm_handle h, const lbm_params *p);
+
+/* Fluid at rest: f^s_i = w_i rho^s with rho^r = rho0 (1 + phi0)/2,
+ * rho^b = rho0 (1 - phi0)/2. phi0_dev: device float32 [N] (solid entries
+ * ignored). Needs lbm_set_params() first. */
+lbm_status lbm_init_state(lbm_handle h, const float *phi0_dev, void *stream);
+
+/* Advance nsteps time steps (Eq. 1), asynchronously. */
+lbm_status lbm_step(lbm_handle h, int nsteps, void *stream);
+
+/* Profiling form of lbm_step(): the same nsteps steps, with CUDA events
+ * recorded on `stream` around each of the five passes of a step (phase
+ * field; Eq. 34; gradient and wetting; Eq. 35; collision). Adds the elapsed
+ * milliseconds of each pass, summed over the steps, to pass_ms[0..4] (host
+ * array) and synchronises the stream. The results equal lbm_step()'s. */
+lbm_status lbm_step_timed(lbm_handle h, int nsteps, void *stream,
+                          double *pass_ms);
+
+/* Fields of the most recent step, each into caller device buffers (any may
+ * be NULL): rho [N] (rho^r + rho^b after streaming and Zou-He), phi [N]
+ * (with the inlet/outlet values and, at solid-boundary nodes, Eq. 34), u
+ * [3][N] (Eq. 22). Solid nodes hold 0 (phi: Eq. 34 value at solid-boundary
+ * nodes). Before the first step: the initial state, u = 0. */
+lbm_status lbm_macros(lbm_handle h, float *rho, float *phi, float *u,
+                      void *stream);
+
+/* One reduction (kind LBM_MASS_R ... LBM_CA_B), accumulated in FP64,
+ * written to *out_host; synchronises the stream. LBM_ERR_NONFINITE if the
+ * sum is not finite. */
+lbm_status lbm_reduce(lbm_handle h, int kind, double *out_host, void *stream);
+
+/* The stored (post-recolouring) populations as float32 [2][Q][N] in the
+ * caller's device buffer (solid nodes 0), and back. */
+lbm_status lbm_get_populations(lbm_handle h, float *dst_dev, void *stream);
+lbm_status lbm_set_populations(lbm_handle h, const float *src_dev,
+                               void *stream);
+
+/* Node classes (uint8 [N], LBM_CLS_*) and wall normals (float32 [3][N],
+ * zero away from fluid-boundary nodes) into caller device buffers. */
+lbm_status lbm_get_geometry(lbm_handle h, uint8_t *cls_dev, float *nw_dev,
+                            void *stream);
+
+/* Counts fixed at lbm_init_geometry: nodes, fluid nodes, solid-boundary
+ * nodes and fluid-boundary nodes. */
+lbm_status lbm_counts(lbm_handle h, int64_t *n_nodes, int64_t *n_fluid,
+                      int64_t *n_solid_bnd, int64_t *n_fluid_bnd);
+
+/* Message of the last failed call on this handle ("" if none). */
+const char *lbm_last_error(lbm_handle h);
+
+/* Release the handle (host memory only; the workspace stays the caller's). */
+void lbm_destroy(lbm_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBMGB_H */

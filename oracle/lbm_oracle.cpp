@@ -24,7 +24,7 @@
 //     order, with weights 4/9, 1/9, 1/36;
 //   * out-of-domain neighbours on a non-periodic axis: halfway bounce-back
 //     for streaming, coordinate clamping (zero gradient) for every stencil;
-//   * thresholds: |C| <= 1e-8 -> n_c = 0; Scheme-II leaves n_c unchanged
+//   * thresholds: |C| <= 1e-8 -> C = n_c = 0; Scheme-II leaves n_c unchanged
 //     when sin(theta') < 1e-6; the Scheme-I secant stops early when the two
 //     last residuals differ by less than 1e-12.
 //
@@ -403,7 +403,8 @@ struct Oracle {
   }
 
   // Eq. (6) with c = dt = 1, and Eq. (11)/(27): C = 3 sum_i w_i e_i
-  // phi(x + e_i), n_c = C/|C| (zero when |C| <= EPS_C).
+  // phi(x + e_i), n_c = C/|C|. Where |C| <= EPS_C the node holds no
+  // interface: C and n_c are set to zero (reading of the threshold).
   void colour_gradient() {
 #pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
@@ -415,7 +416,7 @@ struct Oracle {
       }
       double m = std::sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
       for (int a = 0; a < 3; ++a) {
-        C[a * N + n] = G[a];
+        C[a * N + n] = (m > EPS_C) ? G[a] : 0.0;
         nc[a * N + n] = (m > EPS_C) ? G[a] / m : 0.0;
       }
     }

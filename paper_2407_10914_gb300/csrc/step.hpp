@@ -1,0 +1,43 @@
+// Host-side entry points of the device passes (step, geometry, reductions).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "context.hpp"
+
+namespace lbm {
+
+// One time step: the five passes of step.cu on stream s. `macros` also
+// stores rho and u of this step.
+void launch_step(int Q, int storage, const Dom &d, cudaStream_t s,
+                 bool macros);
+
+// The same step with an event recorded before each pass and after the last
+// (ev[0..5]); passes that do not run (no solid-boundary nodes) record
+// back-to-back events.
+void launch_step_events(int Q, int storage, const Dom &d, cudaStream_t s,
+                        bool macros, cudaEvent_t *ev);
+
+// Geometry set-up (geometry.cu): classes, Eq. (25) smoothing, Eq. (26)
+// normals, the solid-boundary list and the counts.
+cudaError_t build_geometry(lbm_ctx *c, cudaStream_t s);
+
+// f^s_i = w_i rho^s at fluid nodes (zero elsewhere), phi and the macros of
+// the initial state (geometry.cu).
+void launch_init_state(int Q, int storage, const Dom &d, const float *phi0,
+                       cudaStream_t s);
+
+// Dense float32 export/import of the stored populations (geometry.cu).
+void launch_export_pops(int Q, int storage, const Dom &d, float *dst,
+                        cudaStream_t s);
+void launch_import_pops(int Q, int storage, const Dom &d, const float *src,
+                        cudaStream_t s);
+
+// Wall normals as float32 [3][N] (geometry.cu).
+void launch_export_nw(const Dom &d, float *out, cudaStream_t s);
+
+// FP64 reductions (reduce.cu): the result lands in *out_dev.
+void launch_reduce(int Q, int storage, const Dom &d, int kind, double *partials,
+                   int slots, double *out_dev, cudaStream_t s);
+
+}  // namespace lbm

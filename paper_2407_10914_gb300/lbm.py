@@ -1,0 +1,316 @@
+"""Python binding of the C-ABI in ``include/lbmgb.h`` (argument marshalling
+only; every step of the method runs in the CUDA library ``liblbmgb.so``).
+
+PyTorch provides the device memory (the workspace and every buffer passed to
+the library) and the stream (``torch.cuda.current_stream()``). The module
+fails loudly if the library is missing or no GPU is present: there is no
+CPU fallback.
+
+The functions ``lbm_*`` mirror the C names one to one; :class:`Session` is
+a convenience owner of one domain and its workspace.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbmgb.so")
+
+LBM_OK = 0
+STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA",
+          -3: "LBM_ERR_STATE", -4: "LBM_ERR_NONFINITE", -5: "LBM_ERR_TIMEOUT",
+          -6: "LBM_ERR_NOMEM"}
+STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
+(LBM_MASS_R, LBM_MASS_B, LBM_SW_COUNT, LBM_SW_SMOOTH, LBM_DP, LBM_CA_R,
+ LBM_CA_B) = range(7)
+EXPORTS = ("lbm_workspace_bytes", "lbm_init_geometry", "lbm_set_params",
+           "lbm_init_state", "lbm_step", "lbm_step_timed", "lbm_macros",
+           "lbm_reduce",
+           "lbm_get_populations", "lbm_set_populations", "lbm_get_geometry",
+           "lbm_counts", "lbm_last_error", "lbm_destroy")
+
+
+class LbmError(RuntimeError):
+    pass
+
+
+class lbm_params(C.Structure):
+    """Mirror of the C struct ``lbm_params``."""
+    _fields_ = [("tau_r", C.c_double), ("tau_b", C.c_double),
+                ("gamma", C.c_double), ("beta", C.c_double),
+                ("rho0", C.c_double), ("theta_deg", C.c_double),
+                ("wetting", C.c_int), ("zou_he", C.c_int),
+                ("flow_axis", C.c_int),
+                ("rho_in", C.c_double), ("rho_out", C.c_double),
+                ("zeta_r", C.c_double), ("g", C.c_double * 3)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load ``liblbmgb.so`` (no GPU needed to load it) and declare the
+    prototypes of every exported entry point."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise LbmError(f"CUDA library not built: {path} (run "
+                       "python -m paper_2407_10914_gb300.build)")
+    L = C.CDLL(path)
+    vp, sz, i64p = C.c_void_p, C.c_size_t, C.POINTER(C.c_int64)
+    L.lbm_workspace_bytes.restype = sz
+    L.lbm_workspace_bytes.argtypes = [C.c_int] * 4 + [vp, C.c_int]
+    L.lbm_init_geometry.restype = C.c_int
+    L.lbm_init_geometry.argtypes = [C.POINTER(vp)] + [C.c_int] * 4 + [
+        vp, C.c_uint, C.c_int, vp, sz, vp]
+    L.lbm_set_params.restype = C.c_int
+    L.lbm_set_params.argtypes = [vp, C.POINTER(lbm_params)]
+    L.lbm_init_state.restype = C.c_int
+    L.lbm_init_state.argtypes = [vp, vp, vp]
+    L.lbm_step.restype = C.c_int
+    L.lbm_step.argtypes = [vp, C.c_int, vp]
+    L.lbm_step_timed.restype = C.c_int
+    L.lbm_step_timed.argtypes = [vp, C.c_int, vp, C.POINTER(C.c_double)]
+    L.lbm_macros.restype = C.c_int
+    L.lbm_macros.argtypes = [vp, vp, vp, vp, vp]
+    L.lbm_reduce.restype = C.c_int
+    L.lbm_reduce.argtypes = [vp, C.c_int, C.POINTER(C.c_double), vp]
+    L.lbm_get_populations.restype = C.c_int
+    L.lbm_get_populations.argtypes = [vp, vp, vp]
+    L.lbm_set_populations.restype = C.c_int
+    L.lbm_set_populations.argtypes = [vp, vp, vp]
+    L.lbm_get_geometry.restype = C.c_int
+    L.lbm_get_geometry.argtypes = [vp, vp, vp, vp]
+    L.lbm_counts.restype = C.c_int
+    L.lbm_counts.argtypes = [vp, i64p, i64p, i64p, i64p]
+    L.lbm_last_error.restype = C.c_char_p
+    L.lbm_last_error.argtypes = [vp]
+    L.lbm_destroy.restype = None
+    L.lbm_destroy.argtypes = [vp]
+    _lib = L
+    return L
+
+
+def _check(st: int, h=None, what: str = ""):
+    if st != LBM_OK:
+        msg = ""
+        if h:
+            msg = load_library().lbm_last_error(h).decode()
+        raise LbmError(f"{what}: {STATUS.get(st, st)} {msg}")
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise LbmError("no CUDA device: the LBM step runs only on the GPU")
+    return torch
+
+
+def _stream(torch):
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(t) -> C.c_void_p:
+    return C.c_void_p(t.data_ptr())
+
+
+def make_params(**kw) -> lbm_params:
+    d = dict(tau_r=1.0, tau_b=1.0, gamma=0.01, beta=0.95, rho0=1.0,
+             theta_deg=90.0, wetting=0, zou_he=0, flow_axis=0, rho_in=1.0,
+             rho_out=1.0, zeta_r=1.0, g=(0.0, 0.0, 0.0))
+    for k in kw:
+        if k not in d:
+            raise KeyError(k)
+    d.update(kw)
+    return lbm_params(d["tau_r"], d["tau_b"], d["gamma"], d["beta"],
+                      d["rho0"], d["theta_deg"], int(d["wetting"]),
+                      int(d["zou_he"]), int(d["flow_axis"]), d["rho_in"],
+                      d["rho_out"], d["zeta_r"], (C.c_double * 3)(*d["g"]))
+
+
+# ------------------------------------------------ one-to-one C wrappers
+def lbm_workspace_bytes(lattice, nx, ny, nz, solid: Optional[np.ndarray],
+                        storage=0) -> int:
+    L = load_library()
+    sp = None if solid is None else solid.ctypes.data_as(C.c_void_p)
+    return int(L.lbm_workspace_bytes(lattice, nx, ny, nz, sp, storage))
+
+
+def lbm_init_geometry(lattice, nx, ny, nz, solid: np.ndarray, periodic_mask,
+                      storage, workspace, stream) -> C.c_void_p:
+    L = load_library()
+    h = C.c_void_p()
+    solid = np.ascontiguousarray(solid, np.uint8)
+    st = L.lbm_init_geometry(C.byref(h), lattice, nx, ny, nz,
+                             solid.ctypes.data_as(C.c_void_p), periodic_mask,
+                             storage, _dptr(workspace), workspace.numel(),
+                             stream)
+    _check(st, None, "lbm_init_geometry")
+    return h
+
+
+def lbm_set_params(h, p: lbm_params):
+    _check(load_library().lbm_set_params(h, C.byref(p)), h, "lbm_set_params")
+
+
+def lbm_init_state(h, phi0, stream):
+    _check(load_library().lbm_init_state(h, _dptr(phi0), stream), h,
+           "lbm_init_state")
+
+
+def lbm_step(h, nsteps, stream):
+    _check(load_library().lbm_step(h, int(nsteps), stream), h, "lbm_step")
+
+
+PASSES = ("phase", "phi_solid", "gradient", "nc_solid", "collide")
+
+
+def lbm_step_timed(h, nsteps, stream) -> dict:
+    ms = (C.c_double * 5)()
+    _check(load_library().lbm_step_timed(h, int(nsteps), stream, ms), h,
+           "lbm_step_timed")
+    return dict(zip(PASSES, ms[:]))
+
+
+def lbm_macros(h, rho, phi, u, stream):
+    p = [None if t is None else _dptr(t) for t in (rho, phi, u)]
+    _check(load_library().lbm_macros(h, *p, stream), h, "lbm_macros")
+
+
+def lbm_reduce(h, kind, stream) -> float:
+    out = C.c_double()
+    _check(load_library().lbm_reduce(h, int(kind), C.byref(out), stream), h,
+           "lbm_reduce")
+    return out.value
+
+
+def lbm_get_populations(h, dst, stream):
+    _check(load_library().lbm_get_populations(h, _dptr(dst), stream), h,
+           "lbm_get_populations")
+
+
+def lbm_set_populations(h, src, stream):
+    _check(load_library().lbm_set_populations(h, _dptr(src), stream), h,
+           "lbm_set_populations")
+
+
+def lbm_get_geometry(h, cls, nw, stream):
+    p = [None if t is None else _dptr(t) for t in (cls, nw)]
+    _check(load_library().lbm_get_geometry(h, *p, stream), h,
+           "lbm_get_geometry")
+
+
+def lbm_counts(h):
+    v = [C.c_int64() for _ in range(4)]
+    _check(load_library().lbm_counts(h, *[C.byref(x) for x in v]), h,
+           "lbm_counts")
+    return tuple(x.value for x in v)
+
+
+def lbm_destroy(h):
+    if h:
+        load_library().lbm_destroy(h)
+
+
+# ------------------------------------------------------------ Session
+class Session:
+    """One domain on the current CUDA device: the workspace (a torch uint8
+    tensor), the library handle and the helpers that move fields in and
+    out as torch tensors of shape (nz, ny, nx) (x fastest)."""
+
+    def __init__(self, lattice: int, solid: np.ndarray, periodic=(True,) * 3,
+                 storage: str = "fp32", device: str = "cuda"):
+        torch = _torch()
+        self.torch = torch
+        solid = np.ascontiguousarray(solid, np.uint8)
+        if solid.ndim == 2:
+            solid = solid[None]
+        self.q = lattice
+        self.shape = solid.shape
+        nz, ny, nx = self.shape
+        self.N = nx * ny * nz
+        self.storage = storage
+        self.device = torch.device(device)
+        mask = sum((1 << a) for a in range(3) if periodic[a])
+        ws = lbm_workspace_bytes(lattice, nx, ny, nz, solid, STORAGE[storage])
+        if ws == 0:
+            raise LbmError("bad domain")
+        self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
+        self.h = lbm_init_geometry(lattice, nx, ny, nz, solid, mask,
+                                   STORAGE[storage], self.workspace,
+                                   self.stream())
+        self.counts = lbm_counts(self.h)
+
+    def stream(self):
+        return _stream(self.torch)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            lbm_destroy(h)
+            self.h = None
+
+    @property
+    def n_fluid(self) -> int:
+        return int(self.counts[1])
+
+    def set_params(self, **kw):
+        lbm_set_params(self.h, make_params(**kw))
+
+    def init_state(self, phi0):
+        t = self.torch.as_tensor(np.asarray(phi0, np.float32).reshape(self.shape)
+                                 if isinstance(phi0, np.ndarray) else phi0)
+        t = t.to(self.device, self.torch.float32).contiguous()
+        lbm_init_state(self.h, t, self.stream())
+
+    def step(self, n: int = 1):
+        lbm_step(self.h, n, self.stream())
+
+    def step_timed(self, n: int = 1) -> dict:
+        """Per-pass milliseconds summed over n steps (CUDA events)."""
+        return lbm_step_timed(self.h, n, self.stream())
+
+    def macros(self):
+        t = self.torch
+        rho = t.empty(self.shape, dtype=t.float32, device=self.device)
+        phi = t.empty_like(rho)
+        u = t.empty((3,) + self.shape, dtype=t.float32, device=self.device)
+        lbm_macros(self.h, rho, phi, u, self.stream())
+        return dict(rho=rho, phi=phi, u=u)
+
+    def reduce(self, kind: int) -> float:
+        return lbm_reduce(self.h, kind, self.stream())
+
+    def get_populations(self):
+        t = self.torch
+        out = t.empty((2, self.q) + self.shape, dtype=t.float32,
+                      device=self.device)
+        lbm_get_populations(self.h, out, self.stream())
+        return out
+
+    def set_populations(self, f):
+        t = self.torch
+        src = t.as_tensor(f).to(self.device, t.float32).contiguous()
+        assert src.numel() == 2 * self.q * self.N
+        lbm_set_populations(self.h, src, self.stream())
+
+    def geometry(self):
+        t = self.torch
+        cls = t.empty(self.shape, dtype=t.uint8, device=self.device)
+        nw = t.empty((3,) + self.shape, dtype=t.float32, device=self.device)
+        lbm_get_geometry(self.h, cls, nw, self.stream())
+        return cls, nw
+
+
+def session_for(case, storage: str = "fp32") -> Session:
+    """A Session set up from a :class:`workloads.Case` (geometry, params,
+    initial state)."""
+    s = Session(case.lattice, case.solid, case.periodic, storage)
+    s.set_params(**case.params)
+    s.init_state(case.phi0.astype(np.float32))
+    return s

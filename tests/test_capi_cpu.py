@@ -1,0 +1,71 @@
+"""Host-side checks of the C-ABI library that need no GPU: it loads, it
+exports every function include/lbmgb.h declares, and argument errors are
+reported before any device work."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2407_10914_gb300 import build as B, lbm
+    B.build()
+    return lbm.load_library()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "lbmgb.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(lbm_[a-z_0-9]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declarations_are_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_binding_names_match_header():
+    from paper_2407_10914_gb300 import lbm
+    assert sorted(lbm.EXPORTS) == declared_functions()
+    for n in lbm.EXPORTS:
+        if n != "lbm_last_error":
+            assert callable(getattr(lbm, n))
+
+
+def test_workspace_bytes_host_only(lib):
+    from paper_2407_10914_gb300 import lbm
+    solid = np.zeros((4, 5, 6), np.uint8)
+    n19 = lbm.lbm_workspace_bytes(19, 6, 5, 4, solid, 0)
+    n19h = lbm.lbm_workspace_bytes(19, 6, 5, 4, solid, 1)
+    assert n19 > 2 * 2 * 19 * 120 * 4 and n19h < n19
+    assert lbm.lbm_workspace_bytes(7, 6, 5, 4, solid, 0) == 0
+    assert lbm.lbm_workspace_bytes(9, 6, 5, 2, solid, 0) == 0  # D2Q9 needs nz=1
+    assert lbm.lbm_workspace_bytes(19, 6, 5, 4, solid, 5) == 0
+
+
+def test_init_geometry_rejects_bad_arguments(lib):
+    h = C.c_void_p()
+    solid = np.zeros(8, np.uint8)
+    sp = solid.ctypes.data_as(C.c_void_p)
+    fake_ws = C.c_void_p(256)  # never touched: the checks come first
+    assert lib.lbm_init_geometry(C.byref(h), 7, 2, 2, 2, sp, 7, 0, fake_ws,
+                                 1 << 20, None) == -1
+    assert lib.lbm_init_geometry(C.byref(h), 19, 2, 2, 2, None, 7, 0,
+                                 fake_ws, 1 << 20, None) == -1
+    allsolid = np.ones(8, np.uint8)
+    assert lib.lbm_init_geometry(C.byref(h), 19, 2, 2, 2,
+                                 allsolid.ctypes.data_as(C.c_void_p), 7, 0,
+                                 fake_ws, 1 << 20, None) == -1
+    assert lib.lbm_init_geometry(C.byref(h), 19, 2, 2, 2, sp, 7, 0,
+                                 C.c_void_p(257), 1 << 20, None) == -1
+    assert lib.lbm_init_geometry(C.byref(h), 19, 2, 2, 2, sp, 7, 0, fake_ws,
+                                 16, None) == -6
+    assert not h.value
