@@ -34,37 +34,61 @@ lbm_status cuda_fail(lbm_ctx *c, cudaError_t e, const char *where) {
   return fail(c, LBM_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
-size_t pop_bytes(int Q, long long Np, int storage) {
-  return storage == LBM_STORAGE_FP32 ? (size_t)2 * Q * Np * sizeof(float)
-                                     : (size_t)Q * Np * 4;  // half2 pairs
+long long count_solid(const uint8_t *solid, long long N) {
+  if (!solid) return 0;
+  long long k = 0;
+  for (long long n = 0; n < N; ++n) k += solid[n] != 0;
+  return k;
 }
 
 // Byte offsets of every buffer inside the caller's workspace.
 struct Layout {
-  size_t fA, fB, phi, nc, cls, nw, sbnd, mask, rho, u, red, out, cnt, total;
+  size_t TA, TB, SA, SB, mf, ncf, nw, fg, macro;  // F-space
+  size_t ms, ncs, sg;                             // S-space
+  size_t map, cls, mask, fbase, sbase, cntf, cnts, g0, g1;
+  size_t red, out, cnt, total;
+  long long NF, NFp, NS, nseg;
 };
 
-Layout make_layout(int Q, long long N, long long Np, int storage,
-                   long long n_solid) {
+// NF is the number of fluid nodes; NS an upper bound of the solid-boundary
+// nodes (the number of solid nodes).
+Layout make_layout(int Q, int nx, int ny, int nz, int storage, long long NF,
+                   long long NS) {
   Layout L{};
+  const long long N = (long long)nx * ny * nz;
+  L.NF = NF;
+  L.NFp = pad64(NF > 0 ? NF : 1);
+  L.NS = NS;
+  L.nseg = (long long)((nx + lbm::SEG - 1) / lbm::SEG) * ny * nz;
   size_t o = 0;
   auto take = [&](size_t bytes) {
     size_t at = o;
-    o = align_up(o + bytes);
+    o = align_up(o + (bytes > 0 ? bytes : 1));
     return at;
   };
-  const size_t pb = pop_bytes(Q, Np, storage);
-  L.fA = take(pb);
-  // the smoothing ping-pong buffers (2 x 8N bytes, set-up only) live in fB
-  L.fB = take(pb > (size_t)16 * N ? pb : (size_t)16 * N);
-  L.phi = take((size_t)N * 4);
-  L.nc = take((size_t)N * 16);
+  const size_t tb = (size_t)Q * L.NFp * (storage == LBM_STORAGE_FP32 ? 4 : 2);
+  const size_t nfp = (size_t)L.NFp, nsp = (size_t)pad64(NS > 0 ? NS : 1);
+  L.TA = take(tb);
+  L.TB = take(tb);
+  L.SA = take(nfp * 16);
+  L.SB = take(nfp * 16);
+  L.mf = take(nfp * 4);
+  L.ncf = take(nfp * 16);
+  L.nw = take(nfp * 16);
+  L.fg = take(nfp * 4);
+  L.macro = take(nfp * 16);
+  L.ms = take(nsp * 4);
+  L.ncs = take(nsp * 16);
+  L.sg = take(nsp * 4);
+  L.map = take((size_t)N * 2);
   L.cls = take((size_t)N);
-  L.nw = take((size_t)N * 16);
-  L.sbnd = take((size_t)(n_solid > 0 ? n_solid : 1) * 4);
   L.mask = take((size_t)N);
-  L.rho = take((size_t)N * 4);
-  L.u = take((size_t)N * 12);
+  L.fbase = take((size_t)(L.nseg + 1) * 4);
+  L.sbase = take((size_t)(L.nseg + 1) * 4);
+  L.cntf = take((size_t)L.nseg * 4);
+  L.cnts = take((size_t)L.nseg * 4);
+  L.g0 = take((size_t)N * 8);
+  L.g1 = take((size_t)N * 8);
   L.red = take((size_t)RED_SLOTS * 4 * 8);
   L.out = take(4 * 8);
   L.cnt = take(4 * 8);
@@ -77,14 +101,16 @@ bool valid_shape(int lattice, int nx, int ny, int nz) {
   if (nx < 1 || ny < 1 || nz < 1) return false;
   if (lattice == 9 && nz != 1) return false;
   const long long N = (long long)nx * ny * nz;
-  return N < (1LL << 31);  // node indices are stored as int32 in lists
+  return N < (1LL << 31);  // box indices are stored as int32
 }
 
-long long count_solid(const uint8_t *solid, long long N) {
-  if (!solid) return N;
-  long long k = 0;
-  for (long long n = 0; n < N; ++n) k += solid[n] != 0;
-  return k;
+void swap_buffers(lbm_ctx *c) {
+  const void *t = c->d.T_src;
+  c->d.T_src = c->d.T_dst;
+  c->d.T_dst = const_cast<void *>(t);
+  const float4 *u = c->d.S_src;
+  c->d.S_src = c->d.S_dst;
+  c->d.S_dst = const_cast<float4 *>(u);
 }
 
 }  // namespace
@@ -96,8 +122,9 @@ size_t lbm_workspace_bytes(int lattice, int nx, int ny, int nz,
   if (!valid_shape(lattice, nx, ny, nz)) return 0;
   if (storage < 0 || storage > 2) return 0;
   const long long N = (long long)nx * ny * nz;
-  return make_layout(lattice, N, pad64(N), storage,
-                     count_solid(solid_host, N)).total;
+  const long long ns = solid_host ? count_solid(solid_host, N) : N;
+  const long long nf = solid_host ? N - ns : N;
+  return make_layout(lattice, nx, ny, nz, storage, nf, ns).total;
 }
 
 lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
@@ -111,10 +138,10 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
     return LBM_ERR_ARG;
   if (((uintptr_t)ws) % ALIGN) return LBM_ERR_ARG;
   const long long N = (long long)nx * ny * nz;
-  const long long Np = pad64(N);
   const long long n_solid = count_solid(solid_host, N);
   if (n_solid == N) return LBM_ERR_ARG;  // no fluid node
-  const Layout L = make_layout(lattice, N, Np, storage, n_solid);
+  const Layout L = make_layout(lattice, nx, ny, nz, storage, N - n_solid,
+                               n_solid);
   if (ws_bytes < L.total) return LBM_ERR_NOMEM;
   lbm_ctx *c = new (std::nothrow) lbm_ctx();
   if (!c) return LBM_ERR_NOMEM;
@@ -125,14 +152,18 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
   c->ny = ny;
   c->nz = nz;
   c->N = N;
-  c->Np = Np;
   c->periodic = periodic_mask;
   c->storage = storage;
-  c->fA = base + L.fA;
-  c->fB = base + L.fB;
+  c->nseg = L.nseg;
+  c->TA = base + L.TA;
+  c->TB = base + L.TB;
+  c->SA = (float4 *)(base + L.SA);
+  c->SB = (float4 *)(base + L.SB);
   c->mask = (uint8_t *)(base + L.mask);
-  c->g0 = (double *)(base + L.fB);
-  c->g1 = (double *)(base + L.fB) + N;
+  c->g0 = (double *)(base + L.g0);
+  c->g1 = (double *)(base + L.g1);
+  c->cnt_f = (int *)(base + L.cntf);
+  c->cnt_s = (int *)(base + L.cnts);
   c->red = (double *)(base + L.red);
   c->red_slots = RED_SLOTS;
   c->red_out = (double *)(base + L.out);
@@ -142,18 +173,27 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
   d.ny = ny;
   d.nz = nz;
   d.N = N;
-  d.Np = Np;
   d.periodic = periodic_mask;
-  d.f_src = c->fA;
-  d.f_dst = c->fB;
-  d.phi = (float *)(base + L.phi);
-  d.nc = (float4 *)(base + L.nc);
+  d.spr = (nx + lbm::SEG - 1) / lbm::SEG;
+  d.NF = (int)L.NF;
+  d.NS = (int)L.NS;  // upper bound until the lists are built
+  d.NFp = L.NFp;
+  d.map = (const uint16_t *)(base + L.map);
+  d.fbase = (const int *)(base + L.fbase);
+  d.sbase = (const int *)(base + L.sbase);
+  d.fg = (const int *)(base + L.fg);
+  d.sg = (const int *)(base + L.sg);
   d.cls = (const uint8_t *)(base + L.cls);
   d.nw = (const float4 *)(base + L.nw);
-  d.sbnd = (const int *)(base + L.sbnd);
-  d.n_sbnd = 0;
-  d.rho_m = (float *)(base + L.rho);
-  d.u_m = (float *)(base + L.u);
+  d.T_src = c->TA;
+  d.T_dst = c->TB;
+  d.S_src = c->SA;
+  d.S_dst = c->SB;
+  d.mf = (float *)(base + L.mf);
+  d.ms = (float *)(base + L.ms);
+  d.ncf = (float4 *)(base + L.ncf);
+  d.ncs = (float4 *)(base + L.ncs);
+  d.macro = (float4 *)(base + L.macro);
   cudaError_t e = cudaMemcpyAsync(c->mask, solid_host, (size_t)N,
                                   cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = lbm::build_geometry(c, s);
@@ -201,7 +241,6 @@ lbm_status lbm_set_params(lbm_handle c, const lbm_params *p) {
   k.beta = (float)p->beta;
   k.rho0 = (float)p->rho0;
   const double th = p->theta_deg * 3.14159265358979323846 / 180.0;
-  k.theta = (float)th;
   k.cos_t = (float)std::cos(th);
   k.sin_t = (float)std::sin(th);
   k.wetting = p->wetting;
@@ -210,7 +249,11 @@ lbm_status lbm_set_params(lbm_handle c, const lbm_params *p) {
   k.rho_in_r = (float)(p->rho_in * p->zeta_r);
   k.rho_in_b = (float)(p->rho_in * (1.0 - p->zeta_r));
   k.rho_out = (float)p->rho_out;
-  k.phi_in = (float)(p->zeta_r - (1.0 - p->zeta_r));
+  {
+    const double phi_in = p->zeta_r - (1.0 - p->zeta_r);
+    const double mu = 0.5 * (1.0 - std::fabs(phi_in));
+    k.m_in = (float)std::copysign(mu, phi_in < 0.0 ? -1.0 : 1.0);
+  }
   for (int a = 0; a < 3; ++a) k.g[a] = (float)p->g[a];
   c->params_set = true;
   return LBM_OK;
@@ -232,9 +275,7 @@ lbm_status lbm_step(lbm_handle c, int nsteps, void *stream) {
   cudaStream_t s = (cudaStream_t)stream;
   for (int k = 0; k < nsteps; ++k) {
     lbm::launch_step(c->Q, c->storage, c->d, s, k == nsteps - 1);
-    void *t = c->d.f_src;
-    c->d.f_src = c->d.f_dst;
-    c->d.f_dst = t;
+    swap_buffers(c);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "step");
@@ -256,9 +297,7 @@ lbm_status lbm_step_timed(lbm_handle c, int nsteps, void *stream,
   }
   for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
     lbm::launch_step_events(c->Q, c->storage, c->d, s, k == nsteps - 1, ev);
-    void *t = c->d.f_src;
-    c->d.f_src = c->d.f_dst;
-    c->d.f_dst = t;
+    swap_buffers(c);
     e = cudaEventSynchronize(ev[5]);
     for (int p = 0; p < 5 && e == cudaSuccess; ++p) {
       float ms = 0.f;
@@ -276,15 +315,8 @@ lbm_status lbm_macros(lbm_handle c, float *rho, float *phi, float *u,
                       void *stream) {
   if (!c) return LBM_ERR_ARG;
   if (!c->state_set) return fail(c, LBM_ERR_STATE, "init the state first");
-  cudaStream_t s = (cudaStream_t)stream;
-  const size_t b = (size_t)c->N * sizeof(float);
-  cudaError_t e = cudaSuccess;
-  if (rho && e == cudaSuccess)
-    e = cudaMemcpyAsync(rho, c->d.rho_m, b, cudaMemcpyDeviceToDevice, s);
-  if (phi && e == cudaSuccess)
-    e = cudaMemcpyAsync(phi, c->d.phi, b, cudaMemcpyDeviceToDevice, s);
-  if (u && e == cudaSuccess)
-    e = cudaMemcpyAsync(u, c->d.u_m, 3 * b, cudaMemcpyDeviceToDevice, s);
+  lbm::launch_export_macros(c->d, rho, phi, u, (cudaStream_t)stream);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "macros");
   return LBM_OK;
 }
@@ -327,6 +359,7 @@ lbm_status lbm_reduce(lbm_handle c, int kind, double *out, void *stream) {
 
 lbm_status lbm_get_populations(lbm_handle c, float *dst, void *stream) {
   if (!c || !dst) return LBM_ERR_ARG;
+  if (!c->state_set) return fail(c, LBM_ERR_STATE, "init the state first");
   lbm::launch_export_pops(c->Q, c->storage, c->d, dst, (cudaStream_t)stream);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "get_populations");

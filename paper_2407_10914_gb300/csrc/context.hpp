@@ -1,5 +1,21 @@
 // Internal state of one domain and the kernel-argument block shared by the
 // step, geometry and reduction translation units.
+//
+// Memory layout (all inside the caller's workspace):
+//  * the box is cut into segments of SEG = 256 nodes along x; a uint16 map
+//    over the box holds, per node, its class (bits 8-9) and its rank among
+//    the nodes of the same kind (fluid, or solid-boundary) in its segment
+//    (bits 0-7); per-segment bases turn (segment, rank) into an index of
+//    the compact fluid list ("F-space") or solid-boundary list ("S-space");
+//  * populations live in F-space only, in the post-recolouring form that
+//    Eqs. (20)-(21) give them: f''_i = f^r'_i + f^b'_i per direction (Q
+//    planes) plus one float4 per node (q, v): q the signed minority colour
+//    fraction (see phase encoding below) and v = beta rho^r rho^b / rho n,
+//    from which f^r'_i and f^b'_i are rebuilt exactly;
+//  * the phase field is stored "encoded": m = +min(rho^r,rho^b)/rho where
+//    phi >= 0 and -min(rho^r,rho^b)/rho (signed zero included) where phi < 0,
+//    so that phi - sign(phi) keeps full float32 relative accuracy near the
+//    pure phases (the colour gradient of Eq. 6 is built from it).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -8,6 +24,8 @@
 #include "../../include/lbmgb.h"
 
 namespace lbm {
+
+constexpr int SEG = 256;
 
 enum : uint8_t {
   CLS_SOLID = LBM_CLS_SOLID,
@@ -18,33 +36,39 @@ enum : uint8_t {
 
 // Constants of the step as the kernels use them (float, precomputed).
 struct StepConst {
-  float nu_r, nu_b;        // kinematic viscosities
+  float nu_r, nu_b;  // kinematic viscosities
   float gamma, beta, rho0;
-  float cos_t, sin_t, theta;
+  float cos_t, sin_t;
   int wetting, zou_he, axis;
   float rho_in_r, rho_in_b, rho_out;  // rho_in zeta^s, rho_out
-  float phi_in;                       // zeta^r - zeta^b
+  float m_in;                          // encoded inlet phase field
   float g[3];
 };
 
 // Everything a kernel needs, passed by value.
 struct Dom {
   int nx, ny, nz;
-  long long N;         // nodes
-  long long Np;        // padded stride of one population plane
+  long long N;      // nodes of the box
   unsigned periodic;
-  // populations: fp32 [2][Q][Np] or, for 16-bit storage, two planes of
-  // [Q][Np] 16-bit values (T, D)
-  void *f_src;
-  void *f_dst;
-  float *phi;          // [N]
-  float4 *nc;          // [N] (n_c, |C|); at solid-boundary nodes (Eq. 35, 0)
-  const uint8_t *cls;  // [N]
-  const float4 *nw;    // [N] wall normal at fluid-boundary nodes
-  const int *sbnd;     // solid-boundary node list
-  int n_sbnd;
-  float *rho_m;        // [N] macros of the last step
-  float *u_m;          // [3][N]
+  int spr;          // segments per x-row
+  int NF, NS;       // fluid nodes, solid-boundary nodes
+  long long NFp;    // stride of one population plane (NF rounded up)
+  const uint16_t *map;  // [N]
+  const int *fbase;     // [nseg + 1]
+  const int *sbase;     // [nseg + 1]
+  const int *fg;        // [NF] box index of fluid node k
+  const int *sg;        // [NS] box index of solid-boundary node j
+  const uint8_t *cls;   // [N]
+  const float4 *nw;     // [NF] wall normal (fluid-boundary nodes), else 0
+  const void *T_src;    // [Q][NFp] f'' (float32, or 16-bit offsets)
+  void *T_dst;
+  const float4 *S_src;  // [NF] (q, v)
+  float4 *S_dst;
+  float *mf;            // [NF] encoded phase field
+  float *ms;            // [NS] encoded phase field (Eq. 34)
+  float4 *ncf;          // [NF] (n_c, |C|)
+  float4 *ncs;          // [NS] (n_c of Eq. 35, 0)
+  float4 *macro;        // [NF] (u_x, u_y, u_z, rho) of the last macro step
   StepConst c;
 };
 
@@ -53,20 +77,23 @@ struct Dom {
 struct lbm_ctx {
   int Q = 0;
   int nx = 0, ny = 0, nz = 0;
-  long long N = 0, Np = 0;
+  long long N = 0;
   unsigned periodic = 0;
   int storage = 0;
+  long long nseg = 0;
   long long n_fluid = 0, n_sbnd = 0, n_fbnd = 0;
   bool params_set = false;
   bool state_set = false;
   lbm_params p{};
   lbm::Dom d{};
-  void *fA = nullptr, *fB = nullptr;  // population buffers (current = fA)
-  uint8_t *mask = nullptr;            // device copy of the solid image
-  double *g0 = nullptr, *g1 = nullptr;  // smoothing ping-pong (init only)
-  double *red = nullptr;              // reduction partials
-  double *red_out = nullptr;          // 4 doubles: the combined partials
+  void *TA = nullptr, *TB = nullptr;      // population planes (current = A)
+  float4 *SA = nullptr, *SB = nullptr;
+  uint8_t *mask = nullptr;                // device copy of the solid image
+  double *g0 = nullptr, *g1 = nullptr;    // smoothing ping-pong (set-up)
+  int *cnt_f = nullptr, *cnt_s = nullptr; // per-segment counts (set-up)
+  double *red = nullptr;                  // reduction partials
+  double *red_out = nullptr;              // 4 doubles: the combined partials
   int red_slots = 0;
-  unsigned long long *counters = nullptr;  // device counters
+  unsigned long long *counters = nullptr;
   char err[256] = {0};
 };

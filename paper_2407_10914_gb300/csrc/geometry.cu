@@ -1,6 +1,7 @@
-// Set-up passes: node classes, the smoothing of Eq. (25), the wall normal of
-// Eq. (26), the solid-boundary list; the initial state; dense population
-// export/import. These run once (or on request), not in the time loop.
+// Set-up passes: node classes; the compact fluid (F) and solid-boundary (S)
+// lists with the per-segment map; the smoothing of Eq. (25) and the wall
+// normal of Eq. (26); the initial state; dense export/import of the state and
+// fields. These run once or on request, not in the time loop.
 #include <cuda_runtime.h>
 
 #include "stencil.cuh"
@@ -20,22 +21,117 @@ static inline unsigned gblocks(long long n) {
 template <int Q>
 __global__ void k_classify(Dom d, const uint8_t *__restrict__ mask,
                            uint8_t *__restrict__ cls) {
-  const long long n = (long long)blockIdx.x * GBLOCK + threadIdx.x;
-  if (n >= d.N) return;
+  const long long g = (long long)blockIdx.x * GBLOCK + threadIdx.x;
+  if (g >= d.N) return;
   int x, y, z;
-  node_coords(d, n, x, y, z);
-  const bool solid = mask[n] != 0;
+  box_coords(d, g, x, y, z);
+  const bool solid = mask[g] != 0;
   bool bnd = false;
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     bool out = false;
-    const long long m = nb_index(d, x, y, z, Lattice<Q>::e(i, 0),
-                                 Lattice<Q>::e(i, 1), Lattice<Q>::e(i, 2),
-                                 false, out);
-    if (!out && ((mask[m] != 0) != solid)) bnd = true;
+    const int X = axis_step(x + Lattice<Q>::ex(i), d.nx, d.periodic & 1u, false, out);
+    const int Y = axis_step(y + Lattice<Q>::ey(i), d.ny, d.periodic & 2u, false, out);
+    const int Z = axis_step(z + Lattice<Q>::ez(i), d.nz, d.periodic & 4u, false, out);
+    if (out) continue;
+    const long long m = X + (long long)d.nx * (Y + (long long)d.ny * Z);
+    if ((mask[m] != 0) != solid) bnd = true;
   }
-  cls[n] = solid ? (bnd ? CLS_SOLID_BND : CLS_SOLID)
+  cls[g] = solid ? (bnd ? CLS_SOLID_BND : CLS_SOLID)
                  : (bnd ? CLS_FLUID_BND : CLS_FLUID);
+}
+
+// One block per segment (SEG = GBLOCK nodes along x): fluid and
+// solid-boundary counts.
+__global__ void k_seg_count(Dom d, int *__restrict__ cf, int *__restrict__ cs) {
+  const long long seg = blockIdx.x;
+  const long long row = seg / d.spr;
+  const int x = (int)(seg - row * d.spr) * SEG + threadIdx.x;
+  int c = CLS_SOLID;
+  if (x < d.nx) c = d.cls[x + (long long)d.nx * row];
+  const int nf = __syncthreads_count(c & 2);
+  const int ns = __syncthreads_count(c == CLS_SOLID_BND);
+  if (threadIdx.x == 0) {
+    cf[seg] = nf;
+    cs[seg] = ns;
+  }
+}
+
+// Exclusive prefix sum of n counts into base[0..n] (base[n] = total), one
+// block of 1024 threads walking the array in chunks of 1024.
+__global__ void k_scan(const int *__restrict__ cnt, long long n,
+                       int *__restrict__ base) {
+  __shared__ int warp_tot[32];
+  __shared__ int carry;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (long long off = 0; off < n; off += 1024) {
+    const long long i = off + threadIdx.x;
+    const int v = i < n ? cnt[i] : 0;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += t;
+    }
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+      int t = warp_tot[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += u;
+      }
+      warp_tot[lane] = t;  // inclusive over warps
+    }
+    __syncthreads();
+    const int before = (warp > 0 ? warp_tot[warp - 1] : 0) + carry;
+    if (i < n) base[i] = before + inc - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = before + inc;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) base[n] = carry;
+}
+
+// One block per segment: rank of each node among the nodes of its kind in
+// the segment; map = (class << 8) | rank; the F and S lists hold box indices.
+__global__ void k_build_map(Dom d, uint16_t *__restrict__ map,
+                            int *__restrict__ fg, int *__restrict__ sg) {
+  __shared__ int wf[GBLOCK / 32], ws[GBLOCK / 32];
+  const long long seg = blockIdx.x;
+  const long long row = seg / d.spr;
+  const int x = (int)(seg - row * d.spr) * SEG + threadIdx.x;
+  const long long g = x + (long long)d.nx * row;
+  const bool valid = x < d.nx;
+  const int c = valid ? d.cls[g] : CLS_SOLID;
+  const bool isf = valid && (c & 2), iss = valid && c == CLS_SOLID_BND;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned bf = __ballot_sync(0xffffffffu, isf);
+  const unsigned bs = __ballot_sync(0xffffffffu, iss);
+  const unsigned lt = (1u << lane) - 1u;
+  if (lane == 0) {
+    wf[warp] = __popc(bf);
+    ws[warp] = __popc(bs);
+  }
+  __syncthreads();
+  int of = 0, os = 0;
+  for (int w = 0; w < warp; ++w) {
+    of += wf[w];
+    os += ws[w];
+  }
+  if (!valid) return;
+  int rank = 0;
+  if (isf) {
+    rank = of + __popc(bf & lt);
+    fg[d.fbase[seg] + rank] = (int)g;
+  } else if (iss) {
+    rank = os + __popc(bs & lt);
+    sg[d.sbase[seg] + rank] = (int)g;
+  }
+  map[g] = (uint16_t)((c << 8) | rank);
 }
 
 __global__ void k_indicator(long long N, const uint8_t *__restrict__ mask,
@@ -53,7 +149,7 @@ __global__ void k_smooth(Dom d, const double *__restrict__ gin,
   const long long n = (long long)blockIdx.x * GBLOCK + threadIdx.x;
   if (n >= d.N) return;
   int x, y, z;
-  node_coords(d, n, x, y, z);
+  box_coords(d, n, x, y, z);
   const double w3[4] = {8.0 / 27.0, 2.0 / 27.0, 1.0 / 54.0, 1.0 / 216.0};
   const double w2[3] = {4.0 / 9.0, 1.0 / 9.0, 1.0 / 36.0};
   constexpr int KR = DIM == 3 ? 1 : 0;
@@ -65,181 +161,212 @@ __global__ void k_smooth(Dom d, const double *__restrict__ gin,
 #pragma unroll
       for (int i = -1; i <= 1; ++i) {
         bool out = false;
-        const long long m = nb_index(d, x, y, z, i, j, k, true, out);
+        const int X = axis_step(x + i, d.nx, d.periodic & 1u, true, out);
+        const int Y = axis_step(y + j, d.ny, d.periodic & 2u, true, out);
+        const int Z = axis_step(z + k, d.nz, d.periodic & 4u, true, out);
         const int r2 = i * i + j * j + k * k;
-        acc += (DIM == 3 ? w3[r2] : w2[r2]) * gin[m];
+        acc += (DIM == 3 ? w3[r2] : w2[r2]) *
+               gin[X + (long long)d.nx * (Y + (long long)d.ny * Z)];
       }
   gout[n] = acc;
 }
 
 // Eq. (26): n_w = grad g^(3) by the Eq. (6) stencil, normalised, at
-// fluid-boundary nodes; zero elsewhere (and where the gradient vanishes).
+// fluid-boundary nodes (F-space); zero elsewhere and where it vanishes.
 template <int Q>
-__global__ void k_wall_normal(Dom d, const double *__restrict__ g,
+__global__ void k_wall_normal(Dom d, const double *__restrict__ g3,
                               float4 *__restrict__ nw) {
-  const long long n = (long long)blockIdx.x * GBLOCK + threadIdx.x;
-  if (n >= d.N) return;
+  const int k = blockIdx.x * GBLOCK + threadIdx.x;
+  if (k >= d.NF) return;
+  const long long g = d.fg[k];
   float4 out4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (d.cls[n] == CLS_FLUID_BND) {
+  if (d.cls[g] == CLS_FLUID_BND) {
     int x, y, z;
-    node_coords(d, n, x, y, z);
+    box_coords(d, g, x, y, z);
     double G[3] = {0.0, 0.0, 0.0};
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       bool out = false;
-      const long long m = nb_index(d, x, y, z, Lattice<Q>::e(i, 0),
-                                   Lattice<Q>::e(i, 1), Lattice<Q>::e(i, 2),
-                                   true, out);
-      const double p = 3.0 * Lattice<Q>::wd(i) * g[m];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) G[a] += Lattice<Q>::e(i, a) * p;
+      const int X = axis_step(x + Lattice<Q>::ex(i), d.nx, d.periodic & 1u, true, out);
+      const int Y = axis_step(y + Lattice<Q>::ey(i), d.ny, d.periodic & 2u, true, out);
+      const int Z = axis_step(z + Lattice<Q>::ez(i), d.nz, d.periodic & 4u, true, out);
+      const double p = 3.0 * Lattice<Q>::wd(i) *
+                       g3[X + (long long)d.nx * (Y + (long long)d.ny * Z)];
+      G[0] += Lattice<Q>::ex(i) * p;
+      G[1] += Lattice<Q>::ey(i) * p;
+      G[2] += Lattice<Q>::ez(i) * p;
     }
     const double mag = sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
     if (mag > 1e-12)
       out4 = make_float4((float)(G[0] / mag), (float)(G[1] / mag),
                          (float)(G[2] / mag), 0.f);
   }
-  nw[n] = out4;
+  nw[k] = out4;
 }
 
-// Compact list of solid-boundary nodes and the counts (fluid, solid-bnd,
-// fluid-bnd) in counters[0..2]. The list order is irrelevant to the results.
-__global__ void k_lists(Dom d, int *__restrict__ sbnd,
-                        unsigned long long *__restrict__ counters) {
-  const long long n = (long long)blockIdx.x * GBLOCK + threadIdx.x;
-  if (n >= d.N) return;
-  const uint8_t c = d.cls[n];
-  if (c & 2) atomicAdd(&counters[0], 1ull);
-  if (c == CLS_FLUID_BND) atomicAdd(&counters[2], 1ull);
-  if (c == CLS_SOLID_BND) {
-    const unsigned long long k = atomicAdd(&counters[1], 1ull);
-    sbnd[k] = (int)n;
-  }
+__global__ void k_count_fbnd(Dom d, unsigned long long *__restrict__ c) {
+  const int k = blockIdx.x * GBLOCK + threadIdx.x;
+  const bool b = k < d.NF && d.cls[d.fg[k]] == CLS_FLUID_BND;
+  const int n = __syncthreads_count(b);
+  if (threadIdx.x == 0 && n) atomicAdd(c, (unsigned long long)n);
 }
 
 cudaError_t build_geometry(lbm_ctx *c, cudaStream_t s) {
   Dom &d = c->d;
-  const unsigned g = gblocks(d.N);
+  const unsigned gN = gblocks(d.N);
   uint8_t *cls = const_cast<uint8_t *>(d.cls);
   if (c->Q == 19)
-    k_classify<19><<<g, GBLOCK, 0, s>>>(d, c->mask, cls);
+    k_classify<19><<<gN, GBLOCK, 0, s>>>(d, c->mask, cls);
   else
-    k_classify<9><<<g, GBLOCK, 0, s>>>(d, c->mask, cls);
-  k_indicator<<<g, GBLOCK, 0, s>>>(d.N, c->mask, c->g0);
+    k_classify<9><<<gN, GBLOCK, 0, s>>>(d, c->mask, cls);
+  k_seg_count<<<(unsigned)c->nseg, GBLOCK, 0, s>>>(d, c->cnt_f, c->cnt_s);
+  k_scan<<<1, 1024, 0, s>>>(c->cnt_f, c->nseg, const_cast<int *>(d.fbase));
+  k_scan<<<1, 1024, 0, s>>>(c->cnt_s, c->nseg, const_cast<int *>(d.sbase));
+  k_build_map<<<(unsigned)c->nseg, GBLOCK, 0, s>>>(
+      d, const_cast<uint16_t *>(d.map), const_cast<int *>(d.fg),
+      const_cast<int *>(d.sg));
+  int tot[2] = {0, 0};
+  cudaError_t e = cudaMemcpyAsync(&tot[0], d.fbase + c->nseg, sizeof(int),
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&tot[1], d.sbase + c->nseg, sizeof(int),
+                        cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e;
+  if (tot[0] != d.NF || tot[1] > d.NS) return cudaErrorInvalidValue;
+  d.NS = tot[1];
+  c->n_fluid = tot[0];
+  c->n_sbnd = tot[1];
+  // Eq. (25) three times, then Eq. (26) at the fluid-boundary nodes
+  k_indicator<<<gN, GBLOCK, 0, s>>>(d.N, c->mask, c->g0);
   double *gi = c->g0, *go = c->g1;
   for (int itr = 0; itr < 3; ++itr) {
     if (c->Q == 19)
-      k_smooth<3><<<g, GBLOCK, 0, s>>>(d, gi, go);
+      k_smooth<3><<<gN, GBLOCK, 0, s>>>(d, gi, go);
     else
-      k_smooth<2><<<g, GBLOCK, 0, s>>>(d, gi, go);
+      k_smooth<2><<<gN, GBLOCK, 0, s>>>(d, gi, go);
     double *t = gi;
     gi = go;
     go = t;
   }
+  const unsigned gF = gblocks(d.NF);
   float4 *nw = const_cast<float4 *>(d.nw);
   if (c->Q == 19)
-    k_wall_normal<19><<<g, GBLOCK, 0, s>>>(d, gi, nw);
+    k_wall_normal<19><<<gF, GBLOCK, 0, s>>>(d, gi, nw);
   else
-    k_wall_normal<9><<<g, GBLOCK, 0, s>>>(d, gi, nw);
-  cudaError_t e = cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), s);
+    k_wall_normal<9><<<gF, GBLOCK, 0, s>>>(d, gi, nw);
+  e = cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  k_lists<<<g, GBLOCK, 0, s>>>(d, const_cast<int *>(d.sbnd), c->counters);
-  unsigned long long h[4] = {0, 0, 0, 0};
-  e = cudaMemcpyAsync(h, c->counters, sizeof(h), cudaMemcpyDeviceToHost, s);
+  k_count_fbnd<<<gF, GBLOCK, 0, s>>>(d, c->counters);
+  unsigned long long nfb = 0;
+  e = cudaMemcpyAsync(&nfb, c->counters, sizeof(nfb), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;
-  e = cudaStreamSynchronize(s);
-  if (e != cudaSuccess) return e;
-  c->n_fluid = (long long)h[0];
-  c->n_sbnd = (long long)h[1];
-  c->n_fbnd = (long long)h[2];
-  d.n_sbnd = (int)h[1];
+  c->n_fbnd = (long long)nfb;
   return cudaGetLastError();
 }
 
 // ------------------------------------------------------------ state I/O
+// Fluid at rest: f^s_i = w_i rho^s, i.e. f''_i = w_i rho0, q from phi0, v = 0.
 template <int Q, int ST>
 __global__ void k_init_state(Dom d, const float *__restrict__ phi0) {
-  const long long n = (long long)blockIdx.x * GBLOCK + threadIdx.x;
-  if (n >= d.N) return;
-  const PopIO<Q, ST> io(d);
-  const bool fluid = is_fluid_cls(d.cls[n]);
-  float r = 0.f, b = 0.f;
-  if (fluid) {
-    const float p = phi0[n];
-    r = d.c.rho0 * 0.5f * (1.f + p);
-    b = d.c.rho0 * 0.5f * (1.f - p);
-  }
+  const int k = blockIdx.x * GBLOCK + threadIdx.x;
+  if (k < d.NF) {
+    const float p = phi0[d.fg[k]];
+    const float m = m_encode(p < 0.f, 0.5f * (1.f - fabsf(p)));
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const float w = Lattice<Q>::w(i);
-    if (fluid)
-      io.store(i, n, w * r, w * b);
-    else
-      io.store(i, n, 0.f, 0.f);
+    for (int i = 0; i < Q; ++i)
+      TIO<Q, ST>::store(d, d.T_dst, i, k, Lattice<Q>::w(i) * d.c.rho0);
+    d.S_dst[k] = make_float4(m, 0.f, 0.f, 0.f);
+    d.mf[k] = m;
+    d.ncf[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    d.macro[k] = make_float4(0.f, 0.f, 0.f, d.c.rho0);
   }
-  d.phi[n] = fluid ? (r - b) / (r + b) : 0.f;
-  d.nc[n] = make_float4(0.f, 0.f, 0.f, 0.f);
-  d.rho_m[n] = fluid ? r + b : 0.f;
-  d.u_m[n] = 0.f;
-  d.u_m[d.N + n] = 0.f;
-  d.u_m[2 * d.N + n] = 0.f;
+  if (k < d.NS) {
+    d.ms[k] = 0.5f;  // phi = 0 until the first step fills Eq. (34)
+    d.ncs[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
 }
 
 template <int Q, int ST>
 __global__ void k_export(Dom d, float *__restrict__ dst) {
-  const long long n = (long long)blockIdx.x * GBLOCK + threadIdx.x;
-  if (n >= d.N) return;
-  const PopIO<Q, ST> io(d);
-  const bool fluid = is_fluid_cls(d.cls[n]);
+  const int k = blockIdx.x * GBLOCK + threadIdx.x;
+  if (k >= d.NF) return;
+  const long long g = d.fg[k];
+  const float4 S = d.S_src[k];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    float r = 0.f, b = 0.f;
-    if (fluid) io.load(i, n, r, b);
-    dst[(long long)i * d.N + n] = r;
-    dst[(long long)(Q + i) * d.N + n] = b;
+    float r, b;
+    rebuild<Q>(TIO<Q, ST>::load(d, i, k), S, i, r, b);
+    dst[(long long)i * d.N + g] = r;
+    dst[(long long)(Q + i) * d.N + g] = b;
   }
+}
+
+// Import of arbitrary f^r, f^b: f''_i = f^r_i + f^b_i, q from the colour
+// densities, v from the minority colour's momentum (sum_i w_i e_i e_i = I/3):
+// v = 3 (sum_i e_i f^r_i - mu j) where red is the minority, else
+// v = 3 (mu j - sum_i e_i f^b_i). Exact for a post-recolouring state.
+template <int Q, int ST>
+__global__ void k_import(Dom d, const float *__restrict__ src) {
+  const int k = blockIdx.x * GBLOCK + threadIdx.x;
+  if (k >= d.NF) return;
+  const long long g = d.fg[k];
+  float rr = 0.f, rb = 0.f, j[3] = {0.f, 0.f, 0.f}, jr[3] = {0.f, 0.f, 0.f},
+        jb[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const float r = src[(long long)i * d.N + g];
+    const float b = src[(long long)(Q + i) * d.N + g];
+    rr += r;
+    rb += b;
+    const float e3[3] = {(float)Lattice<Q>::ex(i), (float)Lattice<Q>::ey(i),
+                         (float)Lattice<Q>::ez(i)};
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      jr[a] += e3[a] * r;
+      jb[a] += e3[a] * b;
+      j[a] += e3[a] * (r + b);
+    }
+    TIO<Q, ST>::store(d, d.T_dst, i, k, r + b);
+  }
+  const bool neg = rr < rb;
+  const float mu = fminf(rr, rb) / (rr + rb);
+  float v[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    v[a] = neg ? 3.f * (jr[a] - mu * j[a]) : 3.f * (mu * j[a] - jb[a]);
+  d.S_dst[k] = make_float4(m_encode(neg, mu), v[0], v[1], v[2]);
 }
 
 template <int Q, int ST>
-__global__ void k_import(Dom d, const float *__restrict__ src) {
-  const long long n = (long long)blockIdx.x * GBLOCK + threadIdx.x;
-  if (n >= d.N) return;
-  const PopIO<Q, ST> io(d);
-  const bool fluid = is_fluid_cls(d.cls[n]);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    float r = 0.f, b = 0.f;
-    if (fluid) {
-      r = src[(long long)i * d.N + n];
-      b = src[(long long)(Q + i) * d.N + n];
-    }
-    io.store(i, n, r, b);
-  }
+static void init_t(const Dom &d, const float *phi0, cudaStream_t s) {
+  const long long n = d.NF > d.NS ? d.NF : d.NS;
+  k_init_state<Q, ST><<<gblocks(n), GBLOCK, 0, s>>>(d, phi0);
 }
 
-// The state kernels write the current buffer: a copy of d with f_dst
-// pointing at it.
+// The state kernels write the current buffers: a copy of d whose T_dst and
+// S_dst point at them.
 void launch_init_state(int Q, int st, const Dom &d0, const float *phi0,
                        cudaStream_t s) {
   Dom d = d0;
-  d.f_dst = d.f_src;
-  const unsigned g = gblocks(d.N);
-#define LBM_INIT(QQ, SS) k_init_state<QQ, SS><<<g, GBLOCK, 0, s>>>(d, phi0)
+  d.T_dst = const_cast<void *>(d.T_src);
+  d.S_dst = const_cast<float4 *>(d.S_src);
   if (Q == 19) {
-    if (st == 0) LBM_INIT(19, 0);
-    if (st == 1) LBM_INIT(19, 1);
-    if (st == 2) LBM_INIT(19, 2);
+    if (st == 0) init_t<19, 0>(d, phi0, s);
+    if (st == 1) init_t<19, 1>(d, phi0, s);
+    if (st == 2) init_t<19, 2>(d, phi0, s);
   } else {
-    if (st == 0) LBM_INIT(9, 0);
-    if (st == 1) LBM_INIT(9, 1);
-    if (st == 2) LBM_INIT(9, 2);
+    if (st == 0) init_t<9, 0>(d, phi0, s);
+    if (st == 1) init_t<9, 1>(d, phi0, s);
+    if (st == 2) init_t<9, 2>(d, phi0, s);
   }
-#undef LBM_INIT
 }
 
 void launch_export_pops(int Q, int st, const Dom &d, float *dst,
                         cudaStream_t s) {
-  const unsigned g = gblocks(d.N);
+  cudaMemsetAsync(dst, 0, sizeof(float) * 2 * Q * (size_t)d.N, s);
+  const unsigned g = gblocks(d.NF);
 #define LBM_EXP(QQ, SS) k_export<QQ, SS><<<g, GBLOCK, 0, s>>>(d, dst)
   if (Q == 19) {
     if (st == 0) LBM_EXP(19, 0);
@@ -256,8 +383,9 @@ void launch_export_pops(int Q, int st, const Dom &d, float *dst,
 void launch_import_pops(int Q, int st, const Dom &d0, const float *src,
                         cudaStream_t s) {
   Dom d = d0;
-  d.f_dst = d.f_src;
-  const unsigned g = gblocks(d.N);
+  d.T_dst = const_cast<void *>(d.T_src);
+  d.S_dst = const_cast<float4 *>(d.S_src);
+  const unsigned g = gblocks(d.NF);
 #define LBM_IMP(QQ, SS) k_import<QQ, SS><<<g, GBLOCK, 0, s>>>(d, src)
   if (Q == 19) {
     if (st == 0) LBM_IMP(19, 0);
@@ -271,21 +399,47 @@ void launch_import_pops(int Q, int st, const Dom &d0, const float *src,
 #undef LBM_IMP
 }
 
-}  // namespace lbm
+// Dense fields of the last macro step: rho, phi (solid-boundary nodes:
+// Eq. 34), u; zero elsewhere.
+__global__ void k_export_macros(Dom d, float *__restrict__ rho,
+                                float *__restrict__ phi, float *__restrict__ u) {
+  const int k = blockIdx.x * GBLOCK + threadIdx.x;
+  if (k < d.NF) {
+    const long long g = d.fg[k];
+    const float4 m = d.macro[k];
+    if (rho) rho[g] = m.w;
+    if (phi) phi[g] = m_phi(d.mf[k]);
+    if (u) {
+      u[g] = m.x;
+      u[d.N + g] = m.y;
+      u[2 * d.N + g] = m.z;
+    }
+  }
+  if (k < d.NS && phi) phi[d.sg[k]] = m_phi(d.ms[k]);
+}
 
-namespace lbm {
+void launch_export_macros(const Dom &d, float *rho, float *phi, float *u,
+                          cudaStream_t s) {
+  if (rho) cudaMemsetAsync(rho, 0, sizeof(float) * (size_t)d.N, s);
+  if (phi) cudaMemsetAsync(phi, 0, sizeof(float) * (size_t)d.N, s);
+  if (u) cudaMemsetAsync(u, 0, sizeof(float) * 3 * (size_t)d.N, s);
+  const long long n = d.NF > d.NS ? d.NF : d.NS;
+  k_export_macros<<<gblocks(n), GBLOCK, 0, s>>>(d, rho, phi, u);
+}
 
 __global__ void k_export_nw(Dom d, float *__restrict__ out) {
-  const long long n = (long long)blockIdx.x * GBLOCK + threadIdx.x;
-  if (n >= d.N) return;
-  const float4 v = d.nw[n];
-  out[n] = v.x;
-  out[d.N + n] = v.y;
-  out[2 * d.N + n] = v.z;
+  const int k = blockIdx.x * GBLOCK + threadIdx.x;
+  if (k >= d.NF) return;
+  const long long g = d.fg[k];
+  const float4 v = d.nw[k];
+  out[g] = v.x;
+  out[d.N + g] = v.y;
+  out[2 * d.N + g] = v.z;
 }
 
 void launch_export_nw(const Dom &d, float *out, cudaStream_t s) {
-  k_export_nw<<<gblocks(d.N), GBLOCK, 0, s>>>(d, out);
+  cudaMemsetAsync(out, 0, sizeof(float) * 3 * (size_t)d.N, s);
+  k_export_nw<<<gblocks(d.NF), GBLOCK, 0, s>>>(d, out);
 }
 
 }  // namespace lbm

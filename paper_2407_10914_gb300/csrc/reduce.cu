@@ -1,6 +1,6 @@
-// FP64 diagnostics: warp-shuffle, then block, then a one-block pass over
-// the per-block partials. Four accumulators per kind; the host combines
-// them (a ratio or a difference) into the reported number.
+// FP64 diagnostics over the compact fluid list: warp-shuffle, then block,
+// then a one-block pass over the per-block partials. Four accumulators per
+// kind; the host combines them (a ratio or a difference).
 #include <cuda_runtime.h>
 
 #include "stencil.cuh"
@@ -35,50 +35,56 @@ __device__ __forceinline__ void block_sum4(double *v) {
   }
 }
 
-// kind: LBM_MASS_R/B: acc0 = sum_i f^s_i; LBM_SW_COUNT: acc0 = #(phi<0);
-// LBM_SW_SMOOTH: acc0 = sum (1-phi)/2; LBM_DP: acc0/acc1 = sum/count of
-// rho on the inlet plane, acc2/acc3 the same on the outlet plane;
-// LBM_CA_R/B: acc0/acc1 = sum/count of u_a over phi > 0 (phi < 0).
+// kind: LBM_MASS_R/B: acc0 = colour density sum_i f^s_i of the stored state
+// (mu rho for the minority colour, (1 - mu) rho for the other);
+// LBM_SW_COUNT: acc0 = #(phi < 0); LBM_SW_SMOOTH: acc0 = sum (1 - phi)/2;
+// LBM_DP: acc0/acc1 = sum/count of rho on the inlet plane, acc2/acc3 the same
+// on the outlet plane; LBM_CA_R/B: acc0/acc1 = sum/count of u_a over phi > 0
+// (phi < 0).
 template <int Q, int ST>
 __global__ void __launch_bounds__(RBLOCK) k_reduce(Dom d, int kind,
                                                    double *__restrict__ part) {
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  const PopIO<Q, ST> io(d);
-  const long long stride = (long long)gridDim.x * RBLOCK;
+  const int stride = gridDim.x * RBLOCK;
   const int a = d.c.axis;
   const int na = axis_extent(d, a);
-  for (long long n = (long long)blockIdx.x * RBLOCK + threadIdx.x; n < d.N;
-       n += stride) {
-    if (!is_fluid_cls(d.cls[n])) continue;
+  for (int k = blockIdx.x * RBLOCK + threadIdx.x; k < d.NF; k += stride) {
     if (kind == LBM_MASS_R || kind == LBM_MASS_B) {
-      double s = 0.0;
+      double rho = 0.0;
 #pragma unroll
-      for (int i = 0; i < Q; ++i) {
-        float r, b;
-        io.load(i, n, r, b);
-        s += (double)(kind == LBM_MASS_R ? r : b);
-      }
-      acc[0] += s;
-    } else if (kind == LBM_SW_COUNT) {
-      acc[0] += d.phi[n] < 0.f ? 1.0 : 0.0;
-    } else if (kind == LBM_SW_SMOOTH) {
-      acc[0] += 0.5 * (1.0 - (double)d.phi[n]);
+      for (int i = 0; i < Q; ++i) rho += (double)TIO<Q, ST>::load(d, i, k);
+      const float q = d.S_src[k].x;
+      const double minor = (double)fabsf(q) * rho;
+      const bool red_minor = signbit(q);
+      const bool want_red = kind == LBM_MASS_R;
+      acc[0] += (want_red == red_minor) ? minor : rho - minor;
+    } else if (kind == LBM_SW_COUNT || kind == LBM_SW_SMOOTH) {
+      const float m = d.mf[k];
+      const float am = fabsf(m);
+      if (kind == LBM_SW_COUNT)
+        acc[0] += (signbit(m) && am < 0.5f) ? 1.0 : 0.0;
+      else
+        acc[0] += signbit(m) ? 1.0 - (double)am : (double)am;
     } else if (kind == LBM_DP) {
       int x, y, z;
-      node_coords(d, n, x, y, z);
+      box_coords(d, d.fg[k], x, y, z);
       const int ca = axis_coord(x, y, z, a);
+      const double rho = d.macro[k].w;
       if (ca == 0) {
-        acc[0] += d.rho_m[n];
+        acc[0] += rho;
         acc[1] += 1.0;
       }
       if (ca == na - 1) {
-        acc[2] += d.rho_m[n];
+        acc[2] += rho;
         acc[3] += 1.0;
       }
     } else {
-      const bool red = d.phi[n] > 0.f;
-      if ((kind == LBM_CA_R) == red) {
-        acc[0] += d.u_m[(long long)a * d.N + n];
+      const float m = d.mf[k];
+      const bool red = !signbit(m) && fabsf(m) < 0.5f;  // phi > 0
+      const bool blue = signbit(m) && fabsf(m) < 0.5f;  // phi < 0
+      if ((kind == LBM_CA_R && red) || (kind == LBM_CA_B && blue)) {
+        const float4 mc = d.macro[k];
+        acc[0] += a == 0 ? mc.x : (a == 1 ? mc.y : mc.z);
         acc[1] += 1.0;
       }
     }
@@ -103,8 +109,8 @@ __global__ void __launch_bounds__(RBLOCK) k_reduce_final(
 
 void launch_reduce(int Q, int st, const Dom &d, int kind, double *part,
                    int slots, double *out, cudaStream_t s) {
-  long long want = (d.N + RBLOCK - 1) / RBLOCK;
-  const int g = (int)(want < slots ? want : slots);
+  const long long want = ((long long)d.NF + RBLOCK - 1) / RBLOCK;
+  const int g = (int)(want < slots ? (want > 0 ? want : 1) : slots);
 #define LBM_RED(QQ, SS) k_reduce<QQ, SS><<<g, RBLOCK, 0, s>>>(d, kind, part)
   if (Q == 19) {
     if (st == 0) LBM_RED(19, 0);

@@ -1,7 +1,8 @@
-// Device building blocks of the step: neighbour arithmetic, population
-// storage policies, the pull of Eq. (1) with halfway bounce-back, Zou-He
-// (App. B), the wetting schemes (Eqs. 28-33) and the collision (Eq. 2,
-// single-rate form) with recolouring (Eqs. 20-21). All arithmetic is FP32.
+// Device building blocks of the step: neighbour lookup in the compact
+// fluid / solid-boundary spaces, the encoded phase field, the storage of the
+// post-recolouring populations and their rebuild, the pull of Eq. (1) with
+// halfway bounce-back, Zou-He (App. B), the wetting schemes (Eqs. 28-33) and
+// the collision (Eq. 2, single-rate form). All arithmetic is FP32.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -16,10 +17,11 @@ constexpr float EPS_C = 1e-8f;        // |C| at or below: no interface
 constexpr float EPS_SIN = 1e-6f;      // Scheme-II: n_c parallel to n_w
 constexpr float EPS_SECANT = 1e-12f;  // Scheme-I: secant denominator
 
-__device__ __forceinline__ void node_coords(const Dom &d, long long n, int &x,
-                                            int &y, int &z) {
-  long long q = n / d.nx;
-  x = (int)(n - q * d.nx);
+// ------------------------------------------------------ coordinates
+__device__ __forceinline__ void box_coords(const Dom &d, long long g, int &x,
+                                           int &y, int &z) {
+  long long q = g / d.nx;
+  x = (int)(g - q * d.nx);
   z = (int)(q / d.ny);
   y = (int)(q - (long long)z * d.ny);
 }
@@ -41,121 +43,141 @@ __device__ __forceinline__ int axis_step(int v, int m, bool per, bool clamp,
   return v;
 }
 
-__device__ __forceinline__ long long nb_index(const Dom &d, int x, int y,
-                                              int z, int dx, int dy, int dz,
-                                              bool clamp, bool &out) {
-  int X = axis_step(x + dx, d.nx, d.periodic & 1u, clamp, out);
-  int Y = axis_step(y + dy, d.ny, d.periodic & 2u, clamp, out);
-  int Z = axis_step(z + dz, d.nz, d.periodic & 4u, clamp, out);
-  return X + (long long)d.nx * (Y + (long long)d.ny * Z);
+struct Loc {
+  int cls;  // LBM_CLS_* of the node
+  int idx;  // F-space index (fluid) or S-space index (solid-boundary)
+};
+
+// Class and compact index of box node (X, Y, Z).
+__device__ __forceinline__ Loc locate(const Dom &d, int X, int Y, int Z) {
+  const long long row = Y + (long long)d.ny * Z;
+  const uint16_t m = __ldg(d.map + X + (long long)d.nx * row);
+  const int cls = m >> 8;
+  const long long seg = (X >> 8) + (long long)d.spr * row;
+  const int base = (cls & 2) ? __ldg(d.fbase + seg) : __ldg(d.sbase + seg);
+  return Loc{cls, base + (m & 255)};
 }
 
-__device__ __forceinline__ bool is_fluid_cls(uint8_t c) { return c & 2; }
+// Neighbour x + e of a node; `out` is set for an off-box neighbour on a
+// non-periodic axis unless clamp is true.
+__device__ __forceinline__ Loc neighbour(const Dom &d, int x, int y, int z,
+                                         int dx, int dy, int dz, bool clamp,
+                                         bool &out) {
+  const int X = axis_step(x + dx, d.nx, d.periodic & 1u, clamp, out);
+  const int Y = axis_step(y + dy, d.ny, d.periodic & 2u, clamp, out);
+  const int Z = axis_step(z + dz, d.nz, d.periodic & 4u, clamp, out);
+  if (out) return Loc{CLS_SOLID, -1};
+  return locate(d, X, Y, Z);
+}
+
+__device__ __forceinline__ bool is_fluid_cls(int c) { return c & 2; }
+
+// ------------------------------------------------------ phase encoding
+// m = +mu where phi >= 0, -mu (signed zero included) where phi < 0, with
+// mu = min(rho^r, rho^b)/rho, i.e. phi = sign(m) (1 - 2|m|).
+__device__ __forceinline__ float m_encode(bool neg, float mu) {
+  return copysignf(mu, neg ? -1.f : 1.f);
+}
+__device__ __forceinline__ float m_of(float rr, float rb) {
+  return m_encode(rr < rb, fminf(rr, rb) / (rr + rb));
+}
+__device__ __forceinline__ float m_phi(float m) {
+  const float a = fabsf(m);
+  return signbit(m) ? 2.f * a - 1.f : 1.f - 2.f * a;
+}
+// phi(nb) - s, s = -1 if own_neg else +1, to full relative accuracy.
+__device__ __forceinline__ float m_excess(float m_nb, bool own_neg) {
+  const float a = fabsf(m_nb);
+  const float mag = ((bool)signbit(m_nb) == own_neg) ? a : 1.f - a;
+  return own_neg ? 2.f * mag : -2.f * mag;
+}
 
 // ------------------------------------------------------------ storage
-// Populations as float32: plane (s*Q + i) of stride Np.
-template <int Q, int STORAGE>
-struct PopIO;
+// f''_i planes: float32, or 16-bit (f''_i/w_i - rho0) so that the stored
+// numbers are O(1e-2) deviations; arithmetic stays FP32.
+template <int Q, int ST>
+struct TIO;
 
 template <int Q>
-struct PopIO<Q, LBM_STORAGE_FP32> {
-  const float *__restrict__ src;
-  float *__restrict__ dst;
-  long long Np;
-  float rho0;
-  __device__ __forceinline__ PopIO(const Dom &d)
-      : src((const float *)d.f_src), dst((float *)d.f_dst), Np(d.Np),
-        rho0(d.c.rho0) {}
-  __device__ __forceinline__ void load(int i, long long n, float &r,
-                                       float &b) const {
-    r = __ldg(src + (long long)i * Np + n);
-    b = __ldg(src + (long long)(Q + i) * Np + n);
+struct TIO<Q, LBM_STORAGE_FP32> {
+  __device__ __forceinline__ static float load(const Dom &d, int i, int k) {
+    return __ldg((const float *)d.T_src + (long long)i * d.NFp + k);
   }
-  __device__ __forceinline__ void store(int i, long long n, float r,
-                                        float b) const {
-    dst[(long long)i * Np + n] = r;
-    dst[(long long)(Q + i) * Np + n] = b;
-  }
-};
-
-// 16-bit offset storage: per (i, n) one pair (T'_i, D'_i) with
-// T'_i = (f^r_i + f^b_i - w_i rho0)/w_i and D'_i = (f^r_i - f^b_i)/w_i,
-// so that both are O(1) numbers; arithmetic stays FP32.
-template <typename H2>
-struct Half2Conv;
-template <>
-struct Half2Conv<__half2> {
-  __device__ __forceinline__ static float2 to(__half2 h) {
-    return __half22float2(h);
-  }
-  __device__ __forceinline__ static __half2 from(float a, float b) {
-    return __floats2half2_rn(a, b);
-  }
-};
-template <>
-struct Half2Conv<__nv_bfloat162> {
-  __device__ __forceinline__ static float2 to(__nv_bfloat162 h) {
-    return __bfloat1622float2(h);
-  }
-  __device__ __forceinline__ static __nv_bfloat162 from(float a, float b) {
-    return __floats2bfloat162_rn(a, b);
-  }
-};
-
-template <int Q, typename H2>
-struct PopIO16 {
-  const H2 *__restrict__ src;
-  H2 *__restrict__ dst;
-  long long Np;
-  float rho0;
-  __device__ __forceinline__ PopIO16(const Dom &d)
-      : src((const H2 *)d.f_src), dst((H2 *)d.f_dst), Np(d.Np),
-        rho0(d.c.rho0) {}
-  __device__ __forceinline__ void load(int i, long long n, float &r,
-                                       float &b) const {
-    const float w = Lattice<Q>::w(i);
-    float2 v = Half2Conv<H2>::to(src[(long long)i * Np + n]);
-    float t = w * (v.x + rho0);
-    float dd = w * v.y;
-    r = 0.5f * (t + dd);
-    b = 0.5f * (t - dd);
-  }
-  __device__ __forceinline__ void store(int i, long long n, float r,
-                                        float b) const {
-    const float iw = 1.0f / Lattice<Q>::w(i);
-    dst[(long long)i * Np + n] =
-        Half2Conv<H2>::from((r + b) * iw - rho0, (r - b) * iw);
+  __device__ __forceinline__ static void store(const Dom &d, void *T, int i,
+                                               int k, float v) {
+    ((float *)T)[(long long)i * d.NFp + k] = v;
   }
 };
 
 template <int Q>
-struct PopIO<Q, LBM_STORAGE_FP16> : PopIO16<Q, __half2> {
-  __device__ __forceinline__ PopIO(const Dom &d) : PopIO16<Q, __half2>(d) {}
+struct TIO<Q, LBM_STORAGE_FP16> {
+  __device__ __forceinline__ static float load(const Dom &d, int i, int k) {
+    const __half h = ((const __half *)d.T_src)[(long long)i * d.NFp + k];
+    return Lattice<Q>::w(i) * (__half2float(h) + d.c.rho0);
+  }
+  __device__ __forceinline__ static void store(const Dom &d, void *T, int i,
+                                               int k, float v) {
+    ((__half *)T)[(long long)i * d.NFp + k] =
+        __float2half_rn(v * (1.f / Lattice<Q>::w(i)) - d.c.rho0);
+  }
 };
+
 template <int Q>
-struct PopIO<Q, LBM_STORAGE_BF16> : PopIO16<Q, __nv_bfloat162> {
-  __device__ __forceinline__ PopIO(const Dom &d)
-      : PopIO16<Q, __nv_bfloat162>(d) {}
+struct TIO<Q, LBM_STORAGE_BF16> {
+  __device__ __forceinline__ static float load(const Dom &d, int i, int k) {
+    const __nv_bfloat16 h =
+        ((const __nv_bfloat16 *)d.T_src)[(long long)i * d.NFp + k];
+    return Lattice<Q>::w(i) * (__bfloat162float(h) + d.c.rho0);
+  }
+  __device__ __forceinline__ static void store(const Dom &d, void *T, int i,
+                                               int k, float v) {
+    ((__nv_bfloat16 *)T)[(long long)i * d.NFp + k] =
+        __float2bfloat16_rn(v * (1.f / Lattice<Q>::w(i)) - d.c.rho0);
+  }
 };
+
+// Rebuild f^r'_i, f^b'_i of a node from its f''_i and (q, v), Eqs. (20)-(21):
+// the minority colour is mu f''_i -+ w_i e_i.v (exact up to rounding, and to
+// full relative accuracy when that colour is scarce), the majority the rest.
+template <int Q>
+__device__ __forceinline__ void rebuild(float T, float4 S, int i, float &fr,
+                                        float &fb) {
+  const float w = Lattice<Q>::w(i);
+  const float ev = (float)Lattice<Q>::ex(i) * S.y +
+                   (float)Lattice<Q>::ey(i) * S.z +
+                   (float)Lattice<Q>::ez(i) * S.w;
+  const float mu = fabsf(S.x);
+  if (signbit(S.x)) {  // blue-rich: red is the minority
+    fr = mu * T + w * ev;
+    fb = T - fr;
+  } else {
+    fb = mu * T - w * ev;
+    fr = T - fb;
+  }
+}
 
 // --------------------------------------------------------------- pull
-// Eq. (1), propagation: f^s_i(x) = f^s_i*(x - e_i) when x - e_i is a fluid
-// node of the box (periodic axes wrap), else the halfway bounce-back
-// f^s_opp(i)*(x).
-template <int Q, int STORAGE>
-__device__ __forceinline__ void pull(const Dom &d, const PopIO<Q, STORAGE> &io,
-                                     long long n, int x, int y, int z,
-                                     float *fr, float *fb) {
+// Eq. (1), propagation: f^s_i(x) = f^s_i'(x - e_i) when x - e_i is a fluid
+// node (periodic axes wrap), else the halfway bounce-back f^s_opp(i)'(x).
+template <int Q, int ST>
+__device__ __forceinline__ void pull(const Dom &d, int k, int x, int y, int z,
+                                     float4 Sown, float *fr, float *fb) {
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
+    if (i == 0) {
+      rebuild<Q>(TIO<Q, ST>::load(d, 0, k), Sown, 0, fr[0], fb[0]);
+      continue;
+    }
     bool out = false;
-    long long src = nb_index(d, x, y, z, -Lattice<Q>::e(i, 0),
-                             -Lattice<Q>::e(i, 1), -Lattice<Q>::e(i, 2),
-                             false, out);
-    if (i != 0 && (out || !is_fluid_cls(d.cls[src])))
-      io.load(Lattice<Q>::opp(i), n, fr[i], fb[i]);
-    else
-      io.load(i, src, fr[i], fb[i]);
+    const Loc L = neighbour(d, x, y, z, -Lattice<Q>::ex(i),
+                            -Lattice<Q>::ey(i), -Lattice<Q>::ez(i), false, out);
+    if (is_fluid_cls(L.cls)) {
+      const float4 S = __ldg(d.S_src + L.idx);
+      rebuild<Q>(TIO<Q, ST>::load(d, i, L.idx), S, i, fr[i], fb[i]);
+    } else {
+      const int o = Lattice<Q>::opp(i);
+      rebuild<Q>(TIO<Q, ST>::load(d, o, k), Sown, o, fr[i], fb[i]);
+    }
   }
 }
 
@@ -294,20 +316,24 @@ __device__ __forceinline__ void scheme1(float *nc, const float *nw, float cth) {
 }
 
 // Scheme-II, Eqs. (32)-(33): with c = n_w.n_c = cos(theta') and
-// s' = sin(theta') = sqrt(1 - c^2),
-//   n_+- = (cos(theta) -+ sin(theta) c/s') n_w +- (sin(theta)/s') n_c,
-// keep the one nearer to n_c (n_+ on a tie); unchanged when s' < EPS_SIN.
+// s' = sin(theta'), n_+- = (cos(theta) -+ sin(theta) c/s') n_w
+// +- (sin(theta)/s') n_c; keep the one nearer to n_c (n_+ on a tie);
+// unchanged when s' < EPS_SIN. Regrouped as n_+- = cos(theta) n_w
+// +- (sin(theta)/s') t with t = n_c - c n_w and s' = |t| (the same numbers
+// for unit vectors), which stays accurate when n_c and n_w are nearly
+// parallel.
 __device__ __forceinline__ void scheme2(float *nc, const float *nw, float cth,
                                         float sth) {
-  float c = fminf(1.f, fmaxf(-1.f, dot3(nw, nc)));
-  const float sp = sqrtf(fmaxf(0.f, 1.f - c * c));
+  const float c = fminf(1.f, fmaxf(-1.f, dot3(nw, nc)));
+  float t[3] = {nc[0] - c * nw[0], nc[1] - c * nw[1], nc[2] - c * nw[2]};
+  const float sp = sqrtf(dot3(t, t));
   if (sp < EPS_SIN) return;
   const float k = sth / sp;
   float np_[3], nm_[3], dp = 0.f, dm = 0.f;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    np_[a] = (cth - k * c) * nw[a] + k * nc[a];
-    nm_[a] = (cth + k * c) * nw[a] - k * nc[a];
+    np_[a] = cth * nw[a] + k * t[a];
+    nm_[a] = cth * nw[a] - k * t[a];
     dp += (np_[a] - nc[a]) * (np_[a] - nc[a]);
     dm += (nm_[a] - nc[a]) * (nm_[a] - nc[a]);
   }
@@ -330,24 +356,17 @@ __device__ __forceinline__ float relaxation_rate(const StepConst &c,
 //   f''_i = f_i - S (f_i - feq_i) + (1 - S/2) G_i + e_i . b,
 //   b = S (j - rho0 u + F/2) / E2,
 // feq of Eq. (A.4), G_i = w_i [3 (e_i - u) + 9 (e_i.u) e_i].F (A.5), u of
-// Eq. (22); then recolouring, Eqs. (20)-(21):
-//   f^r'_i = rho^r/rho f''_i + beta w_i rho^r rho^b/rho (e_i.n),
-//   f^b'_i = f''_i - f^r'_i.
-// fr/fb are overwritten with the post-recolouring populations; u is returned.
+// Eq. (22). ft holds f^t on entry and f''^t on exit.
 template <int Q>
-__device__ __forceinline__ void collide_recolour(const StepConst &c, float *fr,
-                                                 float *fb, float phi,
-                                                 const float *F,
-                                                 const float *nrm, float *u) {
-  float rr, rb;
-  sum_colours<Q>(fr, fb, rr, rb);
-  const float rho = rr + rb;
+__device__ __forceinline__ void collide(const StepConst &c, float *ft,
+                                        float rho, const float *F, float phi,
+                                        float *u) {
   float j[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const float ft = fr[i] + fb[i];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) j[a] += (float)Lattice<Q>::e(i, a) * ft;
+    j[0] += (float)Lattice<Q>::ex(i) * ft[i];
+    j[1] += (float)Lattice<Q>::ey(i) * ft[i];
+    j[2] += (float)Lattice<Q>::ez(i) * ft[i];
   }
   const float irho = 1.f / rho;
 #pragma unroll
@@ -359,25 +378,18 @@ __device__ __forceinline__ void collide_recolour(const StepConst &c, float *fr,
   for (int a = 0; a < 3; ++a)
     b[a] = S * (j[a] - c.rho0 * u[a] + 0.5f * F[a]) * (1.f / Lattice<Q>::E2);
   const float kf = 1.f - 0.5f * S;
-  const float ratio = rr * irho;
-  const float seg = c.beta * rr * rb * irho;
   const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const float ex = (float)Lattice<Q>::e(i, 0), ey = (float)Lattice<Q>::e(i, 1),
-                ez = (float)Lattice<Q>::e(i, 2);
+    const float ex = (float)Lattice<Q>::ex(i), ey = (float)Lattice<Q>::ey(i),
+                ez = (float)Lattice<Q>::ez(i);
     const float w = Lattice<Q>::w(i);
     const float eu = ex * u[0] + ey * u[1] + ez * u[2];
     const float eF = ex * F[0] + ey * F[1] + ez * F[2];
     const float feq = w * (rho + c.rho0 * (3.f * eu + 4.5f * eu * eu - 1.5f * uu));
     const float guo = w * (3.f * (eF - uF) + 9.f * eu * eF);
-    const float ft = fr[i] + fb[i];
-    const float out = ft - S * (ft - feq) + kf * guo +
-                      (ex * b[0] + ey * b[1] + ez * b[2]);
-    const float en = ex * nrm[0] + ey * nrm[1] + ez * nrm[2];
-    const float r = ratio * out + seg * w * en;
-    fr[i] = r;
-    fb[i] = out - r;
+    ft[i] = ft[i] - S * (ft[i] - feq) + kf * guo +
+            (ex * b[0] + ey * b[1] + ez * b[2]);
   }
 }
 

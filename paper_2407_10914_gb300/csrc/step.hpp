@@ -18,12 +18,12 @@ void launch_step(int Q, int storage, const Dom &d, cudaStream_t s,
 void launch_step_events(int Q, int storage, const Dom &d, cudaStream_t s,
                         bool macros, cudaEvent_t *ev);
 
-// Geometry set-up (geometry.cu): classes, Eq. (25) smoothing, Eq. (26)
-// normals, the solid-boundary list and the counts.
+// Geometry set-up (geometry.cu): classes, the compact lists and the map,
+// Eq. (25) smoothing, Eq. (26) normals and the counts.
 cudaError_t build_geometry(lbm_ctx *c, cudaStream_t s);
 
-// f^s_i = w_i rho^s at fluid nodes (zero elsewhere), phi and the macros of
-// the initial state (geometry.cu).
+// f^s_i = w_i rho^s at fluid nodes, phi and the macros of the initial
+// state (geometry.cu).
 void launch_init_state(int Q, int storage, const Dom &d, const float *phi0,
                        cudaStream_t s);
 
@@ -35,6 +35,11 @@ void launch_import_pops(int Q, int storage, const Dom &d, const float *src,
 
 // Wall normals as float32 [3][N] (geometry.cu).
 void launch_export_nw(const Dom &d, float *out, cudaStream_t s);
+
+// Dense rho [N], phi [N], u [3][N] of the last macro step (geometry.cu);
+// any pointer may be null.
+void launch_export_macros(const Dom &d, float *rho, float *phi, float *u,
+                          cudaStream_t s);
 
 // FP64 reductions (reduce.cu): the result lands in *out_dev.
 void launch_reduce(int Q, int storage, const Dom &d, int kind, double *partials,

@@ -106,7 +106,10 @@ def test_one_step_populations(torch, name, case, dev):
     o, f32 = developed(case, dev)
     s = gpu_session(torch, case)
     s.set_populations(torch.from_numpy(f32))
-    np.testing.assert_array_equal(s.get_populations().cpu().numpy(), f32)
+    # the state is held in its post-recolouring form (f'' and q, v); a
+    # float32-rounded state comes back to within float32 rounding
+    back = s.get_populations().cpu().numpy()
+    assert np.abs(back - f32).max() <= 1e-7 * np.abs(f32).max()
     o.step(1)
     s.step(1)
     got = s.get_populations().cpu().numpy().astype(np.float64)
@@ -157,9 +160,37 @@ def test_reductions_match_oracle(torch, name, case, dev):
             n = (o.geometry()[0] >= 2).sum()
             assert abs(g - r) * n <= 3  # phi within 1e-6 of zero may flip
         elif kind in (lbm.LBM_CA_R, lbm.LBM_CA_B):
-            assert abs(g - r) <= 1e-4 * max(scale, 1e-6) + 1e-9
+            # scale: the capillary number of the largest velocity present
+            p = case.params
+            tau = p["tau_r"] if kind == lbm.LBM_CA_R else p["tau_b"]
+            umax = np.abs(o.fields()["u"]).max()
+            ca_scale = p["rho0"] * (tau - 0.5) / 3 * umax / p["gamma"]
+            assert abs(g - r) <= 1e-4 * ca_scale + 1e-12
+        elif kind == lbm.LBM_DP:
+            assert abs(g - r) <= 1e-6  # float32 densities near 1, over 3
         else:
             assert abs(g - r) <= 1e-5 * max(scale, 1e-3)
+
+
+STORAGE_TOL = {"fp16": 1e-4, "bf16": 1e-3}
+
+
+@pytest.mark.parametrize("storage", ["fp16", "bf16"])
+@pytest.mark.parametrize("name,case,dev", [CASES[0], CASES[2], CASES[4]],
+                         ids=[CASES[0][0], CASES[2][0], CASES[4][0]])
+def test_one_step_16bit_storage(torch, storage, name, case, dev):
+    """16-bit storage of f''_i (offsets from w_i rho0, scaled by 1/w_i);
+    the colour fields q, v and all arithmetic stay float32. Stated error
+    after one step from the float32 state: 1e-4 (fp16), 1e-3 (bf16)."""
+    o, f32 = developed(case, dev)
+    s = gpu_session(torch, case, storage)
+    s.set_populations(torch.from_numpy(f32))
+    o.step(1)
+    s.step(1)
+    got = s.get_populations().cpu().numpy().astype(np.float64)
+    err = rel_err(got, o.pops)
+    print(storage, name, err)
+    assert max(err) <= STORAGE_TOL[storage], err
 
 
 def test_droplet_full_run_phase_and_angle(torch):
