@@ -250,9 +250,14 @@ lbm_status lbm_set_params(lbm_handle c, const lbm_params *p) {
   k.rho_in_b = (float)(p->rho_in * (1.0 - p->zeta_r));
   k.rho_out = (float)p->rho_out;
   {
+    // encoded inlet phase field: minority fraction, majority flag in the
+    // lowest mantissa bit (1 = blue)
     const double phi_in = p->zeta_r - (1.0 - p->zeta_r);
-    const double mu = 0.5 * (1.0 - std::fabs(phi_in));
-    k.m_in = (float)std::copysign(mu, phi_in < 0.0 ? -1.0 : 1.0);
+    const float mu = (float)(0.5 * (1.0 - std::fabs(phi_in)));
+    uint32_t bits;
+    std::memcpy(&bits, &mu, 4);
+    bits = (bits & ~1u) | (phi_in < 0.0 ? 1u : 0u);
+    std::memcpy(&k.m_in, &bits, 4);
   }
   for (int a = 0; a < 3; ++a) k.g[a] = (float)p->g[a];
   c->params_set = true;

@@ -9,13 +9,14 @@
 //    the compact fluid list ("F-space") or solid-boundary list ("S-space");
 //  * populations live in F-space only, in the post-recolouring form that
 //    Eqs. (20)-(21) give them: f''_i = f^r'_i + f^b'_i per direction (Q
-//    planes) plus one float4 per node (q, v): q the signed minority colour
-//    fraction (see phase encoding below) and v = beta rho^r rho^b / rho n,
+//    planes) plus one float4 per node (q, v): q the encoded colour split
+//    (as the phase field below) and v = beta rho^r rho^b / rho n,
 //    from which f^r'_i and f^b'_i are rebuilt exactly;
-//  * the phase field is stored "encoded": m = +min(rho^r,rho^b)/rho where
-//    phi >= 0 and -min(rho^r,rho^b)/rho (signed zero included) where phi < 0,
-//    so that phi - sign(phi) keeps full float32 relative accuracy near the
-//    pure phases (the colour gradient of Eq. 6 is built from it).
+//  * the phase field is stored "encoded": m = min(rho^r,rho^b)/rho (signed:
+//    a colour density can overshoot slightly below zero) with the majority
+//    colour in the lowest mantissa bit, so that phi - sign(phi) keeps
+//    float32 relative accuracy near the pure phases (the colour gradient of
+//    Eq. 6 is built from it).
 #pragma once
 
 #include <cuda_runtime.h>

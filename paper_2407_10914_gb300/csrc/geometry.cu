@@ -178,7 +178,7 @@ __global__ void k_wall_normal(Dom d, const double *__restrict__ g3,
                               float4 *__restrict__ nw) {
   const int k = blockIdx.x * GBLOCK + threadIdx.x;
   if (k >= d.NF) return;
-  const long long g = d.fg[k];
+  const int g = d.fg[k];
   float4 out4 = make_float4(0.f, 0.f, 0.f, 0.f);
   if (d.cls[g] == CLS_FLUID_BND) {
     int x, y, z;
@@ -273,7 +273,7 @@ __global__ void k_init_state(Dom d, const float *__restrict__ phi0) {
   const int k = blockIdx.x * GBLOCK + threadIdx.x;
   if (k < d.NF) {
     const float p = phi0[d.fg[k]];
-    const float m = m_encode(p < 0.f, 0.5f * (1.f - fabsf(p)));
+    const float m = m_pack(p < 0.f, 0.5f * (1.f - fabsf(p)));
 #pragma unroll
     for (int i = 0; i < Q; ++i)
       TIO<Q, ST>::store(d, d.T_dst, i, k, Lattice<Q>::w(i) * d.c.rho0);
@@ -292,7 +292,7 @@ template <int Q, int ST>
 __global__ void k_export(Dom d, float *__restrict__ dst) {
   const int k = blockIdx.x * GBLOCK + threadIdx.x;
   if (k >= d.NF) return;
-  const long long g = d.fg[k];
+  const int g = d.fg[k];
   const float4 S = d.S_src[k];
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -311,7 +311,7 @@ template <int Q, int ST>
 __global__ void k_import(Dom d, const float *__restrict__ src) {
   const int k = blockIdx.x * GBLOCK + threadIdx.x;
   if (k >= d.NF) return;
-  const long long g = d.fg[k];
+  const int g = d.fg[k];
   float rr = 0.f, rb = 0.f, j[3] = {0.f, 0.f, 0.f}, jr[3] = {0.f, 0.f, 0.f},
         jb[3] = {0.f, 0.f, 0.f};
 #pragma unroll
@@ -330,13 +330,13 @@ __global__ void k_import(Dom d, const float *__restrict__ src) {
     }
     TIO<Q, ST>::store(d, d.T_dst, i, k, r + b);
   }
-  const bool neg = rr < rb;
+  const bool blue = rr < rb;
   const float mu = fminf(rr, rb) / (rr + rb);
   float v[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
-    v[a] = neg ? 3.f * (jr[a] - mu * j[a]) : 3.f * (mu * j[a] - jb[a]);
-  d.S_dst[k] = make_float4(m_encode(neg, mu), v[0], v[1], v[2]);
+    v[a] = blue ? 3.f * (jr[a] - mu * j[a]) : 3.f * (mu * j[a] - jb[a]);
+  d.S_dst[k] = make_float4(m_pack(blue, mu), v[0], v[1], v[2]);
 }
 
 template <int Q, int ST>
@@ -405,7 +405,7 @@ __global__ void k_export_macros(Dom d, float *__restrict__ rho,
                                 float *__restrict__ phi, float *__restrict__ u) {
   const int k = blockIdx.x * GBLOCK + threadIdx.x;
   if (k < d.NF) {
-    const long long g = d.fg[k];
+    const int g = d.fg[k];
     const float4 m = d.macro[k];
     if (rho) rho[g] = m.w;
     if (phi) phi[g] = m_phi(d.mf[k]);
@@ -430,7 +430,7 @@ void launch_export_macros(const Dom &d, float *rho, float *phi, float *u,
 __global__ void k_export_nw(Dom d, float *__restrict__ out) {
   const int k = blockIdx.x * GBLOCK + threadIdx.x;
   if (k >= d.NF) return;
-  const long long g = d.fg[k];
+  const int g = d.fg[k];
   const float4 v = d.nw[k];
   out[g] = v.x;
   out[d.N + g] = v.y;

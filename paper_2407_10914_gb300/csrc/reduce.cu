@@ -54,17 +54,16 @@ __global__ void __launch_bounds__(RBLOCK) k_reduce(Dom d, int kind,
 #pragma unroll
       for (int i = 0; i < Q; ++i) rho += (double)TIO<Q, ST>::load(d, i, k);
       const float q = d.S_src[k].x;
-      const double minor = (double)fabsf(q) * rho;
-      const bool red_minor = signbit(q);
+      const double minor = (double)q * rho;
+      const bool red_minor = m_blue(q);
       const bool want_red = kind == LBM_MASS_R;
       acc[0] += (want_red == red_minor) ? minor : rho - minor;
     } else if (kind == LBM_SW_COUNT || kind == LBM_SW_SMOOTH) {
       const float m = d.mf[k];
-      const float am = fabsf(m);
       if (kind == LBM_SW_COUNT)
-        acc[0] += (signbit(m) && am < 0.5f) ? 1.0 : 0.0;
+        acc[0] += (m_blue(m) && m < 0.5f) ? 1.0 : 0.0;
       else
-        acc[0] += signbit(m) ? 1.0 - (double)am : (double)am;
+        acc[0] += m_blue(m) ? 1.0 - (double)m : (double)m;
     } else if (kind == LBM_DP) {
       int x, y, z;
       box_coords(d, d.fg[k], x, y, z);
@@ -80,8 +79,8 @@ __global__ void __launch_bounds__(RBLOCK) k_reduce(Dom d, int kind,
       }
     } else {
       const float m = d.mf[k];
-      const bool red = !signbit(m) && fabsf(m) < 0.5f;  // phi > 0
-      const bool blue = signbit(m) && fabsf(m) < 0.5f;  // phi < 0
+      const bool red = !m_blue(m) && m < 0.5f;  // phi > 0
+      const bool blue = m_blue(m) && m < 0.5f;  // phi < 0
       if ((kind == LBM_CA_R && red) || (kind == LBM_CA_B && blue)) {
         const float4 mc = d.macro[k];
         acc[0] += a == 0 ? mc.x : (a == 1 ? mc.y : mc.z);

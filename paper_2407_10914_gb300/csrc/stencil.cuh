@@ -18,12 +18,13 @@ constexpr float EPS_SIN = 1e-6f;      // Scheme-II: n_c parallel to n_w
 constexpr float EPS_SECANT = 1e-12f;  // Scheme-I: secant denominator
 
 // ------------------------------------------------------ coordinates
-__device__ __forceinline__ void box_coords(const Dom &d, long long g, int &x,
+// Box sizes stay below 2^31 nodes, so index arithmetic is 32-bit.
+__device__ __forceinline__ void box_coords(const Dom &d, int g, int &x,
                                            int &y, int &z) {
-  long long q = g / d.nx;
-  x = (int)(g - q * d.nx);
-  z = (int)(q / d.ny);
-  y = (int)(q - (long long)z * d.ny);
+  const unsigned q = (unsigned)g / (unsigned)d.nx;
+  x = g - (int)q * d.nx;
+  z = (int)(q / (unsigned)d.ny);
+  y = (int)q - z * d.ny;
 }
 
 // Coordinate v + dv (|dv| <= 1) on an axis of extent m. Periodic axes wrap;
@@ -50,11 +51,11 @@ struct Loc {
 
 // Class and compact index of box node (X, Y, Z).
 __device__ __forceinline__ Loc locate(const Dom &d, int X, int Y, int Z) {
-  const long long row = Y + (long long)d.ny * Z;
-  const uint16_t m = __ldg(d.map + X + (long long)d.nx * row);
+  const int row = Y + d.ny * Z;
+  const uint16_t m = __ldg(d.map + (X + d.nx * row));
   const int cls = m >> 8;
-  const long long seg = (X >> 8) + (long long)d.spr * row;
-  const int base = (cls & 2) ? __ldg(d.fbase + seg) : __ldg(d.sbase + seg);
+  const int seg = (X >> 8) + d.spr * row;
+  const int base = __ldg(((cls & 2) ? d.fbase : d.sbase) + seg);
   return Loc{cls, base + (m & 255)};
 }
 
@@ -73,26 +74,39 @@ __device__ __forceinline__ Loc neighbour(const Dom &d, int x, int y, int z,
 __device__ __forceinline__ bool is_fluid_cls(int c) { return c & 2; }
 
 // ------------------------------------------------------ phase encoding
-// m = +mu where phi >= 0, -mu (signed zero included) where phi < 0, with
-// mu = min(rho^r, rho^b)/rho, i.e. phi = sign(m) (1 - 2|m|).
-__device__ __forceinline__ float m_encode(bool neg, float mu) {
-  return copysignf(mu, neg ? -1.f : 1.f);
+// A node's colour split is kept as one float m: the minority fraction
+// mu = min(rho^r, rho^b)/rho with its own sign (it can be slightly negative,
+// like the colour density it comes from), and, in the lowest mantissa bit,
+// which colour is the majority (1 = blue, i.e. phi < 0). Then
+// phi = 1 - 2 mu (red majority) or 2 mu - 1 (blue majority), and
+// phi - sign(phi) keeps float32 relative accuracy near the pure phases.
+// Stealing the bit costs one unit in the last place of mu.
+__device__ __forceinline__ float m_pack(bool blue, float mu) {
+  return __uint_as_float((__float_as_uint(mu) & ~1u) | (blue ? 1u : 0u));
+}
+__device__ __forceinline__ bool m_blue(float m) {
+  return __float_as_uint(m) & 1u;
 }
 __device__ __forceinline__ float m_of(float rr, float rb) {
-  return m_encode(rr < rb, fminf(rr, rb) / (rr + rb));
+  return m_pack(rr < rb, fminf(rr, rb) / (rr + rb));
 }
 __device__ __forceinline__ float m_phi(float m) {
-  const float a = fabsf(m);
-  return signbit(m) ? 2.f * a - 1.f : 1.f - 2.f * a;
+  return m_blue(m) ? 2.f * m - 1.f : 1.f - 2.f * m;
 }
-// phi(nb) - s, s = -1 if own_neg else +1, to full relative accuracy.
-__device__ __forceinline__ float m_excess(float m_nb, bool own_neg) {
-  const float a = fabsf(m_nb);
-  const float mag = ((bool)signbit(m_nb) == own_neg) ? a : 1.f - a;
-  return own_neg ? 2.f * mag : -2.f * mag;
+// phi(nb) - s, s = -1 if own_blue else +1, to full relative accuracy.
+__device__ __forceinline__ float m_excess(float m_nb, bool own_blue) {
+  const float mag = (m_blue(m_nb) == own_blue) ? m_nb : 1.f - m_nb;
+  return own_blue ? 2.f * mag : -2.f * mag;
 }
 
 // ------------------------------------------------------------ storage
+// Weight of a run-time direction index (a select on the three shells).
+template <int Q>
+__device__ __forceinline__ float weight_of(int p) {
+  return p == 0 ? Lattice<Q>::w(0)
+                : (p <= (Q == 19 ? 6 : 4) ? Lattice<Q>::w(1) : Lattice<Q>::w(Q - 1));
+}
+
 // f''_i planes: float32, or 16-bit (f''_i/w_i - rho0) so that the stored
 // numbers are O(1e-2) deviations; arithmetic stays FP32.
 template <int Q, int ST>
@@ -102,6 +116,10 @@ template <int Q>
 struct TIO<Q, LBM_STORAGE_FP32> {
   __device__ __forceinline__ static float load(const Dom &d, int i, int k) {
     return __ldg((const float *)d.T_src + (long long)i * d.NFp + k);
+  }
+  // plane p chosen at run time, p in {i, opp(i)} (equal weights)
+  __device__ __forceinline__ static float load_dyn(const Dom &d, int p, int k) {
+    return __ldg((const float *)d.T_src + (long long)p * d.NFp + k);
   }
   __device__ __forceinline__ static void store(const Dom &d, void *T, int i,
                                                int k, float v) {
@@ -114,6 +132,11 @@ struct TIO<Q, LBM_STORAGE_FP16> {
   __device__ __forceinline__ static float load(const Dom &d, int i, int k) {
     const __half h = ((const __half *)d.T_src)[(long long)i * d.NFp + k];
     return Lattice<Q>::w(i) * (__half2float(h) + d.c.rho0);
+  }
+  // plane p at run time with the weight of w(p) = w(i) supplied by caller's i
+  __device__ __forceinline__ static float load_dyn(const Dom &d, int p, int k) {
+    const __half h = ((const __half *)d.T_src)[(long long)p * d.NFp + k];
+    return weight_of<Q>(p) * (__half2float(h) + d.c.rho0);
   }
   __device__ __forceinline__ static void store(const Dom &d, void *T, int i,
                                                int k, float v) {
@@ -129,6 +152,11 @@ struct TIO<Q, LBM_STORAGE_BF16> {
         ((const __nv_bfloat16 *)d.T_src)[(long long)i * d.NFp + k];
     return Lattice<Q>::w(i) * (__bfloat162float(h) + d.c.rho0);
   }
+  __device__ __forceinline__ static float load_dyn(const Dom &d, int p, int k) {
+    const __nv_bfloat16 h =
+        ((const __nv_bfloat16 *)d.T_src)[(long long)p * d.NFp + k];
+    return weight_of<Q>(p) * (__bfloat162float(h) + d.c.rho0);
+  }
   __device__ __forceinline__ static void store(const Dom &d, void *T, int i,
                                                int k, float v) {
     ((__nv_bfloat16 *)T)[(long long)i * d.NFp + k] =
@@ -137,28 +165,37 @@ struct TIO<Q, LBM_STORAGE_BF16> {
 };
 
 // Rebuild f^r'_i, f^b'_i of a node from its f''_i and (q, v), Eqs. (20)-(21):
-// the minority colour is mu f''_i -+ w_i e_i.v (exact up to rounding, and to
-// full relative accuracy when that colour is scarce), the majority the rest.
+// with ev = e_i.v, the minority colour is mu f''_i -+ w_i ev (exact up to
+// rounding, and to full relative accuracy when that colour is scarce), the
+// majority the rest.
+template <int Q>
+__device__ __forceinline__ void rebuild_ev(float T, float q, float ev, int i,
+                                           float &fr, float &fb) {
+  const float w = Lattice<Q>::w(i);
+  if (m_blue(q)) {  // blue majority: red is the minority
+    fr = q * T + w * ev;
+    fb = T - fr;
+  } else {
+    fb = q * T - w * ev;
+    fr = T - fb;
+  }
+}
+
 template <int Q>
 __device__ __forceinline__ void rebuild(float T, float4 S, int i, float &fr,
                                         float &fb) {
-  const float w = Lattice<Q>::w(i);
   const float ev = (float)Lattice<Q>::ex(i) * S.y +
                    (float)Lattice<Q>::ey(i) * S.z +
                    (float)Lattice<Q>::ez(i) * S.w;
-  const float mu = fabsf(S.x);
-  if (signbit(S.x)) {  // blue-rich: red is the minority
-    fr = mu * T + w * ev;
-    fb = T - fr;
-  } else {
-    fb = mu * T - w * ev;
-    fr = T - fb;
-  }
+  rebuild_ev<Q>(T, S.x, ev, i, fr, fb);
 }
 
 // --------------------------------------------------------------- pull
 // Eq. (1), propagation: f^s_i(x) = f^s_i'(x - e_i) when x - e_i is a fluid
 // node (periodic axes wrap), else the halfway bounce-back f^s_opp(i)'(x).
+// Branch-free: the source node and direction are selected, and since
+// e_opp(i) = -e_i and w_opp(i) = w_i the rebuild differs only in the sign
+// of e.v.
 template <int Q, int ST>
 __device__ __forceinline__ void pull(const Dom &d, int k, int x, int y, int z,
                                      float4 Sown, float *fr, float *fb) {
@@ -171,13 +208,14 @@ __device__ __forceinline__ void pull(const Dom &d, int k, int x, int y, int z,
     bool out = false;
     const Loc L = neighbour(d, x, y, z, -Lattice<Q>::ex(i),
                             -Lattice<Q>::ey(i), -Lattice<Q>::ez(i), false, out);
-    if (is_fluid_cls(L.cls)) {
-      const float4 S = __ldg(d.S_src + L.idx);
-      rebuild<Q>(TIO<Q, ST>::load(d, i, L.idx), S, i, fr[i], fb[i]);
-    } else {
-      const int o = Lattice<Q>::opp(i);
-      rebuild<Q>(TIO<Q, ST>::load(d, o, k), Sown, o, fr[i], fb[i]);
-    }
+    const bool fl = is_fluid_cls(L.cls);
+    const int src = fl ? L.idx : k;
+    const float T = TIO<Q, ST>::load_dyn(d, fl ? i : Lattice<Q>::opp(i), src);
+    const float4 S = __ldg(d.S_src + src);
+    const float ev = (float)Lattice<Q>::ex(i) * S.y +
+                     (float)Lattice<Q>::ey(i) * S.z +
+                     (float)Lattice<Q>::ez(i) * S.w;
+    rebuild_ev<Q>(T, S.x, fl ? ev : -ev, i, fr[i], fb[i]);
   }
 }
 

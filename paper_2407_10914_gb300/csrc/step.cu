@@ -78,9 +78,9 @@ __global__ void __launch_bounds__(BLOCK) k_phi_solid(Dom d) {
     ex_pos += w * m_excess(m, false);
     ex_neg += w * m_excess(m, true);
   }
-  const bool neg = sphi < 0.f;
-  const float ex = (neg ? ex_neg : ex_pos) / den;  // phi_s - s
-  d.ms[j] = m_encode(neg, fmaxf(0.f, neg ? 0.5f * ex : -0.5f * ex));
+  const bool blue = sphi < 0.f;
+  const float ex = (blue ? ex_neg : ex_pos) / den;  // phi_s - s
+  d.ms[j] = m_pack(blue, blue ? 0.5f * ex : -0.5f * ex);
 }
 
 // Eq. (6) (c = dt = 1) and Eq. (27), with phi(x + e_i) - s(x) in place of
@@ -91,10 +91,10 @@ template <int Q>
 __global__ void __launch_bounds__(BLOCK) k_gradient(Dom d) {
   const int k = blockIdx.x * BLOCK + threadIdx.x;
   if (k >= d.NF) return;
-  const long long g = __ldg(d.fg + k);
+  const int g = __ldg(d.fg + k);
   int x, y, z;
   box_coords(d, g, x, y, z);
-  const bool own_neg = signbit(d.mf[k]);
+  const bool own_blue = m_blue(d.mf[k]);
   float G[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(BLOCK) k_gradient(Dom d) {
     const Loc L = neighbour(d, x, y, z, Lattice<Q>::ex(i), Lattice<Q>::ey(i),
                             Lattice<Q>::ez(i), true, out);
     const float m = is_fluid_cls(L.cls) ? d.mf[L.idx] : d.ms[L.idx];
-    const float p = 3.f * Lattice<Q>::w(i) * m_excess(m, own_neg);
+    const float p = 3.f * Lattice<Q>::w(i) * m_excess(m, own_blue);
     G[0] += (float)Lattice<Q>::ex(i) * p;
     G[1] += (float)Lattice<Q>::ey(i) * p;
     G[2] += (float)Lattice<Q>::ez(i) * p;
