@@ -109,7 +109,7 @@ def test_one_step_populations(torch, name, case, dev):
     # the state is held in its post-recolouring form (f'' and q, v); a
     # float32-rounded state comes back to within float32 rounding
     back = s.get_populations().cpu().numpy()
-    assert np.abs(back - f32).max() <= 1e-7 * np.abs(f32).max()
+    assert np.abs(back - f32).max() <= 5e-7 * np.abs(f32).max()
     o.step(1)
     s.step(1)
     got = s.get_populations().cpu().numpy().astype(np.float64)
