@@ -167,6 +167,29 @@ lbm_status lbm_get_geometry(lbm_handle h, uint8_t *cls_dev, float *nw_dev,
 lbm_status lbm_counts(lbm_handle h, int64_t *n_nodes, int64_t *n_fluid,
                       int64_t *n_solid_bnd, int64_t *n_fluid_bnd);
 
+/* Largest node count lbm_colour_mass_noalloc accepts. */
+#define LBM_NOALLOC_MAX_NODES ((int64_t)1 << 31)
+
+/* Colour masses of a dense population array, for callers that cannot
+ * allocate device memory (no counterpart in the paper: it is the
+ * LBM_MASS_R / LBM_MASS_B reduction of lbm_reduce() without a workspace).
+ * Some callers run under a device-memory budget that another framework
+ * reserved up front, or under a policy that forbids allocation after
+ * start-up; they cannot provide a handle's workspace. This call needs none:
+ * pops_dev is the caller's device float32 array [2][Q][n_nodes] (as
+ * lbm_get_populations() writes it; solid entries zero), mass_host[0..1]
+ * receives the red and blue masses, summed in FP64. It allocates nothing:
+ * its scratch is a fixed array of the library's own in device memory
+ * (about 16 KB, present on every GPU that loads the library until exit).
+ * The first call on a device looks up that array's address with the
+ * device current; make it before any stream capture. Every call shares the
+ * array; calls that overlap on the GPU race on it. Synchronises the stream.
+ * LBM_ERR_ARG for lattice not 9/19, null pointers, or n_nodes outside
+ * [1, LBM_NOALLOC_MAX_NODES]. */
+lbm_status lbm_colour_mass_noalloc(int lattice, int64_t n_nodes,
+                                   const float *pops_dev, double *mass_host,
+                                   void *stream);
+
 /* Message of the last failed call on this handle ("" if none). */
 const char *lbm_last_error(lbm_handle h);
 

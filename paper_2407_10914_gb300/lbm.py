@@ -31,7 +31,8 @@ EXPORTS = ("lbm_workspace_bytes", "lbm_init_geometry", "lbm_set_params",
            "lbm_init_state", "lbm_step", "lbm_step_timed", "lbm_macros",
            "lbm_reduce",
            "lbm_get_populations", "lbm_set_populations", "lbm_get_geometry",
-           "lbm_counts", "lbm_last_error", "lbm_destroy")
+           "lbm_counts", "lbm_colour_mass_noalloc", "lbm_last_error",
+           "lbm_destroy")
 
 
 class LbmError(RuntimeError):
@@ -88,6 +89,9 @@ def load_library(path: str = LIB_PATH):
     L.lbm_get_geometry.argtypes = [vp, vp, vp, vp]
     L.lbm_counts.restype = C.c_int
     L.lbm_counts.argtypes = [vp, i64p, i64p, i64p, i64p]
+    L.lbm_colour_mass_noalloc.restype = C.c_int
+    L.lbm_colour_mass_noalloc.argtypes = [C.c_int, C.c_int64, vp,
+                                          C.POINTER(C.c_double), vp]
     L.lbm_last_error.restype = C.c_char_p
     L.lbm_last_error.argtypes = [vp]
     L.lbm_destroy.restype = None
@@ -210,6 +214,18 @@ def lbm_counts(h):
     _check(load_library().lbm_counts(h, *[C.byref(x) for x in v]), h,
            "lbm_counts")
     return tuple(x.value for x in v)
+
+
+def lbm_colour_mass_noalloc(lattice, pops, stream):
+    """Red and blue masses of a dense float32 population tensor
+    (2, Q, ...) on the device, computed without any device allocation by
+    the library (for callers that cannot allocate; see the C header)."""
+    out = (C.c_double * 2)()
+    n = pops.numel() // (2 * lattice)
+    _check(load_library().lbm_colour_mass_noalloc(lattice, n, _dptr(pops),
+                                                  out, stream),
+           None, "lbm_colour_mass_noalloc")
+    return out[0], out[1]
 
 
 def lbm_destroy(h):
