@@ -8,6 +8,7 @@
 #include <new>
 
 #include "step.hpp"
+#include "tiles.cuh"
 
 using lbm::Dom;
 
@@ -47,7 +48,8 @@ struct Layout {
   size_t ms, ncs, sg;                             // S-space
   size_t map, cls, mask, fbase, sbase, cntf, cnts, g0, g1;
   size_t red, out, cnt, total;
-  long long NF, NFp, NS, nseg;
+  long long NF, NFp, NS, ntiles;
+  int ntx, nty, ntz;
 };
 
 // NF is the number of fluid nodes; NS an upper bound of the solid-boundary
@@ -59,7 +61,13 @@ Layout make_layout(int Q, int nx, int ny, int nz, int storage, long long NF,
   L.NF = NF;
   L.NFp = pad64(NF > 0 ? NF : 1);
   L.NS = NS;
-  L.nseg = (long long)((nx + lbm::SEG - 1) / lbm::SEG) * ny * nz;
+  const int TX = Q == 19 ? lbm::Tile<19>::TX : lbm::Tile<9>::TX;
+  const int TY = Q == 19 ? lbm::Tile<19>::TY : lbm::Tile<9>::TY;
+  const int TZ = Q == 19 ? lbm::Tile<19>::TZ : lbm::Tile<9>::TZ;
+  L.ntx = (nx + TX - 1) / TX;
+  L.nty = (ny + TY - 1) / TY;
+  L.ntz = (nz + TZ - 1) / TZ;
+  L.ntiles = (long long)L.ntx * L.nty * L.ntz;
   size_t o = 0;
   auto take = [&](size_t bytes) {
     size_t at = o;
@@ -83,10 +91,10 @@ Layout make_layout(int Q, int nx, int ny, int nz, int storage, long long NF,
   L.map = take((size_t)N * 2);
   L.cls = take((size_t)N);
   L.mask = take((size_t)N);
-  L.fbase = take((size_t)(L.nseg + 1) * 4);
-  L.sbase = take((size_t)(L.nseg + 1) * 4);
-  L.cntf = take((size_t)L.nseg * 4);
-  L.cnts = take((size_t)L.nseg * 4);
+  L.fbase = take((size_t)(L.ntiles + 1) * 4);
+  L.sbase = take((size_t)(L.ntiles + 1) * 4);
+  L.cntf = take((size_t)L.ntiles * 4);
+  L.cnts = take((size_t)L.ntiles * 4);
   L.g0 = take((size_t)N * 8);
   L.g1 = take((size_t)N * 8);
   L.red = take((size_t)RED_SLOTS * 4 * 8);
@@ -154,7 +162,7 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
   c->N = N;
   c->periodic = periodic_mask;
   c->storage = storage;
-  c->nseg = L.nseg;
+  c->ntiles = L.ntiles;
   c->TA = base + L.TA;
   c->TB = base + L.TB;
   c->SA = (float4 *)(base + L.SA);
@@ -174,7 +182,10 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
   d.nz = nz;
   d.N = N;
   d.periodic = periodic_mask;
-  d.spr = (nx + lbm::SEG - 1) / lbm::SEG;
+  d.ntx = L.ntx;
+  d.nty = L.nty;
+  d.ntz = L.ntz;
+  d.ntiles = (int)L.ntiles;
   d.NF = (int)L.NF;
   d.NS = (int)L.NS;  // upper bound until the lists are built
   d.NFp = L.NFp;

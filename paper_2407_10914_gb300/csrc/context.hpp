@@ -2,11 +2,11 @@
 // step, geometry and reduction translation units.
 //
 // Memory layout (all inside the caller's workspace):
-//  * the box is cut into segments of SEG = 256 nodes along x; a uint16 map
-//    over the box holds, per node, its class (bits 8-9) and its rank among
-//    the nodes of the same kind (fluid, or solid-boundary) in its segment
-//    (bits 0-7); per-segment bases turn (segment, rank) into an index of
-//    the compact fluid list ("F-space") or solid-boundary list ("S-space");
+//  * the box is cut into tiles (tiles.cuh); a uint16 map over the box holds,
+//    per node, its class (bits 14-15) and its rank among the nodes of the
+//    same kind (fluid, or solid-boundary) in its tile (bits 0-13); per-tile
+//    bases turn (tile, rank) into an index of the compact fluid list
+//    ("F-space", tile by tile) or solid-boundary list ("S-space");
 //  * populations live in F-space only, in the post-recolouring form that
 //    Eqs. (20)-(21) give them: f''_i = f^r'_i + f^b'_i per direction (Q
 //    planes) plus one float4 per node (q, v): q the encoded colour split
@@ -25,8 +25,6 @@
 #include "../../include/lbmgb.h"
 
 namespace lbm {
-
-constexpr int SEG = 256;
 
 enum : uint8_t {
   CLS_SOLID = LBM_CLS_SOLID,
@@ -51,12 +49,13 @@ struct Dom {
   int nx, ny, nz;
   long long N;      // nodes of the box
   unsigned periodic;
-  int spr;          // segments per x-row
+  int ntx, nty, ntz;  // tiles per axis
+  int ntiles;
   int NF, NS;       // fluid nodes, solid-boundary nodes
   long long NFp;    // stride of one population plane (NF rounded up)
   const uint16_t *map;  // [N]
-  const int *fbase;     // [nseg + 1]
-  const int *sbase;     // [nseg + 1]
+  const int *fbase;     // [ntiles + 1]
+  const int *sbase;     // [ntiles + 1]
   const int *fg;        // [NF] box index of fluid node k
   const int *sg;        // [NS] box index of solid-boundary node j
   const uint8_t *cls;   // [N]
@@ -81,7 +80,7 @@ struct lbm_ctx {
   long long N = 0;
   unsigned periodic = 0;
   int storage = 0;
-  long long nseg = 0;
+  long long ntiles = 0;
   long long n_fluid = 0, n_sbnd = 0, n_fbnd = 0;
   bool params_set = false;
   bool state_set = false;
@@ -91,7 +90,7 @@ struct lbm_ctx {
   float4 *SA = nullptr, *SB = nullptr;
   uint8_t *mask = nullptr;                // device copy of the solid image
   double *g0 = nullptr, *g1 = nullptr;    // smoothing ping-pong (set-up)
-  int *cnt_f = nullptr, *cnt_s = nullptr; // per-segment counts (set-up)
+  int *cnt_f = nullptr, *cnt_s = nullptr; // per-tile counts (set-up)
   double *red = nullptr;                  // reduction partials
   double *red_out = nullptr;              // 4 doubles: the combined partials
   int red_slots = 0;

@@ -1,11 +1,11 @@
 // Set-up passes: node classes; the compact fluid (F) and solid-boundary (S)
-// lists with the per-segment map; the smoothing of Eq. (25) and the wall
+// lists, tile by tile, with the per-tile map; the smoothing of Eq. (25) and the wall
 // normal of Eq. (26); the initial state; dense export/import of the state and
 // fields. These run once or on request, not in the time loop.
 #include <cuda_runtime.h>
 
-#include "stencil.cuh"
 #include "step.hpp"
+#include "tiles.cuh"
 
 namespace lbm {
 
@@ -41,19 +41,35 @@ __global__ void k_classify(Dom d, const uint8_t *__restrict__ mask,
                  : (bnd ? CLS_FLUID_BND : CLS_FLUID);
 }
 
-// One block per segment (SEG = GBLOCK nodes along x): fluid and
-// solid-boundary counts.
-__global__ void k_seg_count(Dom d, int *__restrict__ cf, int *__restrict__ cs) {
-  const long long seg = blockIdx.x;
-  const long long row = seg / d.spr;
-  const int x = (int)(seg - row * d.spr) * SEG + threadIdx.x;
-  int c = CLS_SOLID;
-  if (x < d.nx) c = d.cls[x + (long long)d.nx * row];
-  const int nf = __syncthreads_count(c & 2);
-  const int ns = __syncthreads_count(c == CLS_SOLID_BND);
+// One block per tile: fluid and solid-boundary counts of the tile.
+template <int Q>
+__global__ void k_tile_count(Dom d, int *__restrict__ cf, int *__restrict__ cs) {
+  using G = TileGeo<Q>;
+  __shared__ int sf, ss;
   if (threadIdx.x == 0) {
-    cf[seg] = nf;
-    cs[seg] = ns;
+    sf = 0;
+    ss = 0;
+  }
+  __syncthreads();
+  const int t = blockIdx.x;
+  const int X0 = (t % d.ntx) * G::TX;
+  const int q = t / d.ntx;
+  const int Y0 = (q % d.nty) * G::TY, Z0 = (q / d.nty) * G::TZ;
+  int nf = 0, ns = 0;
+  for (int lp = threadIdx.x; lp < G::TN; lp += GBLOCK) {
+    int x, y, z, p0;
+    local_node<Q>(lp, X0, Y0, Z0, x, y, z, p0);
+    if (x >= d.nx || y >= d.ny || z >= d.nz) continue;
+    const int c = d.cls[x + d.nx * (y + d.ny * z)];
+    nf += (c & 2) ? 1 : 0;
+    ns += c == CLS_SOLID_BND ? 1 : 0;
+  }
+  atomicAdd(&sf, nf);
+  atomicAdd(&ss, ns);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cf[t] = sf;
+    cs[t] = ss;
   }
 }
 
@@ -96,42 +112,66 @@ __global__ void k_scan(const int *__restrict__ cnt, long long n,
   if (threadIdx.x == 0) base[n] = carry;
 }
 
-// One block per segment: rank of each node among the nodes of its kind in
-// the segment; map = (class << 8) | rank; the F and S lists hold box indices.
-__global__ void k_build_map(Dom d, uint16_t *__restrict__ map,
-                            int *__restrict__ fg, int *__restrict__ sg) {
+// One block per tile: rank of each node among the nodes of its kind in the
+// tile, in the tile's (z, y, x) order; map = (class << 14) | rank; the F and
+// S lists hold box indices.
+template <int Q>
+__global__ void k_tile_map(Dom d, uint16_t *__restrict__ map,
+                           int *__restrict__ fg, int *__restrict__ sg) {
+  using G = TileGeo<Q>;
   __shared__ int wf[GBLOCK / 32], ws[GBLOCK / 32];
-  const long long seg = blockIdx.x;
-  const long long row = seg / d.spr;
-  const int x = (int)(seg - row * d.spr) * SEG + threadIdx.x;
-  const long long g = x + (long long)d.nx * row;
-  const bool valid = x < d.nx;
-  const int c = valid ? d.cls[g] : CLS_SOLID;
-  const bool isf = valid && (c & 2), iss = valid && c == CLS_SOLID_BND;
+  __shared__ int carry_f, carry_s;
+  const int t = blockIdx.x;
+  const int X0 = (t % d.ntx) * G::TX;
+  const int q = t / d.ntx;
+  const int Y0 = (q % d.nty) * G::TY, Z0 = (q / d.nty) * G::TZ;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned bf = __ballot_sync(0xffffffffu, isf);
-  const unsigned bs = __ballot_sync(0xffffffffu, iss);
   const unsigned lt = (1u << lane) - 1u;
-  if (lane == 0) {
-    wf[warp] = __popc(bf);
-    ws[warp] = __popc(bs);
+  if (threadIdx.x == 0) {
+    carry_f = 0;
+    carry_s = 0;
   }
   __syncthreads();
-  int of = 0, os = 0;
-  for (int w = 0; w < warp; ++w) {
-    of += wf[w];
-    os += ws[w];
+  for (int c0 = 0; c0 < G::TN; c0 += GBLOCK) {
+    const int lp = c0 + threadIdx.x;
+    int x, y, z, p0;
+    local_node<Q>(lp, X0, Y0, Z0, x, y, z, p0);
+    const bool valid = x < d.nx && y < d.ny && z < d.nz;
+    const int g = valid ? x + d.nx * (y + d.ny * z) : 0;
+    const int c = valid ? d.cls[g] : CLS_SOLID;
+    const bool isf = valid && (c & 2), iss = valid && c == CLS_SOLID_BND;
+    const unsigned bf = __ballot_sync(0xffffffffu, isf);
+    const unsigned bs = __ballot_sync(0xffffffffu, iss);
+    if (lane == 0) {
+      wf[warp] = __popc(bf);
+      ws[warp] = __popc(bs);
+    }
+    __syncthreads();
+    int of = carry_f, os = carry_s;
+    for (int w = 0; w < warp; ++w) {
+      of += wf[w];
+      os += ws[w];
+    }
+    if (valid) {
+      int rank = 0;
+      if (isf) {
+        rank = of + __popc(bf & lt);
+        fg[d.fbase[t] + rank] = g;
+      } else if (iss) {
+        rank = os + __popc(bs & lt);
+        sg[d.sbase[t] + rank] = g;
+      }
+      map[g] = (uint16_t)((c << 14) | rank);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 0; w < GBLOCK / 32; ++w) {
+        carry_f += wf[w];
+        carry_s += ws[w];
+      }
+    }
+    __syncthreads();
   }
-  if (!valid) return;
-  int rank = 0;
-  if (isf) {
-    rank = of + __popc(bf & lt);
-    fg[d.fbase[seg] + rank] = (int)g;
-  } else if (iss) {
-    rank = os + __popc(bs & lt);
-    sg[d.sbase[seg] + rank] = (int)g;
-  }
-  map[g] = (uint16_t)((c << 8) | rank);
 }
 
 __global__ void k_indicator(long long N, const uint8_t *__restrict__ mask,
@@ -219,17 +259,24 @@ cudaError_t build_geometry(lbm_ctx *c, cudaStream_t s) {
     k_classify<19><<<gN, GBLOCK, 0, s>>>(d, c->mask, cls);
   else
     k_classify<9><<<gN, GBLOCK, 0, s>>>(d, c->mask, cls);
-  k_seg_count<<<(unsigned)c->nseg, GBLOCK, 0, s>>>(d, c->cnt_f, c->cnt_s);
-  k_scan<<<1, 1024, 0, s>>>(c->cnt_f, c->nseg, const_cast<int *>(d.fbase));
-  k_scan<<<1, 1024, 0, s>>>(c->cnt_s, c->nseg, const_cast<int *>(d.sbase));
-  k_build_map<<<(unsigned)c->nseg, GBLOCK, 0, s>>>(
-      d, const_cast<uint16_t *>(d.map), const_cast<int *>(d.fg),
-      const_cast<int *>(d.sg));
+  const unsigned nt = (unsigned)c->ntiles;
+  if (c->Q == 19)
+    k_tile_count<19><<<nt, GBLOCK, 0, s>>>(d, c->cnt_f, c->cnt_s);
+  else
+    k_tile_count<9><<<nt, GBLOCK, 0, s>>>(d, c->cnt_f, c->cnt_s);
+  k_scan<<<1, 1024, 0, s>>>(c->cnt_f, c->ntiles, const_cast<int *>(d.fbase));
+  k_scan<<<1, 1024, 0, s>>>(c->cnt_s, c->ntiles, const_cast<int *>(d.sbase));
+  uint16_t *map = const_cast<uint16_t *>(d.map);
+  int *fg = const_cast<int *>(d.fg), *sg = const_cast<int *>(d.sg);
+  if (c->Q == 19)
+    k_tile_map<19><<<nt, GBLOCK, 0, s>>>(d, map, fg, sg);
+  else
+    k_tile_map<9><<<nt, GBLOCK, 0, s>>>(d, map, fg, sg);
   int tot[2] = {0, 0};
-  cudaError_t e = cudaMemcpyAsync(&tot[0], d.fbase + c->nseg, sizeof(int),
+  cudaError_t e = cudaMemcpyAsync(&tot[0], d.fbase + c->ntiles, sizeof(int),
                                   cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(&tot[1], d.sbase + c->nseg, sizeof(int),
+    e = cudaMemcpyAsync(&tot[1], d.sbase + c->ntiles, sizeof(int),
                         cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;

@@ -1,8 +1,8 @@
-// Device building blocks of the step: neighbour lookup in the compact
-// fluid / solid-boundary spaces, the encoded phase field, the storage of the
-// post-recolouring populations and their rebuild, the pull of Eq. (1) with
-// halfway bounce-back, Zou-He (App. B), the wetting schemes (Eqs. 28-33) and
-// the collision (Eq. 2, single-rate form). All arithmetic is FP32.
+// Device building blocks of the step: coordinates, the encoded phase field,
+// the storage of the post-recolouring populations and their rebuild, Zou-He
+// (App. B), the wetting schemes (Eqs. 28-33) and the collision (Eq. 2,
+// single-rate form). All arithmetic is FP32. The neighbour lookup and the
+// pull of Eq. (1) are in tiles.cuh.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -42,33 +42,6 @@ __device__ __forceinline__ int axis_step(int v, int m, bool per, bool clamp,
     return m - 1;
   }
   return v;
-}
-
-struct Loc {
-  int cls;  // LBM_CLS_* of the node
-  int idx;  // F-space index (fluid) or S-space index (solid-boundary)
-};
-
-// Class and compact index of box node (X, Y, Z).
-__device__ __forceinline__ Loc locate(const Dom &d, int X, int Y, int Z) {
-  const int row = Y + d.ny * Z;
-  const uint16_t m = __ldg(d.map + (X + d.nx * row));
-  const int cls = m >> 8;
-  const int seg = (X >> 8) + d.spr * row;
-  const int base = __ldg(((cls & 2) ? d.fbase : d.sbase) + seg);
-  return Loc{cls, base + (m & 255)};
-}
-
-// Neighbour x + e of a node; `out` is set for an off-box neighbour on a
-// non-periodic axis unless clamp is true.
-__device__ __forceinline__ Loc neighbour(const Dom &d, int x, int y, int z,
-                                         int dx, int dy, int dz, bool clamp,
-                                         bool &out) {
-  const int X = axis_step(x + dx, d.nx, d.periodic & 1u, clamp, out);
-  const int Y = axis_step(y + dy, d.ny, d.periodic & 2u, clamp, out);
-  const int Z = axis_step(z + dz, d.nz, d.periodic & 4u, clamp, out);
-  if (out) return Loc{CLS_SOLID, -1};
-  return locate(d, X, Y, Z);
 }
 
 __device__ __forceinline__ bool is_fluid_cls(int c) { return c & 2; }
@@ -171,14 +144,11 @@ struct TIO<Q, LBM_STORAGE_BF16> {
 template <int Q>
 __device__ __forceinline__ void rebuild_ev(float T, float q, float ev, int i,
                                            float &fr, float &fb) {
-  const float w = Lattice<Q>::w(i);
-  if (m_blue(q)) {  // blue majority: red is the minority
-    fr = q * T + w * ev;
-    fb = T - fr;
-  } else {
-    fb = q * T - w * ev;
-    fr = T - fb;
-  }
+  const bool blue = m_blue(q);  // blue majority: red is the minority
+  const float minor = q * T + (blue ? Lattice<Q>::w(i) : -Lattice<Q>::w(i)) * ev;
+  const float major = T - minor;  // the minority keeps its relative accuracy
+  fr = blue ? minor : major;
+  fb = blue ? major : minor;
 }
 
 template <int Q>
@@ -188,35 +158,6 @@ __device__ __forceinline__ void rebuild(float T, float4 S, int i, float &fr,
                    (float)Lattice<Q>::ey(i) * S.z +
                    (float)Lattice<Q>::ez(i) * S.w;
   rebuild_ev<Q>(T, S.x, ev, i, fr, fb);
-}
-
-// --------------------------------------------------------------- pull
-// Eq. (1), propagation: f^s_i(x) = f^s_i'(x - e_i) when x - e_i is a fluid
-// node (periodic axes wrap), else the halfway bounce-back f^s_opp(i)'(x).
-// Branch-free: the source node and direction are selected, and since
-// e_opp(i) = -e_i and w_opp(i) = w_i the rebuild differs only in the sign
-// of e.v.
-template <int Q, int ST>
-__device__ __forceinline__ void pull(const Dom &d, int k, int x, int y, int z,
-                                     float4 Sown, float *fr, float *fb) {
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    if (i == 0) {
-      rebuild<Q>(TIO<Q, ST>::load(d, 0, k), Sown, 0, fr[0], fb[0]);
-      continue;
-    }
-    bool out = false;
-    const Loc L = neighbour(d, x, y, z, -Lattice<Q>::ex(i),
-                            -Lattice<Q>::ey(i), -Lattice<Q>::ez(i), false, out);
-    const bool fl = is_fluid_cls(L.cls);
-    const int src = fl ? L.idx : k;
-    const float T = TIO<Q, ST>::load_dyn(d, fl ? i : Lattice<Q>::opp(i), src);
-    const float4 S = __ldg(d.S_src + src);
-    const float ev = (float)Lattice<Q>::ex(i) * S.y +
-                     (float)Lattice<Q>::ey(i) * S.z +
-                     (float)Lattice<Q>::ez(i) * S.w;
-    rebuild_ev<Q>(T, S.x, fl ? ev : -ev, i, fr[i], fb[i]);
-  }
 }
 
 // ------------------------------------------------------------- Zou-He

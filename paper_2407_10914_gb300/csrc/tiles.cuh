@@ -1,0 +1,180 @@
+// Tiles of the box and the shared-memory neighbour table.
+//
+// The box is cut into tiles of TX x TY x TZ nodes (32 x 8 x 8 for D3Q19,
+// 64 x 32 x 1 for D2Q9). Fluid nodes are numbered tile by tile (F-space),
+// and within a tile in (z, y, x) order; solid-boundary nodes likewise
+// (S-space). The uint16 map over the box holds a node's class (bits 14-15)
+// and its rank among the nodes of its kind in its tile (bits 0-13); with the
+// per-tile bases fbase/sbase this gives its F- or S-index.
+//
+// One CTA works on one tile. It first stages, for the tile and a one-node
+// halo, an entry (class << 30 | index) per box position in shared memory
+// (OUT for a position off a non-periodic axis). Every lattice neighbour of a
+// tile node is then one shared-memory read at a compile-time offset.
+#pragma once
+
+#include "stencil.cuh"
+
+namespace lbm {
+
+template <int Q>
+struct Tile;
+
+template <>
+struct Tile<19> {
+  static constexpr int TX = 32, TY = 8, TZ = 8, LX = 5, LY = 3, LZ = 3;
+  static constexpr int RZ = 1;  // halo depth along z
+};
+
+template <>
+struct Tile<9> {
+  static constexpr int TX = 64, TY = 32, TZ = 1, LX = 6, LY = 5, LZ = 0;
+  static constexpr int RZ = 0;
+};
+
+template <int Q>
+struct TileGeo {
+  static constexpr int TX = Tile<Q>::TX, TY = Tile<Q>::TY, TZ = Tile<Q>::TZ;
+  static constexpr int RZ = Tile<Q>::RZ;
+  static constexpr int TN = TX * TY * TZ;
+  static constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2 * RZ;
+  static constexpr int HN = HX * HY * HZ;
+  // offset of the neighbour (dx, dy, dz) in the staged table
+  __host__ __device__ static constexpr int off(int dx, int dy, int dz) {
+    return dx + HX * (dy + HY * dz);
+  }
+  // staged position of the tile-local node (lx, ly, lz)
+  __device__ __forceinline__ static int pos(int lx, int ly, int lz) {
+    return (lx + 1) + HX * ((ly + 1) + HY * (lz + RZ));
+  }
+};
+
+constexpr uint32_t ENTRY_OUT = 0x3FFFFFFFu;  // class 0, no index
+__device__ __forceinline__ int entry_cls(uint32_t e) { return (int)(e >> 30); }
+__device__ __forceinline__ int entry_idx(uint32_t e) {
+  return (int)(e & 0x3FFFFFFFu);
+}
+
+// Tile number of box node (X, Y, Z).
+template <int Q>
+__device__ __forceinline__ int tile_of(const Dom &d, int X, int Y, int Z) {
+  return (X >> Tile<Q>::LX) +
+         d.ntx * ((Y >> Tile<Q>::LY) + d.nty * (Z >> Tile<Q>::LZ));
+}
+
+// Entry of box node (X, Y, Z) (inside the box).
+template <int Q>
+__device__ __forceinline__ uint32_t box_entry(const Dom &d, int X, int Y,
+                                              int Z) {
+  const uint16_t m = __ldg(d.map + (X + d.nx * (Y + d.ny * Z)));
+  const int cls = m >> 14;
+  const int t = tile_of<Q>(d, X, Y, Z);
+  const int base = __ldg(((cls & 2) ? d.fbase : d.sbase) + t);
+  return ((uint32_t)cls << 30) | (uint32_t)(base + (m & 0x3FFF));
+}
+
+// Stage the table of tile t into tab[HN]; list the tile's fluid and
+// solid-boundary nodes (tile-local linear positions) in fpos / spos by rank.
+// Returns the tile origin. Ends with __syncthreads().
+template <int Q>
+__device__ __forceinline__ void stage_tile(const Dom &d, int t, uint32_t *tab,
+                                           uint16_t *fpos, uint16_t *spos,
+                                           int &X0, int &Y0, int &Z0) {
+  using G = TileGeo<Q>;
+  const int ttx = t % d.ntx;
+  const int q = t / d.ntx;
+  const int tty = q % d.nty;
+  const int ttz = q / d.nty;
+  X0 = ttx * G::TX;
+  Y0 = tty * G::TY;
+  Z0 = ttz * G::TZ;
+  for (int p = threadIdx.x; p < G::HN; p += blockDim.x) {
+    const int hx = p % G::HX;
+    const int r = p / G::HX;
+    const int hy = r % G::HY;
+    const int hz = r / G::HY;
+    bool out = false;
+    const int xr = X0 + hx - 1, yr = Y0 + hy - 1, zr = Z0 + hz - G::RZ;
+    const int X = axis_step(xr, d.nx, d.periodic & 1u, false, out);
+    const int Y = axis_step(yr, d.ny, d.periodic & 2u, false, out);
+    const int Z = axis_step(zr, d.nz, d.periodic & 4u, false, out);
+    uint32_t e = ENTRY_OUT;
+    if (!out) e = box_entry<Q>(d, X, Y, Z);
+    tab[p] = e;
+    // members of this tile: interior positions inside the box, no wrap
+    const bool interior = hx >= 1 && hx <= G::TX && hy >= 1 && hy <= G::TY &&
+                          hz >= G::RZ && hz < G::TZ + G::RZ;
+    if (interior && !out && X == xr && Y == yr && Z == zr) {
+      const int c = entry_cls(e);
+      const uint16_t lp =
+          (uint16_t)((hx - 1) + G::TX * ((hy - 1) + G::TY * (hz - G::RZ)));
+      if (c & 2) {
+        fpos[entry_idx(e) - __ldg(d.fbase + t)] = lp;
+      } else if (c == CLS_SOLID_BND) {
+        spos[entry_idx(e) - __ldg(d.sbase + t)] = lp;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// Box coordinates and staged position of the tile-local node lp.
+template <int Q>
+__device__ __forceinline__ void local_node(int lp, int X0, int Y0, int Z0,
+                                           int &x, int &y, int &z, int &p0) {
+  using G = TileGeo<Q>;
+  const int lx = lp & (G::TX - 1);
+  const int ly = (lp >> Tile<Q>::LX) & (G::TY - 1);
+  const int lz = lp >> (Tile<Q>::LX + Tile<Q>::LY);
+  x = X0 + lx;
+  y = Y0 + ly;
+  z = Z0 + lz;
+  p0 = G::pos(lx, ly, lz);
+}
+
+// Entry of the neighbour x + e with off-box coordinates clamped to the box
+// (the zero-gradient rule of the stencils): the staged entry, or, where it
+// is OUT, the entry of the clamped position (also staged).
+template <int Q>
+__device__ __forceinline__ uint32_t clamped_entry(const Dom &d,
+                                                  const uint32_t *tab, int p0,
+                                                  int x, int y, int z, int dx,
+                                                  int dy, int dz) {
+  using G = TileGeo<Q>;
+  uint32_t e = tab[p0 + G::off(dx, dy, dz)];
+  if (e == ENTRY_OUT) {
+    const int cx = (x + dx < 0 || x + dx >= d.nx) ? 0 : dx;
+    const int cy = (y + dy < 0 || y + dy >= d.ny) ? 0 : dy;
+    const int cz = (z + dz < 0 || z + dz >= d.nz) ? 0 : dz;
+    e = tab[p0 + G::off(cx, cy, cz)];
+  }
+  return e;
+}
+
+// Eq. (1) propagation through the staged table: f^s_i(x) = f^s_i'(x - e_i)
+// from a fluid source, else the halfway bounce-back f^s_opp(i)'(x).
+template <int Q, int ST>
+__device__ __forceinline__ void pull_tab(const Dom &d, const uint32_t *tab,
+                                         int p0, int k, float4 Sown, float *fr,
+                                         float *fb) {
+  using G = TileGeo<Q>;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if (i == 0) {
+      rebuild<Q>(TIO<Q, ST>::load(d, 0, k), Sown, 0, fr[0], fb[0]);
+      continue;
+    }
+    const uint32_t e = tab[p0 + G::off(-Lattice<Q>::ex(i), -Lattice<Q>::ey(i),
+                                       -Lattice<Q>::ez(i))];
+    const bool fl = entry_cls(e) & 2;
+    const int src = fl ? entry_idx(e) : k;
+    const float T = TIO<Q, ST>::load_dyn(d, fl ? i : Lattice<Q>::opp(i), src);
+    const float4 S = fl ? __ldg(d.S_src + src) : Sown;
+    const float ev = (float)Lattice<Q>::ex(i) * S.y +
+                     (float)Lattice<Q>::ey(i) * S.z +
+                     (float)Lattice<Q>::ez(i) * S.w;
+    rebuild_ev<Q>(T, S.x, fl ? ev : -ev, i, fr[i], fb[i]);
+  }
+}
+
+}  // namespace lbm
