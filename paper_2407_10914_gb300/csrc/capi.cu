@@ -46,9 +46,10 @@ long long count_solid(const uint8_t *solid, long long N) {
 struct Layout {
   size_t TA, TB, SA, SB, mf, ncf, nw, fg, macro;  // F-space
   size_t ms, ncs, sg;                             // S-space
+  size_t nbf, nbs, fflag;                         // neighbour tables
   size_t map, cls, mask, fbase, sbase, cntf, cnts, g0, g1;
   size_t red, out, cnt, total;
-  long long NF, NFp, NS, ntiles;
+  long long NF, NFp, NS, NSp, ntiles;
   int ntx, nty, ntz;
 };
 
@@ -88,6 +89,10 @@ Layout make_layout(int Q, int nx, int ny, int nz, int storage, long long NF,
   L.ms = take(nsp * 4);
   L.ncs = take(nsp * 16);
   L.sg = take(nsp * 4);
+  L.NSp = (long long)nsp;
+  L.nbf = take((size_t)(Q - 1) * nfp * 4);
+  L.nbs = take((size_t)(Q - 1) * nsp * 4);
+  L.fflag = take(nfp);
   L.map = take((size_t)N * 2);
   L.cls = take((size_t)N);
   L.mask = take((size_t)N);
@@ -195,6 +200,10 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
   d.fg = (const int *)(base + L.fg);
   d.sg = (const int *)(base + L.sg);
   d.cls = (const uint8_t *)(base + L.cls);
+  d.nbf = (const uint32_t *)(base + L.nbf);
+  d.nbs = (const uint32_t *)(base + L.nbs);
+  d.NSp = L.NSp;
+  d.fflag = (const uint8_t *)(base + L.fflag);
   d.nw = (const float4 *)(base + L.nw);
   d.T_src = c->TA;
   d.T_dst = c->TB;

@@ -59,6 +59,12 @@ struct Dom {
   const int *fg;        // [NF] box index of fluid node k
   const int *sg;        // [NS] box index of solid-boundary node j
   const uint8_t *cls;   // [N]
+  // neighbour tables, one plane per direction i = 1..Q-1 (plane i - 1),
+  // entry = class << 30 | OUT << 29 | index (see tiles.cuh)
+  const uint32_t *nbf;  // [Q-1][NFp] of the fluid nodes
+  const uint32_t *nbs;  // [Q-1][NSp] of the solid-boundary nodes
+  long long NSp;        // stride of one S-space plane
+  const uint8_t *fflag; // [NF] bit0 fluid-boundary, bit1 inlet, bit2 outlet
   const float4 *nw;     // [NF] wall normal (fluid-boundary nodes), else 0
   const void *T_src;    // [Q][NFp] f'' (float32, or 16-bit offsets)
   void *T_dst;

@@ -174,6 +174,57 @@ __global__ void k_tile_map(Dom d, uint16_t *__restrict__ map,
   }
 }
 
+// One block per tile: per-node neighbour tables of the tile's fluid and
+// solid-boundary nodes, from the staged tile table. An off-box neighbour on
+// a non-periodic axis gets the entry of the clamped position with the OUT
+// bit. Node flags: bit 0 fluid-boundary; bit 1 + 2a / 2 + 2a the first /
+// last plane along axis a.
+template <int Q>
+__global__ void k_build_nbr(Dom d, uint32_t *__restrict__ nbf,
+                            uint32_t *__restrict__ nbs,
+                            uint8_t *__restrict__ fflag) {
+  using G = TileGeo<Q>;
+  __shared__ uint32_t tab[G::HN];
+  __shared__ uint16_t fpos[G::TN];
+  __shared__ uint16_t spos[G::TN];
+  const int t = blockIdx.x;
+  const int fb0 = d.fbase[t], nf = d.fbase[t + 1] - fb0;
+  const int sb0 = d.sbase[t], ns = d.sbase[t + 1] - sb0;
+  if (nf == 0 && ns == 0) return;
+  int X0, Y0, Z0;
+  stage_tile<Q>(d, t, tab, fpos, spos, X0, Y0, Z0);
+  for (int j = threadIdx.x; j < nf + ns; j += GBLOCK) {
+    const bool fluid = j < nf;
+    const int r = fluid ? j : j - nf;
+    int x, y, z, p0;
+    local_node<Q>(fluid ? fpos[r] : spos[r], X0, Y0, Z0, x, y, z, p0);
+    for (int i = 1; i < Q; ++i) {
+      const int dx = Lattice<Q>::ex(i), dy = Lattice<Q>::ey(i),
+                dz = Lattice<Q>::ez(i);
+      uint32_t e = tab[p0 + G::off(dx, dy, dz)];
+      if (e == ENTRY_OUT) {
+        const int cx = (x + dx < 0 || x + dx >= d.nx) ? 0 : dx;
+        const int cy = (y + dy < 0 || y + dy >= d.ny) ? 0 : dy;
+        const int cz = (z + dz < 0 || z + dz >= d.nz) ? 0 : dz;
+        e = tab[p0 + G::off(cx, cy, cz)] | OUT_BIT;
+      }
+      if (fluid)
+        nbf[(long long)(i - 1) * d.NFp + fb0 + r] = e;
+      else
+        nbs[(long long)(i - 1) * d.NSp + sb0 + r] = e;
+    }
+    if (fluid) {
+      uint8_t f = entry_cls(tab[p0]) == CLS_FLUID_BND ? 1u : 0u;
+      const int c[3] = {x, y, z}, n[3] = {d.nx, d.ny, d.nz};
+      for (int a = 0; a < 3; ++a) {
+        if (c[a] == 0) f |= (uint8_t)(2u << (2 * a));
+        if (c[a] == n[a] - 1) f |= (uint8_t)(4u << (2 * a));
+      }
+      fflag[fb0 + r] = f;
+    }
+  }
+}
+
 __global__ void k_indicator(long long N, const uint8_t *__restrict__ mask,
                             double *__restrict__ g) {
   const long long n = (long long)blockIdx.x * GBLOCK + threadIdx.x;
@@ -284,6 +335,15 @@ cudaError_t build_geometry(lbm_ctx *c, cudaStream_t s) {
   d.NS = tot[1];
   c->n_fluid = tot[0];
   c->n_sbnd = tot[1];
+  {
+    uint32_t *nbf = const_cast<uint32_t *>(d.nbf);
+    uint32_t *nbs = const_cast<uint32_t *>(d.nbs);
+    uint8_t *ff = const_cast<uint8_t *>(d.fflag);
+    if (c->Q == 19)
+      k_build_nbr<19><<<nt, GBLOCK, 0, s>>>(d, nbf, nbs, ff);
+    else
+      k_build_nbr<9><<<nt, GBLOCK, 0, s>>>(d, nbf, nbs, ff);
+  }
   // Eq. (25) three times, then Eq. (26) at the fluid-boundary nodes
   k_indicator<<<gN, GBLOCK, 0, s>>>(d.N, c->mask, c->g0);
   double *gi = c->g0, *go = c->g1;

@@ -49,11 +49,18 @@ struct TileGeo {
   }
 };
 
-constexpr uint32_t ENTRY_OUT = 0x3FFFFFFFu;  // class 0, no index
+// Entries: class << 30 | index (index < 2^29). A staged position off a
+// non-periodic axis holds ENTRY_OUT. In the per-node neighbour tables an
+// off-box neighbour holds the entry of the clamped position (the stencils'
+// zero-gradient rule) with the OUT bit set (the pull bounces back, the
+// extrapolations skip it).
+constexpr uint32_t ENTRY_OUT = 0x3FFFFFFFu;  // class 0, staging only
+constexpr uint32_t OUT_BIT = 1u << 29;
 __device__ __forceinline__ int entry_cls(uint32_t e) { return (int)(e >> 30); }
 __device__ __forceinline__ int entry_idx(uint32_t e) {
-  return (int)(e & 0x3FFFFFFFu);
+  return (int)(e & 0x1FFFFFFFu);
 }
+__device__ __forceinline__ bool entry_out(uint32_t e) { return e & OUT_BIT; }
 
 // Tile number of box node (X, Y, Z).
 template <int Q>
@@ -151,22 +158,21 @@ __device__ __forceinline__ uint32_t clamped_entry(const Dom &d,
   return e;
 }
 
-// Eq. (1) propagation through the staged table: f^s_i(x) = f^s_i'(x - e_i)
-// from a fluid source, else the halfway bounce-back f^s_opp(i)'(x).
+// Eq. (1) propagation through the neighbour table: f^s_i(x) = f^s_i'(x - e_i)
+// from a fluid source (entry of direction opp(i), which points to x - e_i),
+// else the halfway bounce-back f^s_opp(i)'(x).
 template <int Q, int ST>
-__device__ __forceinline__ void pull_tab(const Dom &d, const uint32_t *tab,
-                                         int p0, int k, float4 Sown, float *fr,
-                                         float *fb) {
-  using G = TileGeo<Q>;
+__device__ __forceinline__ void pull_nb(const Dom &d, int k, float4 Sown,
+                                        float *fr, float *fb) {
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     if (i == 0) {
       rebuild<Q>(TIO<Q, ST>::load(d, 0, k), Sown, 0, fr[0], fb[0]);
       continue;
     }
-    const uint32_t e = tab[p0 + G::off(-Lattice<Q>::ex(i), -Lattice<Q>::ey(i),
-                                       -Lattice<Q>::ez(i))];
-    const bool fl = entry_cls(e) & 2;
+    const uint32_t e =
+        __ldg(d.nbf + (long long)(Lattice<Q>::opp(i) - 1) * d.NFp + k);
+    const bool fl = (entry_cls(e) & 2) && !entry_out(e);
     const int src = fl ? entry_idx(e) : k;
     const float T = TIO<Q, ST>::load_dyn(d, fl ? i : Lattice<Q>::opp(i), src);
     const float4 S = fl ? __ldg(d.S_src + src) : Sown;
@@ -174,6 +180,38 @@ __device__ __forceinline__ void pull_tab(const Dom &d, const uint32_t *tab,
                      (float)Lattice<Q>::ey(i) * S.z +
                      (float)Lattice<Q>::ez(i) * S.w;
     rebuild_ev<Q>(T, S.x, fl ? ev : -ev, i, fr[i], fb[i]);
+  }
+}
+
+// The same pull reduced to what the collision needs away from Zou-He
+// planes: f^t_i = f^r_i + f^b_i (which is f''_i of the source, no colour
+// rebuild) and the colour densities rho^r, rho^b (the rebuilt colours
+// summed as they arrive), so no per-colour arrays stay live.
+template <int Q, int ST>
+__device__ __forceinline__ void pull_sums(const Dom &d, int k, float4 Sown,
+                                          float *ft, float &rr, float &rb) {
+  rr = 0.f;
+  rb = 0.f;
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    float fr, fb;
+    if (i == 0) {
+      ft[0] = TIO<Q, ST>::load(d, 0, k);
+      rebuild<Q>(ft[0], Sown, 0, fr, fb);
+    } else {
+      const uint32_t e =
+          __ldg(d.nbf + (long long)(Lattice<Q>::opp(i) - 1) * d.NFp + k);
+      const bool fl = (entry_cls(e) & 2) && !entry_out(e);
+      const int src = fl ? entry_idx(e) : k;
+      ft[i] = TIO<Q, ST>::load_dyn(d, fl ? i : Lattice<Q>::opp(i), src);
+      const float4 S = fl ? __ldg(d.S_src + src) : Sown;
+      const float ev = (float)Lattice<Q>::ex(i) * S.y +
+                       (float)Lattice<Q>::ey(i) * S.z +
+                       (float)Lattice<Q>::ez(i) * S.w;
+      rebuild_ev<Q>(ft[i], S.x, fl ? ev : -ev, i, fr, fb);
+    }
+    rr += fr;
+    rb += fb;
   }
 }
 
