@@ -46,7 +46,7 @@ long long count_solid(const uint8_t *solid, long long N) {
 struct Layout {
   size_t TA, TB, SA, SB, mf, ncf, nw, fg, macro;  // F-space
   size_t ms, ncs, sg;                             // S-space
-  size_t nbf, nbs, fflag;                         // neighbour tables
+  size_t nbf, nbs, fflag, zh;                     // neighbour tables
   size_t map, cls, mask, fbase, sbase, cntf, cnts, g0, g1;
   size_t red, out, cnt, total;
   long long NF, NFp, NS, NSp, ntiles;
@@ -93,6 +93,7 @@ Layout make_layout(int Q, int nx, int ny, int nz, int storage, long long NF,
   L.nbf = take((size_t)(Q - 1) * nfp * 4);
   L.nbs = take((size_t)(Q - 1) * nsp * 4);
   L.fflag = take(nfp);
+  L.zh = take(3 * nfp * 4);
   L.map = take((size_t)N * 2);
   L.cls = take((size_t)N);
   L.mask = take((size_t)N);
@@ -204,6 +205,9 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
   d.nbs = (const uint32_t *)(base + L.nbs);
   d.NSp = L.NSp;
   d.fflag = (const uint8_t *)(base + L.fflag);
+  c->zh_lists = (int *)(base + L.zh);
+  d.zh_list = c->zh_lists;
+  d.n_zh = 0;
   d.nw = (const float4 *)(base + L.nw);
   d.T_src = c->TA;
   d.T_dst = c->TB;
@@ -266,6 +270,8 @@ lbm_status lbm_set_params(lbm_handle c, const lbm_params *p) {
   k.wetting = p->wetting;
   k.zou_he = p->zou_he;
   k.axis = p->flow_axis;
+  c->d.zh_list = c->zh_lists + (size_t)p->flow_axis * c->d.NFp;
+  c->d.n_zh = p->zou_he ? (int)c->zh_count[p->flow_axis] : 0;
   k.rho_in_r = (float)(p->rho_in * p->zeta_r);
   k.rho_in_b = (float)(p->rho_in * (1.0 - p->zeta_r));
   k.rho_out = (float)p->rho_out;

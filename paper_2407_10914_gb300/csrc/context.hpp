@@ -64,7 +64,10 @@ struct Dom {
   const uint32_t *nbf;  // [Q-1][NFp] of the fluid nodes
   const uint32_t *nbs;  // [Q-1][NSp] of the solid-boundary nodes
   long long NSp;        // stride of one S-space plane
-  const uint8_t *fflag; // [NF] bit0 fluid-boundary, bit1 inlet, bit2 outlet
+  const uint8_t *fflag; // [NF] bit 0 fluid-boundary; bit 1+2a / 2+2a: on the
+                        // first / last plane along axis a
+  const int *zh_list;   // fluid nodes of the two Zou-He planes of the axis
+  int n_zh;
   const float4 *nw;     // [NF] wall normal (fluid-boundary nodes), else 0
   const void *T_src;    // [Q][NFp] f'' (float32, or 16-bit offsets)
   void *T_dst;
@@ -101,5 +104,7 @@ struct lbm_ctx {
   double *red_out = nullptr;              // 4 doubles: the combined partials
   int red_slots = 0;
   unsigned long long *counters = nullptr;
+  int *zh_lists = nullptr;                // [3][NFp]: plane nodes per axis
+  long long zh_count[3] = {0, 0, 0};
   char err[256] = {0};
 };

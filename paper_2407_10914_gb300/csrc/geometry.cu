@@ -225,6 +225,20 @@ __global__ void k_build_nbr(Dom d, uint32_t *__restrict__ nbf,
   }
 }
 
+// Fluid nodes on the first or last plane of each axis (the Zou-He planes
+// of that axis), appended to one list per axis; the order is irrelevant.
+__global__ void k_zh_lists(Dom d, int *__restrict__ lists, long long stride,
+                           unsigned long long *__restrict__ counts) {
+  const int k = blockIdx.x * GBLOCK + threadIdx.x;
+  if (k >= d.NF) return;
+  const uint8_t f = d.fflag[k];
+  for (int a = 0; a < 3; ++a)
+    if (f & (6u << (2 * a))) {
+      const unsigned long long at = atomicAdd(&counts[1 + a], 1ull);
+      lists[a * stride + (long long)at] = k;
+    }
+}
+
 __global__ void k_indicator(long long N, const uint8_t *__restrict__ mask,
                             double *__restrict__ g) {
   const long long n = (long long)blockIdx.x * GBLOCK + threadIdx.x;
@@ -365,11 +379,13 @@ cudaError_t build_geometry(lbm_ctx *c, cudaStream_t s) {
   e = cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   k_count_fbnd<<<gF, GBLOCK, 0, s>>>(d, c->counters);
-  unsigned long long nfb = 0;
-  e = cudaMemcpyAsync(&nfb, c->counters, sizeof(nfb), cudaMemcpyDeviceToHost, s);
+  k_zh_lists<<<gF, GBLOCK, 0, s>>>(d, c->zh_lists, d.NFp, c->counters);
+  unsigned long long h4[4] = {0, 0, 0, 0};
+  e = cudaMemcpyAsync(h4, c->counters, sizeof(h4), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;
-  c->n_fbnd = (long long)nfb;
+  c->n_fbnd = (long long)h4[0];
+  for (int a = 0; a < 3; ++a) c->zh_count[a] = (long long)h4[1 + a];
   return cudaGetLastError();
 }
 

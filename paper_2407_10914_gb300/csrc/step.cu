@@ -206,15 +206,16 @@ __global__ void __launch_bounds__(BLOCK, 4) k_collide(Dom d) {
   collide_store<Q, ST, MACROS>(d, k, kappa, c4, ft, rr, rb, m_phi(d.mf[k]));
 }
 
-// The same for the nodes of the Zou-He inlet and outlet planes, with the
-// populations rebuilt per colour by Appendix B before the collision.
+// The same for the nodes of the Zou-He inlet and outlet planes (one thread
+// per node of their list), with the populations rebuilt per colour by
+// Appendix B before the collision.
 template <int Q, int ST, bool MACROS>
 __global__ void __launch_bounds__(BLOCK) k_collide_zh(Dom d) {
-  const int k = blockIdx.x * BLOCK + threadIdx.x;
-  if (k >= d.NF) return;
+  const int j = blockIdx.x * BLOCK + threadIdx.x;
+  if (j >= d.n_zh) return;
+  const int k = __ldg(d.zh_list + j);
   const int a = d.c.axis;
   const uint8_t fl = __ldg(d.fflag + k);
-  if (!(fl & (6u << (2 * a)))) return;
   float4 c4;
   const float kappa = curvature<Q>(d, k, c4);
   float fr[Q], fb[Q];
@@ -247,12 +248,13 @@ static void launch_step_t(const Dom &d, cudaStream_t s, bool macros,
   if (ev) cudaEventRecord(ev[3], s);
   if (d.NS > 0) k_nc_solid<Q><<<gs, BLOCK, 0, s>>>(d);
   if (ev) cudaEventRecord(ev[4], s);
+  const unsigned gz = (unsigned)((d.n_zh + BLOCK - 1) / BLOCK);
   if (macros) {
     k_collide<Q, ST, true><<<g, BLOCK, 0, s>>>(d);
-    if (d.c.zou_he) k_collide_zh<Q, ST, true><<<g, BLOCK, 0, s>>>(d);
+    if (d.n_zh > 0) k_collide_zh<Q, ST, true><<<gz, BLOCK, 0, s>>>(d);
   } else {
     k_collide<Q, ST, false><<<g, BLOCK, 0, s>>>(d);
-    if (d.c.zou_he) k_collide_zh<Q, ST, false><<<g, BLOCK, 0, s>>>(d);
+    if (d.n_zh > 0) k_collide_zh<Q, ST, false><<<gz, BLOCK, 0, s>>>(d);
   }
   if (ev) cudaEventRecord(ev[5], s);
 }
