@@ -44,7 +44,7 @@ long long count_solid(const uint8_t *solid, long long N) {
 
 // Byte offsets of every buffer inside the caller's workspace.
 struct Layout {
-  size_t TA, TB, SA, SB, mf, ncf, nw, fg, macro;  // F-space
+  size_t TA, TB, U, R, SA, SB, mf, ncf, nw, fg, macro;  // F-space
   size_t ms, ncs, sg;                             // S-space
   size_t nbf, nbs, fflag, zh;                     // neighbour tables
   size_t map, cls, mask, fbase, sbase, cntf, cnts, g0, g1;
@@ -79,6 +79,8 @@ Layout make_layout(int Q, int nx, int ny, int nz, int storage, long long NF,
   const size_t nfp = (size_t)L.NFp, nsp = (size_t)pad64(NS > 0 ? NS : 1);
   L.TA = take(tb);
   L.TB = take(tb);
+  L.U = take(tb);
+  L.R = take(nfp * 8);
   L.SA = take(nfp * 16);
   L.SB = take(nfp * 16);
   L.mf = take(nfp * 4);
@@ -209,6 +211,8 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
   d.zh_list = c->zh_lists;
   d.n_zh = 0;
   d.nw = (const float4 *)(base + L.nw);
+  d.U = base + L.U;
+  d.R = (float2 *)(base + L.R);
   d.T_src = c->TA;
   d.T_dst = c->TB;
   d.S_src = c->SA;

@@ -71,6 +71,8 @@ struct Dom {
   const float4 *nw;     // [NF] wall normal (fluid-boundary nodes), else 0
   const void *T_src;    // [Q][NFp] f'' (float32, or 16-bit offsets)
   void *T_dst;
+  void *U;              // [Q][NFp] f^t after streaming and App. B (as T)
+  float2 *R;            // [NF] (rho^r, rho^b) after streaming and App. B
   const float4 *S_src;  // [NF] (q, v)
   float4 *S_dst;
   float *mf;            // [NF] encoded phase field

@@ -87,8 +87,13 @@ struct TIO;
 
 template <int Q>
 struct TIO<Q, LBM_STORAGE_FP32> {
+  __device__ __forceinline__ static float load_from(const Dom &d,
+                                                   const void *buf, int i,
+                                                   int k) {
+    return __ldg((const float *)buf + (long long)i * d.NFp + k);
+  }
   __device__ __forceinline__ static float load(const Dom &d, int i, int k) {
-    return __ldg((const float *)d.T_src + (long long)i * d.NFp + k);
+    return load_from(d, d.T_src, i, k);
   }
   // plane p chosen at run time, p in {i, opp(i)} (equal weights)
   __device__ __forceinline__ static float load_dyn(const Dom &d, int p, int k) {
@@ -102,9 +107,14 @@ struct TIO<Q, LBM_STORAGE_FP32> {
 
 template <int Q>
 struct TIO<Q, LBM_STORAGE_FP16> {
-  __device__ __forceinline__ static float load(const Dom &d, int i, int k) {
-    const __half h = ((const __half *)d.T_src)[(long long)i * d.NFp + k];
+  __device__ __forceinline__ static float load_from(const Dom &d,
+                                                   const void *buf, int i,
+                                                   int k) {
+    const __half h = ((const __half *)buf)[(long long)i * d.NFp + k];
     return Lattice<Q>::w(i) * (__half2float(h) + d.c.rho0);
+  }
+  __device__ __forceinline__ static float load(const Dom &d, int i, int k) {
+    return load_from(d, d.T_src, i, k);
   }
   // plane p at run time with the weight of w(p) = w(i) supplied by caller's i
   __device__ __forceinline__ static float load_dyn(const Dom &d, int p, int k) {
@@ -120,10 +130,15 @@ struct TIO<Q, LBM_STORAGE_FP16> {
 
 template <int Q>
 struct TIO<Q, LBM_STORAGE_BF16> {
-  __device__ __forceinline__ static float load(const Dom &d, int i, int k) {
+  __device__ __forceinline__ static float load_from(const Dom &d,
+                                                   const void *buf, int i,
+                                                   int k) {
     const __nv_bfloat16 h =
-        ((const __nv_bfloat16 *)d.T_src)[(long long)i * d.NFp + k];
+        ((const __nv_bfloat16 *)buf)[(long long)i * d.NFp + k];
     return Lattice<Q>::w(i) * (__bfloat162float(h) + d.c.rho0);
+  }
+  __device__ __forceinline__ static float load(const Dom &d, int i, int k) {
+    return load_from(d, d.T_src, i, k);
   }
   __device__ __forceinline__ static float load_dyn(const Dom &d, int p, int k) {
     const __nv_bfloat16 h =

@@ -1,13 +1,14 @@
 // The time step as five dependent passes. Each pass needs the previous one's
 // values at lattice neighbours:
-//   1 k_phase      (fluid)  pull + Zou-He + Eqs. (7)-(9), inlet/outlet phi
+//   1 k_stream     (fluid)  pull of Eq. (1), App. B on the Zou-He planes
+//                  (k_stream_zh), Eqs. (7)-(9): stores f^t, (rho^r, rho^b)
+//                  and the phase field
 //   2 k_phi_solid  (solid-boundary) Eq. (34)
 //   3 k_gradient   (fluid)  Eqs. (6), (27) and wetting, Eqs. (28)-(33)
 //   4 k_nc_solid   (solid-boundary) Eq. (35)
-//   5 k_collide    (fluid)  Eq. (12), (5), (36); pull again; Eq. (2)
-//                  single-rate; store f'' and (q, v), i.e. the recoloured
-//                  state of Eqs. (20)-(21); k_collide_zh does the same for
-//                  the Zou-He planes with App. B applied first
+//   5 k_collide    (fluid)  Eq. (12), (5), (36); Eq. (2) single-rate on the
+//                  stored f^t; store f'' and (q, v), i.e. the recoloured
+//                  state of Eqs. (20)-(21)
 // One thread per node of the compact fluid (F) or solid-boundary (S) list;
 // every lattice neighbour is one entry of the node's precomputed neighbour
 // table (built at set-up, geometry.cu).
@@ -28,35 +29,65 @@ __device__ __forceinline__ uint32_t nb_s(const Dom &d, int dir, int j) {
 }
 
 template <int Q, int ST>
-__device__ __forceinline__ float phase_of(const Dom &d, int k) {
-  float ft[Q], rr, rb;
-  pull_sums<Q, ST>(d, k, __ldg(d.S_src + k), ft, rr, rb);
-  return m_of(rr, rb);
+__device__ __forceinline__ void store_streamed(const Dom &d, int k,
+                                               const float *ft, float rr,
+                                               float rb, float m) {
+#pragma unroll
+  for (int i = 0; i < Q; ++i) TIO<Q, ST>::store(d, d.U, i, k, ft[i]);
+  d.R[k] = make_float2(rr, rb);
+  d.mf[k] = m;
 }
 
-// Encoded phase field of a fluid node from its streamed populations, with
-// the Zou-He overrides: zeta^r - zeta^b on the inlet plane; on the outlet
-// plane phi(x - a), Eq. (39), from the streamed populations of that node
-// (the node's own value if that node is solid).
+// Streamed populations of a fluid node off the Zou-He planes (Eq. 1), their
+// colour densities and the encoded phase field (Eqs. 7-9).
 template <int Q, int ST>
-__global__ void __launch_bounds__(BLOCK) k_phase(Dom d) {
+__global__ void __launch_bounds__(BLOCK) k_stream(Dom d) {
   const int k = blockIdx.x * BLOCK + threadIdx.x;
   if (k >= d.NF) return;
-  if (d.c.zou_he) {
-    const int a = d.c.axis;
-    const uint8_t fl = __ldg(d.fflag + k);
-    if (fl & (2u << (2 * a))) {
-      d.mf[k] = d.c.m_in;
-      return;
+  if (d.c.zou_he && (__ldg(d.fflag + k) & (6u << (2 * d.c.axis)))) return;
+  float ft[Q], rr, rb;
+  pull_sums<Q, ST>(d, k, __ldg(d.S_src + k), ft, rr, rb);
+  store_streamed<Q, ST>(d, k, ft, rr, rb, m_of(rr, rb));
+}
+
+// The same on the Zou-He planes (one thread per node of their list): the
+// per-colour unknowns of App. B, then the sums. The phase field there is
+// zeta^r - zeta^b on the inlet plane and, on the outlet plane, phi(x - a)
+// (Eq. 39) from the streamed populations of that node (the node's own if
+// that node is solid); the outlet's chi^s of (B.12)-(B.13) use it.
+template <int Q, int ST>
+__global__ void __launch_bounds__(BLOCK) k_stream_zh(Dom d) {
+  const int j = blockIdx.x * BLOCK + threadIdx.x;
+  if (j >= d.n_zh) return;
+  const int k = __ldg(d.zh_list + j);
+  const int a = d.c.axis;
+  const uint8_t fl = __ldg(d.fflag + k);
+  const float4 Sown = __ldg(d.S_src + k);
+  float fr[Q], fb[Q];
+  pull_nb<Q, ST>(d, k, Sown, fr, fb);
+  float m;
+  if (fl & (2u << (2 * a))) {
+    m = d.c.m_in;
+    zou_he_inlet<Q>(fr, d.c.rho_in_r, a);
+    zou_he_inlet<Q>(fb, d.c.rho_in_b, a);
+  } else {
+    const uint32_t e = nb_f(d, 2 * a + 2, k);  // the node at x - a
+    float rr, rb;
+    if ((entry_cls(e) & 2) && !entry_out(e)) {
+      float ft[Q];
+      const int kb = entry_idx(e);
+      pull_sums<Q, ST>(d, kb, __ldg(d.S_src + kb), ft, rr, rb);
+    } else {
+      sum_colours<Q>(fr, fb, rr, rb);
     }
-    if (fl & (4u << (2 * a))) {
-      const uint32_t e = nb_f(d, 2 * a + 2, k);  // the node at x - a
-      const bool behind = (entry_cls(e) & 2) && !entry_out(e);
-      d.mf[k] = phase_of<Q, ST>(d, behind ? entry_idx(e) : k);
-      return;
-    }
+    m = m_of(rr, rb);
+    zou_he_outlet<Q>(fr, fb, d.c.rho_out, m_phi(m), a);
   }
-  d.mf[k] = phase_of<Q, ST>(d, k);
+  float rr, rb;
+  sum_colours<Q>(fr, fb, rr, rb);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) fr[i] += fb[i];  // f^t
+  store_streamed<Q, ST>(d, k, fr, rr, rb, m);
 }
 
 // Eq. (34): phi at a solid-boundary node = w-weighted mean over its fluid
@@ -173,18 +204,27 @@ __device__ __forceinline__ float curvature(const Dom &d, int k, float4 &c4) {
 }
 
 // Eq. (5) F = 1/2 gamma kappa C (C = |C| n_c) plus rho g (Eq. 36), the
-// collision of f^t, and the store of the recoloured state: f''_i and (q, v)
-// with q the encoded rho^r/rho and v = beta rho^r rho^b / rho n (Eqs. 20-21).
+// collision (Eq. 2) of the stored f^t, and the store of the recoloured
+// state: f''_i and (q, v) with q the encoded rho^r/rho and
+// v = beta rho^r rho^b / rho n (Eqs. 20-21). The relaxation rate follows
+// the node's phase field (Eq. 39's value on the outlet plane).
 template <int Q, int ST, bool MACROS>
-__device__ __forceinline__ void collide_store(const Dom &d, int k, float kappa,
-                                              float4 c4, float *ft, float rr,
-                                              float rb, float phi) {
+__global__ void __launch_bounds__(BLOCK, 4) k_collide(Dom d) {
+  const int k = blockIdx.x * BLOCK + threadIdx.x;
+  if (k >= d.NF) return;
+  float4 c4;
+  const float kappa = curvature<Q>(d, k, c4);
+  float ft[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) ft[i] = TIO<Q, ST>::load_from(d, d.U, i, k);
+  const float2 R = d.R[k];
+  const float rr = R.x, rb = R.y;
   const float rho = rr + rb;
   const float hk = 0.5f * d.c.gamma * kappa * c4.w;
   const float F[3] = {hk * c4.x + rho * d.c.g[0], hk * c4.y + rho * d.c.g[1],
                       hk * c4.z + rho * d.c.g[2]};
   float u[3];
-  collide<Q>(d.c, ft, rho, F, phi, u);
+  collide<Q>(d.c, ft, rho, F, m_phi(d.mf[k]), u);
 #pragma unroll
   for (int i = 0; i < Q; ++i) TIO<Q, ST>::store(d, d.T_dst, i, k, ft[i]);
   const float seg = d.c.beta * rr * rb / rho;
@@ -192,55 +232,15 @@ __device__ __forceinline__ void collide_store(const Dom &d, int k, float kappa,
   if (MACROS) d.macro[k] = make_float4(u[0], u[1], u[2], rho);
 }
 
-// Curvature, force, collision and recolouring of every fluid node off the
-// Zou-He planes (those are k_collide_zh's).
-template <int Q, int ST, bool MACROS>
-__global__ void __launch_bounds__(BLOCK, 4) k_collide(Dom d) {
-  const int k = blockIdx.x * BLOCK + threadIdx.x;
-  if (k >= d.NF) return;
-  if (d.c.zou_he && (__ldg(d.fflag + k) & (6u << (2 * d.c.axis)))) return;
-  float4 c4;
-  const float kappa = curvature<Q>(d, k, c4);
-  float ft[Q], rr, rb;
-  pull_sums<Q, ST>(d, k, __ldg(d.S_src + k), ft, rr, rb);
-  collide_store<Q, ST, MACROS>(d, k, kappa, c4, ft, rr, rb, m_phi(d.mf[k]));
-}
-
-// The same for the nodes of the Zou-He inlet and outlet planes (one thread
-// per node of their list), with the populations rebuilt per colour by
-// Appendix B before the collision.
-template <int Q, int ST, bool MACROS>
-__global__ void __launch_bounds__(BLOCK) k_collide_zh(Dom d) {
-  const int j = blockIdx.x * BLOCK + threadIdx.x;
-  if (j >= d.n_zh) return;
-  const int k = __ldg(d.zh_list + j);
-  const int a = d.c.axis;
-  const uint8_t fl = __ldg(d.fflag + k);
-  float4 c4;
-  const float kappa = curvature<Q>(d, k, c4);
-  float fr[Q], fb[Q];
-  pull_nb<Q, ST>(d, k, __ldg(d.S_src + k), fr, fb);
-  const float phi = m_phi(d.mf[k]);
-  if (fl & (2u << (2 * a))) {
-    zou_he_inlet<Q>(fr, d.c.rho_in_r, a);
-    zou_he_inlet<Q>(fb, d.c.rho_in_b, a);
-  } else {
-    zou_he_outlet<Q>(fr, fb, d.c.rho_out, phi, a);
-  }
-  float rr, rb;
-  sum_colours<Q>(fr, fb, rr, rb);
-#pragma unroll
-  for (int i = 0; i < Q; ++i) fr[i] += fb[i];  // f^t
-  collide_store<Q, ST, MACROS>(d, k, kappa, c4, fr, rr, rb, phi);
-}
-
 template <int Q, int ST>
 static void launch_step_t(const Dom &d, cudaStream_t s, bool macros,
                           cudaEvent_t *ev) {
   const unsigned g = (unsigned)((d.NF + BLOCK - 1) / BLOCK);
   const unsigned gs = (unsigned)((d.NS + BLOCK - 1) / BLOCK);
+  const unsigned gz = (unsigned)((d.n_zh + BLOCK - 1) / BLOCK);
   if (ev) cudaEventRecord(ev[0], s);
-  k_phase<Q, ST><<<g, BLOCK, 0, s>>>(d);
+  k_stream<Q, ST><<<g, BLOCK, 0, s>>>(d);
+  if (d.n_zh > 0) k_stream_zh<Q, ST><<<gz, BLOCK, 0, s>>>(d);
   if (ev) cudaEventRecord(ev[1], s);
   if (d.NS > 0) k_phi_solid<Q><<<gs, BLOCK, 0, s>>>(d);
   if (ev) cudaEventRecord(ev[2], s);
@@ -248,14 +248,10 @@ static void launch_step_t(const Dom &d, cudaStream_t s, bool macros,
   if (ev) cudaEventRecord(ev[3], s);
   if (d.NS > 0) k_nc_solid<Q><<<gs, BLOCK, 0, s>>>(d);
   if (ev) cudaEventRecord(ev[4], s);
-  const unsigned gz = (unsigned)((d.n_zh + BLOCK - 1) / BLOCK);
-  if (macros) {
+  if (macros)
     k_collide<Q, ST, true><<<g, BLOCK, 0, s>>>(d);
-    if (d.n_zh > 0) k_collide_zh<Q, ST, true><<<gz, BLOCK, 0, s>>>(d);
-  } else {
+  else
     k_collide<Q, ST, false><<<g, BLOCK, 0, s>>>(d);
-    if (d.n_zh > 0) k_collide_zh<Q, ST, false><<<gz, BLOCK, 0, s>>>(d);
-  }
   if (ev) cudaEventRecord(ev[5], s);
 }
 
