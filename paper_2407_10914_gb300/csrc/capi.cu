@@ -46,10 +46,10 @@ long long count_solid(const uint8_t *solid, long long N) {
 struct Layout {
   size_t TA, TB, U, R, SA, SB, mf, ncf, nw, fg, macro;  // F-space
   size_t ms, ncs, sg;                             // S-space
-  size_t nbf, nbs, fflag, zh;                     // neighbour tables
+  size_t nbf, soff, slink, fflag, zh;             // neighbour lookup
   size_t map, cls, mask, fbase, sbase, cntf, cnts, g0, g1;
   size_t red, out, cnt, total;
-  long long NF, NFp, NS, NSp, ntiles;
+  long long NF, NFp, NS, ntiles;
   int ntx, nty, ntz;
 };
 
@@ -91,9 +91,9 @@ Layout make_layout(int Q, int nx, int ny, int nz, int storage, long long NF,
   L.ms = take(nsp * 4);
   L.ncs = take(nsp * 16);
   L.sg = take(nsp * 4);
-  L.NSp = (long long)nsp;
   L.nbf = take((size_t)(Q - 1) * nfp * 4);
-  L.nbs = take((size_t)(Q - 1) * nsp * 4);
+  L.soff = take((nsp + 1) * 4);
+  L.slink = take((size_t)(Q - 1) * nsp * 4);  // bound: Q - 1 links a node
   L.fflag = take(nfp);
   L.zh = take(3 * nfp * 4);
   L.map = take((size_t)N * 2);
@@ -204,8 +204,8 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
   d.sg = (const int *)(base + L.sg);
   d.cls = (const uint8_t *)(base + L.cls);
   d.nbf = (const uint32_t *)(base + L.nbf);
-  d.nbs = (const uint32_t *)(base + L.nbs);
-  d.NSp = L.NSp;
+  d.soff = (const int *)(base + L.soff);
+  d.slink = (const uint32_t *)(base + L.slink);
   d.fflag = (const uint8_t *)(base + L.fflag);
   c->zh_lists = (int *)(base + L.zh);
   d.zh_list = c->zh_lists;
@@ -222,8 +222,13 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
   d.ncf = (float4 *)(base + L.ncf);
   d.ncs = (float4 *)(base + L.ncs);
   d.macro = (float4 *)(base + L.macro);
-  cudaError_t e = cudaMemcpyAsync(c->mask, solid_host, (size_t)N,
-                                  cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaStreamCreateWithFlags(&c->side.s, cudaStreamNonBlocking);
+  if (e == cudaSuccess)
+    e = cudaEventCreateWithFlags(&c->side.fork, cudaEventDisableTiming);
+  if (e == cudaSuccess)
+    e = cudaEventCreateWithFlags(&c->side.join, cudaEventDisableTiming);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->mask, solid_host, (size_t)N, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = lbm::build_geometry(c, s);
   if (e != cudaSuccess) {
     delete c;
@@ -309,7 +314,7 @@ lbm_status lbm_step(lbm_handle c, int nsteps, void *stream) {
   if (!c->state_set) return fail(c, LBM_ERR_STATE, "init the state first");
   cudaStream_t s = (cudaStream_t)stream;
   for (int k = 0; k < nsteps; ++k) {
-    lbm::launch_step(c->Q, c->storage, c->d, s, k == nsteps - 1);
+    lbm::launch_step(c->Q, c->storage, c->d, s, c->side, k == nsteps - 1);
     swap_buffers(c);
   }
   cudaError_t e = cudaGetLastError();
@@ -331,7 +336,8 @@ lbm_status lbm_step_timed(lbm_handle c, int nsteps, void *stream,
     return cuda_fail(c, e, "step_timed events");
   }
   for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
-    lbm::launch_step_events(c->Q, c->storage, c->d, s, k == nsteps - 1, ev);
+    lbm::launch_step_events(c->Q, c->storage, c->d, s, c->side, k == nsteps - 1,
+                            ev);
     swap_buffers(c);
     e = cudaEventSynchronize(ev[5]);
     for (int p = 0; p < 5 && e == cudaSuccess; ++p) {

@@ -62,8 +62,11 @@ struct Dom {
   // neighbour tables, one plane per direction i = 1..Q-1 (plane i - 1),
   // entry = class << 30 | OUT << 29 | index (see tiles.cuh)
   const uint32_t *nbf;  // [Q-1][NFp] of the fluid nodes
-  const uint32_t *nbs;  // [Q-1][NSp] of the solid-boundary nodes
-  long long NSp;        // stride of one S-space plane
+  // fluid lattice neighbours of the solid-boundary nodes (the terms of
+  // Eqs. 34-35), node j's at [soff[j], soff[j+1]): F-index, bit 31 set for
+  // a diagonal direction (weight w_diag instead of w_axis)
+  const int *soff;         // [NS + 1]
+  const uint32_t *slink;
   const uint8_t *fflag; // [NF] bit 0 fluid-boundary; bit 1+2a / 2+2a: on the
                         // first / last plane along axis a
   const int *zh_list;   // fluid nodes of the two Zou-He planes of the axis
@@ -83,6 +86,15 @@ struct Dom {
   StepConst c;
 };
 
+}  // namespace lbm
+
+namespace lbm {
+// A second stream for work that overlaps the main pass (the Zou-He planes'
+// stream pass), forked from and joined back into the caller's stream.
+struct Side {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+};
 }  // namespace lbm
 
 struct lbm_ctx {
@@ -108,5 +120,11 @@ struct lbm_ctx {
   unsigned long long *counters = nullptr;
   int *zh_lists = nullptr;                // [3][NFp]: plane nodes per axis
   long long zh_count[3] = {0, 0, 0};
+  lbm::Side side;
   char err[256] = {0};
+  ~lbm_ctx() {
+    if (side.fork) cudaEventDestroy(side.fork);
+    if (side.join) cudaEventDestroy(side.join);
+    if (side.s) cudaStreamDestroy(side.s);
+  }
 };

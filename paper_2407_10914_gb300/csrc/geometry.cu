@@ -112,6 +112,58 @@ __global__ void k_scan(const int *__restrict__ cnt, long long n,
   if (threadIdx.x == 0) base[n] = carry;
 }
 
+// Device-wide exclusive prefix sum in three launches: per 1024-element
+// block a local scan and its total; the single-block scan of the totals;
+// the block offsets added back. out has n + 1 entries (out[n] = total),
+// bsum ceil(n / 1024) + 1.
+__global__ void k_scan_local(const int *__restrict__ in, long long n,
+                             int *__restrict__ out, int *__restrict__ bsum) {
+  __shared__ int warp_tot[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long i = (long long)blockIdx.x * 1024 + threadIdx.x;
+  const int v = i < n ? in[i] : 0;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) warp_tot[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int t = warp_tot[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += u;
+    }
+    warp_tot[lane] = t;
+  }
+  __syncthreads();
+  const int before = warp > 0 ? warp_tot[warp - 1] : 0;
+  if (i < n) out[i] = before + inc - v;
+  if (threadIdx.x == 1023) bsum[blockIdx.x] = before + inc;
+}
+
+__global__ void k_scan_add(int *__restrict__ out, long long n,
+                           const int *__restrict__ bsum, long long nb) {
+  const long long i = (long long)blockIdx.x * 1024 + threadIdx.x;
+  if (i < n) out[i] += bsum[blockIdx.x];
+  if (i == 0) out[n] = bsum[nb];
+}
+
+static void scan_exclusive(const int *in, int *out, long long n, int *bsum,
+                           cudaStream_t s) {
+  const long long nb = (n + 1023) / 1024;
+  if (nb == 0) {
+    cudaMemsetAsync(out, 0, sizeof(int), s);
+    return;
+  }
+  k_scan_local<<<(unsigned)nb, 1024, 0, s>>>(in, n, out, bsum);
+  k_scan<<<1, 1024, 0, s>>>(bsum, nb, bsum);  // in place
+  k_scan_add<<<(unsigned)nb, 1024, 0, s>>>(out, n, bsum, nb);
+}
+
 // One block per tile: rank of each node among the nodes of its kind in the
 // tile, in the tile's (z, y, x) order; map = (class << 14) | rank; the F and
 // S lists hold box indices.
@@ -174,14 +226,12 @@ __global__ void k_tile_map(Dom d, uint16_t *__restrict__ map,
   }
 }
 
-// One block per tile: per-node neighbour tables of the tile's fluid and
-// solid-boundary nodes, from the staged tile table. An off-box neighbour on
-// a non-periodic axis gets the entry of the clamped position with the OUT
-// bit. Node flags: bit 0 fluid-boundary; bit 1 + 2a / 2 + 2a the first /
-// last plane along axis a.
+// One block per tile: the neighbour tables of the tile's fluid nodes, from
+// the staged tile table. An off-box neighbour on a non-periodic axis gets
+// the entry of the clamped position with the OUT bit. Node flags: bit 0
+// fluid-boundary; bit 1 + 2a / 2 + 2a the first / last plane along axis a.
 template <int Q>
 __global__ void k_build_nbr(Dom d, uint32_t *__restrict__ nbf,
-                            uint32_t *__restrict__ nbs,
                             uint8_t *__restrict__ fflag) {
   using G = TileGeo<Q>;
   __shared__ uint32_t tab[G::HN];
@@ -189,15 +239,12 @@ __global__ void k_build_nbr(Dom d, uint32_t *__restrict__ nbf,
   __shared__ uint16_t spos[G::TN];
   const int t = blockIdx.x;
   const int fb0 = d.fbase[t], nf = d.fbase[t + 1] - fb0;
-  const int sb0 = d.sbase[t], ns = d.sbase[t + 1] - sb0;
-  if (nf == 0 && ns == 0) return;
+  if (nf == 0) return;
   int X0, Y0, Z0;
   stage_tile<Q>(d, t, tab, fpos, spos, X0, Y0, Z0);
-  for (int j = threadIdx.x; j < nf + ns; j += GBLOCK) {
-    const bool fluid = j < nf;
-    const int r = fluid ? j : j - nf;
+  for (int r = threadIdx.x; r < nf; r += GBLOCK) {
     int x, y, z, p0;
-    local_node<Q>(fluid ? fpos[r] : spos[r], X0, Y0, Z0, x, y, z, p0);
+    local_node<Q>(fpos[r], X0, Y0, Z0, x, y, z, p0);
     for (int i = 1; i < Q; ++i) {
       const int dx = Lattice<Q>::ex(i), dy = Lattice<Q>::ey(i),
                 dz = Lattice<Q>::ez(i);
@@ -208,35 +255,63 @@ __global__ void k_build_nbr(Dom d, uint32_t *__restrict__ nbf,
         const int cz = (z + dz < 0 || z + dz >= d.nz) ? 0 : dz;
         e = tab[p0 + G::off(cx, cy, cz)] | OUT_BIT;
       }
-      if (fluid)
-        nbf[(long long)(i - 1) * d.NFp + fb0 + r] = e;
-      else
-        nbs[(long long)(i - 1) * d.NSp + sb0 + r] = e;
+      nbf[(long long)(i - 1) * d.NFp + fb0 + r] = e;
     }
-    if (fluid) {
-      uint8_t f = entry_cls(tab[p0]) == CLS_FLUID_BND ? 1u : 0u;
-      const int c[3] = {x, y, z}, n[3] = {d.nx, d.ny, d.nz};
-      for (int a = 0; a < 3; ++a) {
-        if (c[a] == 0) f |= (uint8_t)(2u << (2 * a));
-        if (c[a] == n[a] - 1) f |= (uint8_t)(4u << (2 * a));
-      }
-      fflag[fb0 + r] = f;
+    uint8_t f = entry_cls(tab[p0]) == CLS_FLUID_BND ? 1u : 0u;
+    const int c[3] = {x, y, z}, n[3] = {d.nx, d.ny, d.nz};
+    for (int a = 0; a < 3; ++a) {
+      if (c[a] == 0) f |= (uint8_t)(2u << (2 * a));
+      if (c[a] == n[a] - 1) f |= (uint8_t)(4u << (2 * a));
     }
+    fflag[fb0 + r] = f;
   }
 }
 
-// Fluid nodes on the first or last plane of each axis (the Zou-He planes
-// of that axis), appended to one list per axis; the order is irrelevant.
-__global__ void k_zh_lists(Dom d, int *__restrict__ lists, long long stride,
-                           unsigned long long *__restrict__ counts) {
+// One thread per solid-boundary node: its fluid lattice neighbours that are
+// inside the box (the terms of Eqs. 34-35), in direction order. With
+// links == nullptr only their number goes to cnt[j]; otherwise they are
+// written from off[j] on as F-index | (diagonal direction) << 31.
+template <int Q>
+__global__ void k_s_links(Dom d, const int *__restrict__ off,
+                          uint32_t *__restrict__ links, int *__restrict__ cnt) {
+  const int j = blockIdx.x * GBLOCK + threadIdx.x;
+  if (j >= d.NS) return;
+  int x, y, z;
+  box_coords(d, d.sg[j], x, y, z);
+  const int at = links ? off[j] : 0;
+  int n = 0;
+  for (int i = 1; i < Q; ++i) {
+    bool out = false;
+    const int X = axis_step(x + Lattice<Q>::ex(i), d.nx, d.periodic & 1u, false, out);
+    const int Y = axis_step(y + Lattice<Q>::ey(i), d.ny, d.periodic & 2u, false, out);
+    const int Z = axis_step(z + Lattice<Q>::ez(i), d.nz, d.periodic & 4u, false, out);
+    if (out) continue;
+    const uint32_t e = box_entry<Q>(d, X, Y, Z);
+    if (!(entry_cls(e) & 2)) continue;
+    if (links)
+      links[at + n] = (uint32_t)entry_idx(e) |
+                      (Lattice<Q>::w(i) < Lattice<Q>::w(1) ? 0x80000000u : 0u);
+    ++n;
+  }
+  if (!links) cnt[j] = n;
+}
+
+// Fluid node k on the first or last plane of axis a (a Zou-He plane).
+__device__ __forceinline__ int on_planes(const Dom &d, int k, int a) {
+  return (d.fflag[k] & (6u << (2 * a))) ? 1 : 0;
+}
+
+__global__ void k_zh_mark(Dom d, int a, int *__restrict__ cnt) {
   const int k = blockIdx.x * GBLOCK + threadIdx.x;
-  if (k >= d.NF) return;
-  const uint8_t f = d.fflag[k];
-  for (int a = 0; a < 3; ++a)
-    if (f & (6u << (2 * a))) {
-      const unsigned long long at = atomicAdd(&counts[1 + a], 1ull);
-      lists[a * stride + (long long)at] = k;
-    }
+  if (k < d.NF) cnt[k] = on_planes(d, k, a);
+}
+
+// The Zou-He planes' fluid nodes of axis a in F order: node k goes to
+// list[off[k]].
+__global__ void k_zh_fill(Dom d, int a, const int *__restrict__ off,
+                          int *__restrict__ list) {
+  const int k = blockIdx.x * GBLOCK + threadIdx.x;
+  if (k < d.NF && on_planes(d, k, a)) list[off[k]] = k;
 }
 
 __global__ void k_indicator(long long N, const uint8_t *__restrict__ mask,
@@ -351,12 +426,11 @@ cudaError_t build_geometry(lbm_ctx *c, cudaStream_t s) {
   c->n_sbnd = tot[1];
   {
     uint32_t *nbf = const_cast<uint32_t *>(d.nbf);
-    uint32_t *nbs = const_cast<uint32_t *>(d.nbs);
     uint8_t *ff = const_cast<uint8_t *>(d.fflag);
     if (c->Q == 19)
-      k_build_nbr<19><<<nt, GBLOCK, 0, s>>>(d, nbf, nbs, ff);
+      k_build_nbr<19><<<nt, GBLOCK, 0, s>>>(d, nbf, ff);
     else
-      k_build_nbr<9><<<nt, GBLOCK, 0, s>>>(d, nbf, nbs, ff);
+      k_build_nbr<9><<<nt, GBLOCK, 0, s>>>(d, nbf, ff);
   }
   // Eq. (25) three times, then Eq. (26) at the fluid-boundary nodes
   k_indicator<<<gN, GBLOCK, 0, s>>>(d.N, c->mask, c->g0);
@@ -376,16 +450,46 @@ cudaError_t build_geometry(lbm_ctx *c, cudaStream_t s) {
     k_wall_normal<19><<<gF, GBLOCK, 0, s>>>(d, gi, nw);
   else
     k_wall_normal<9><<<gF, GBLOCK, 0, s>>>(d, gi, nw);
+  // the smoothing buffers are free from here on: scan scratch
+  int *cnt = (int *)c->g0;
+  int *bsum = (int *)c->g1;
+  int *pos = bsum + ((d.N + 1023) / 1024 + 2);
+  // links of the solid-boundary nodes (Eqs. 34-35)
+  const unsigned gS = gblocks(d.NS);
+  int *soff = const_cast<int *>(d.soff);
+  uint32_t *slink = const_cast<uint32_t *>(d.slink);
+  if (d.NS > 0) {
+    if (c->Q == 19)
+      k_s_links<19><<<gS, GBLOCK, 0, s>>>(d, nullptr, nullptr, cnt);
+    else
+      k_s_links<9><<<gS, GBLOCK, 0, s>>>(d, nullptr, nullptr, cnt);
+  }
+  scan_exclusive(cnt, soff, d.NS, bsum, s);
+  if (d.NS > 0) {
+    if (c->Q == 19)
+      k_s_links<19><<<gS, GBLOCK, 0, s>>>(d, soff, slink, nullptr);
+    else
+      k_s_links<9><<<gS, GBLOCK, 0, s>>>(d, soff, slink, nullptr);
+  }
+  // the Zou-He planes' fluid nodes per axis, in F order
+  int zh_n[3] = {0, 0, 0};
+  for (int a = 0; a < 3; ++a) {
+    k_zh_mark<<<gF, GBLOCK, 0, s>>>(d, a, cnt);
+    scan_exclusive(cnt, pos, d.NF, bsum, s);
+    k_zh_fill<<<gF, GBLOCK, 0, s>>>(d, a, pos, c->zh_lists + (size_t)a * d.NFp);
+    e = cudaMemcpyAsync(&zh_n[a], pos + d.NF, sizeof(int),
+                        cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return e;
+  }
   e = cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   k_count_fbnd<<<gF, GBLOCK, 0, s>>>(d, c->counters);
-  k_zh_lists<<<gF, GBLOCK, 0, s>>>(d, c->zh_lists, d.NFp, c->counters);
-  unsigned long long h4[4] = {0, 0, 0, 0};
-  e = cudaMemcpyAsync(h4, c->counters, sizeof(h4), cudaMemcpyDeviceToHost, s);
+  unsigned long long nfb = 0;
+  e = cudaMemcpyAsync(&nfb, c->counters, sizeof(nfb), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return e;
-  c->n_fbnd = (long long)h4[0];
-  for (int a = 0; a < 3; ++a) c->zh_count[a] = (long long)h4[1 + a];
+  c->n_fbnd = (long long)nfb;
+  for (int a = 0; a < 3; ++a) c->zh_count[a] = zh_n[a];
   return cudaGetLastError();
 }
 

@@ -24,8 +24,10 @@ constexpr int BLOCK = 256;
 __device__ __forceinline__ uint32_t nb_f(const Dom &d, int dir, int k) {
   return __ldg(d.nbf + (long long)(dir - 1) * d.NFp + k);
 }
-__device__ __forceinline__ uint32_t nb_s(const Dom &d, int dir, int j) {
-  return __ldg(d.nbs + (long long)(dir - 1) * d.NSp + j);
+// Weight of a solid-boundary link (bit 31: diagonal direction).
+template <int Q>
+__device__ __forceinline__ float link_w(uint32_t l) {
+  return (l >> 31) ? Lattice<Q>::w(Q - 1) : Lattice<Q>::w(1);
 }
 
 template <int Q, int ST>
@@ -98,12 +100,11 @@ __global__ void __launch_bounds__(BLOCK) k_phi_solid(Dom d) {
   const int j = blockIdx.x * BLOCK + threadIdx.x;
   if (j >= d.NS) return;
   float den = 0.f, sphi = 0.f, ex_pos = 0.f, ex_neg = 0.f;
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const uint32_t e = nb_s(d, i, j);
-    if (!(entry_cls(e) & 2) || entry_out(e)) continue;
-    const float w = Lattice<Q>::w(i);
-    const float m = d.mf[entry_idx(e)];
+  const int e = __ldg(d.soff + j + 1);
+  for (int p = __ldg(d.soff + j); p < e; ++p) {
+    const uint32_t l = __ldg(d.slink + p);
+    const float w = link_w<Q>(l);
+    const float m = d.mf[l & 0x7FFFFFFFu];
     den += w;
     sphi += w * m_phi(m);
     ex_pos += w * m_excess(m, false);
@@ -161,12 +162,11 @@ __global__ void __launch_bounds__(BLOCK) k_nc_solid(Dom d) {
   const int j = blockIdx.x * BLOCK + threadIdx.x;
   if (j >= d.NS) return;
   float num[3] = {0.f, 0.f, 0.f}, den = 0.f;
-#pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const uint32_t e = nb_s(d, i, j);
-    if (!(entry_cls(e) & 2) || entry_out(e)) continue;
-    const float4 v = d.ncf[entry_idx(e)];
-    const float w = Lattice<Q>::w(i);
+  const int e = __ldg(d.soff + j + 1);
+  for (int p = __ldg(d.soff + j); p < e; ++p) {
+    const uint32_t l = __ldg(d.slink + p);
+    const float w = link_w<Q>(l);
+    const float4 v = d.ncf[l & 0x7FFFFFFFu];
     num[0] += w * v.x;
     num[1] += w * v.y;
     num[2] += w * v.z;
@@ -233,14 +233,21 @@ __global__ void __launch_bounds__(BLOCK, 4) k_collide(Dom d) {
 }
 
 template <int Q, int ST>
-static void launch_step_t(const Dom &d, cudaStream_t s, bool macros,
-                          cudaEvent_t *ev) {
+static void launch_step_t(const Dom &d, cudaStream_t s, const Side &side,
+                          bool macros, cudaEvent_t *ev) {
   const unsigned g = (unsigned)((d.NF + BLOCK - 1) / BLOCK);
   const unsigned gs = (unsigned)((d.NS + BLOCK - 1) / BLOCK);
   const unsigned gz = (unsigned)((d.n_zh + BLOCK - 1) / BLOCK);
   if (ev) cudaEventRecord(ev[0], s);
+  if (d.n_zh > 0) {
+    // the planes' strided gathers overlap the bulk pass
+    cudaEventRecord(side.fork, s);
+    cudaStreamWaitEvent(side.s, side.fork, 0);
+    k_stream_zh<Q, ST><<<gz, BLOCK, 0, side.s>>>(d);
+    cudaEventRecord(side.join, side.s);
+  }
   k_stream<Q, ST><<<g, BLOCK, 0, s>>>(d);
-  if (d.n_zh > 0) k_stream_zh<Q, ST><<<gz, BLOCK, 0, s>>>(d);
+  if (d.n_zh > 0) cudaStreamWaitEvent(s, side.join, 0);
   if (ev) cudaEventRecord(ev[1], s);
   if (d.NS > 0) k_phi_solid<Q><<<gs, BLOCK, 0, s>>>(d);
   if (ev) cudaEventRecord(ev[2], s);
@@ -256,26 +263,26 @@ static void launch_step_t(const Dom &d, cudaStream_t s, bool macros,
 }
 
 static void dispatch(int Q, int storage, const Dom &d, cudaStream_t s,
-                     bool macros, cudaEvent_t *ev) {
+                     const Side &side, bool macros, cudaEvent_t *ev) {
   if (Q == 19) {
-    if (storage == LBM_STORAGE_FP32) launch_step_t<19, LBM_STORAGE_FP32>(d, s, macros, ev);
-    if (storage == LBM_STORAGE_FP16) launch_step_t<19, LBM_STORAGE_FP16>(d, s, macros, ev);
-    if (storage == LBM_STORAGE_BF16) launch_step_t<19, LBM_STORAGE_BF16>(d, s, macros, ev);
+    if (storage == LBM_STORAGE_FP32) launch_step_t<19, LBM_STORAGE_FP32>(d, s, side, macros, ev);
+    if (storage == LBM_STORAGE_FP16) launch_step_t<19, LBM_STORAGE_FP16>(d, s, side, macros, ev);
+    if (storage == LBM_STORAGE_BF16) launch_step_t<19, LBM_STORAGE_BF16>(d, s, side, macros, ev);
   } else {
-    if (storage == LBM_STORAGE_FP32) launch_step_t<9, LBM_STORAGE_FP32>(d, s, macros, ev);
-    if (storage == LBM_STORAGE_FP16) launch_step_t<9, LBM_STORAGE_FP16>(d, s, macros, ev);
-    if (storage == LBM_STORAGE_BF16) launch_step_t<9, LBM_STORAGE_BF16>(d, s, macros, ev);
+    if (storage == LBM_STORAGE_FP32) launch_step_t<9, LBM_STORAGE_FP32>(d, s, side, macros, ev);
+    if (storage == LBM_STORAGE_FP16) launch_step_t<9, LBM_STORAGE_FP16>(d, s, side, macros, ev);
+    if (storage == LBM_STORAGE_BF16) launch_step_t<9, LBM_STORAGE_BF16>(d, s, side, macros, ev);
   }
 }
 
 void launch_step(int Q, int storage, const Dom &d, cudaStream_t s,
-                 bool macros) {
-  dispatch(Q, storage, d, s, macros, nullptr);
+                 const Side &side, bool macros) {
+  dispatch(Q, storage, d, s, side, macros, nullptr);
 }
 
 void launch_step_events(int Q, int storage, const Dom &d, cudaStream_t s,
-                        bool macros, cudaEvent_t *ev) {
-  dispatch(Q, storage, d, s, macros, ev);
+                        const Side &side, bool macros, cudaEvent_t *ev) {
+  dispatch(Q, storage, d, s, side, macros, ev);
 }
 
 }  // namespace lbm
