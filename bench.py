@@ -9,9 +9,12 @@ One JSON line on rank 0:
              solid image and phi0 copied in from pinned memory, geometry set-up,
              K steps each followed by the FP64 saturation read-back (8 bytes),
              the final phase field copied out;
-  roofline   the collision pass (the dominant kernel) against the measured
-             HBM copy bandwidth, algorithmic bytes = 2 x 2Q x 4 B per fluid
-             node (populations read + written);
+  roofline   the dominant pass (the longest; the stream pass on the rock)
+             against the measured HBM copy bandwidth, with the pass's
+             algorithmic bytes per fluid node (pass_bytes below) times the
+             nodes it processes; every pass's figures are under "passes";
+  step_bandwidth  the step-level accounting of 308 B per fluid-node update
+             (2 x 2Q populations of 4 B plus a 4 B link mask);
   cpu_baseline  the FP64 oracle on a bounded slab of the same rock.
 
 `--impl reference` times the oracle (the reference arm of this build) on the
@@ -36,6 +39,31 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS & % HBM roofline: plain FP32 vs FP16-storage/batched at stated error"
 BYTES_POP = {"fp32": 4, "fp16": 2, "bf16": 2}
+
+
+def pass_bytes(Q: int, bpp: int) -> dict:
+    """Algorithmic DRAM bytes per processed node of each pass: what the pass
+    must read and write once (a gathered field counts once per node, since
+    every element is read by a fixed number of neighbours that L2 serves).
+    Fluid passes read the node's (Q - 1) x 4 B neighbour-table entries;
+    solid-boundary passes their CSR links (4.2 per node on the rock, taken
+    as 5 x 4 B) and two offsets."""
+    tab = (Q - 1) * 4
+    return {
+        # T_i of the sources (each once), (q, v) 16 B, table, flags 1 B;
+        # writes f^t (Q planes), (rho^r, rho^b) 8 B, phase field 4 B
+        "stream": Q * bpp + 16 + tab + 1 + Q * bpp + 8 + 4,
+        # links + offsets, neighbour phase 4 B; write 4 B
+        "phi_solid": 5 * 4 + 8 + 4 + 4,
+        # table, phase field 4 B, flags, wall normal 16 B (fluid-boundary
+        # nodes, about 45 %: 7 B); write (n_c, |C|) 16 B
+        "gradient": tab + 4 + 1 + 7 + 16,
+        # links + offsets, neighbour n_c 16 B; write 16 B
+        "nc_solid": 5 * 4 + 8 + 16 + 16,
+        # table, (n_c, |C|) 16 B, f^t, (rho^r, rho^b), phase 4 B; writes
+        # f'' (Q planes) and (q, v) 16 B
+        "collide": tab + 16 + Q * bpp + 8 + 4 + Q * bpp + 16,
+    }
 
 
 def parse():
@@ -244,7 +272,6 @@ def run_ours(args):
     s.init_state(case.phi0.astype(np.float32))
     nf = s.n_fluid
     n_sbnd = s.counts[2]
-    passes = 5 if n_sbnd > 0 else 3
     stream = torch.cuda.current_stream()
 
     s.step(args.warmup)
@@ -267,13 +294,32 @@ def run_ours(args):
     # per-pass times (events inside the library, on the same stream)
     k2 = max(1, min(args.steps, 200))
     pass_ms = s.step_timed(k2)
-    coll_ms = pass_ms["collide"] / k2
     bpp = BYTES_POP[args.storage]
-    alg_bytes = 2 * 2 * Q * 4 * nf if args.storage == "fp32" else 2 * Q * 4 * nf
-    achieved = alg_bytes / (coll_ms * 1e-3) / 1e9
+    pb = pass_bytes(Q, bpp)
+    n_of = {"stream": nf, "phi_solid": n_sbnd, "gradient": nf,
+            "nc_solid": n_sbnd, "collide": nf}
     peak, peak_src = measured_peaks()
-    traffic = recorded_traffic("k_collide", name)
+    passes_out = {}
+    for p, t in pass_ms.items():
+        if t <= 0 or n_of[p] == 0:
+            continue
+        t1 = t / k2
+        b = pb[p] * n_of[p]
+        passes_out[p] = {"ms": round(t1, 5), "bytes_per_node": pb[p],
+                         "nodes": n_of[p],
+                         "GBps": round(b / (t1 * 1e-3) / 1e9, 1),
+                         "frac": round(b / (t1 * 1e-3) / 1e9 / peak, 4)}
+    dom = max(passes_out, key=lambda p: passes_out[p]["ms"])
+    kern = {"stream": "k_stream", "phi_solid": "k_phi_solid",
+            "gradient": "k_gradient", "nc_solid": "k_nc_solid",
+            "collide": "k_collide"}[dom]
+    alg_bytes = pb[dom] * n_of[dom]
+    dom_ms = passes_out[dom]["ms"]
+    achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(kern, name)
     step_bytes = (2 * 2 * Q * bpp + 4) * nf  # populations read+written + link bits
+    zou_he = int(case.params.get("zou_he", 0))
+    launches_per_step = 3 + (2 if n_sbnd > 0 else 0) + (1 if zou_he else 0)
 
     e2e = None
     if not args.no_e2e:
@@ -300,12 +346,16 @@ def run_ours(args):
                 "l2": "inputs larger than L2 (two population buffers of "
                       f"{2 * Q * bpp * case.n_nodes / 1e9:.2f} GB)",
             },
-            "roofline": {"bound": "hbm", "kernel": "k_collide",
+            "roofline": {"bound": "hbm", "kernel": kern,
                          "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": traffic, "peak_source": peak_src,
                          "algorithmic_bytes_per_launch": alg_bytes,
-                         "avg_launch_ms": round(coll_ms, 5)},
+                         "avg_launch_ms": dom_ms,
+                         "timing": "CUDA events around the pass on the "
+                                   "launching stream, mean of "
+                                   f"{k2} steps"},
+            "passes": passes_out,
             "step_bandwidth": {"bytes_per_update": 2 * 2 * Q * bpp + 4,
                                "GBps": round(step_bytes / (ms_max / args.steps
                                                            * 1e-3) / 1e9, 1),
@@ -313,7 +363,7 @@ def run_ours(args):
                                    step_bytes / (ms_max / args.steps * 1e-3)
                                    / 1e9 / peak, 4)},
             "pass_ms_per_step": {k: round(v / k2, 5) for k, v in pass_ms.items()},
-            "gpu_launches": passes * args.steps,
+            "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
             "total_node_MLUPS": round(ws * case.n_nodes * args.steps
                                       / (ms_max * 1e-3) / 1e6, 1),

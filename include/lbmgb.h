@@ -127,12 +127,13 @@ lbm_status lbm_set_params(lbm_handle h, const lbm_params *p);
  * ignored). Needs lbm_set_params() first. */
 lbm_status lbm_init_state(lbm_handle h, const float *phi0_dev, void *stream);
 
-/* Advance nsteps time steps (Eq. 1), asynchronously. */
+/* Advance nsteps time steps (Eq. 1), asynchronously on `stream`. */
 lbm_status lbm_step(lbm_handle h, int nsteps, void *stream);
 
 /* Profiling form of lbm_step(): the same nsteps steps, with CUDA events
- * recorded on `stream` around each of the five passes of a step (phase
- * field; Eq. 34; gradient and wetting; Eq. 35; collision). Adds the elapsed
+ * recorded on `stream` around each of the five passes of a step (streaming
+ * with App. B and the phase field; Eq. 34; gradient and wetting; Eq. 35;
+ * curvature, force and collision). Adds the elapsed
  * milliseconds of each pass, summed over the steps, to pass_ms[0..4] (host
  * array) and synchronises the stream. The results equal lbm_step()'s. */
 lbm_status lbm_step_timed(lbm_handle h, int nsteps, void *stream,

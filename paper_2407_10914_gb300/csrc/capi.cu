@@ -222,13 +222,8 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
   d.ncf = (float4 *)(base + L.ncf);
   d.ncs = (float4 *)(base + L.ncs);
   d.macro = (float4 *)(base + L.macro);
-  cudaError_t e = cudaStreamCreateWithFlags(&c->side.s, cudaStreamNonBlocking);
-  if (e == cudaSuccess)
-    e = cudaEventCreateWithFlags(&c->side.fork, cudaEventDisableTiming);
-  if (e == cudaSuccess)
-    e = cudaEventCreateWithFlags(&c->side.join, cudaEventDisableTiming);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(c->mask, solid_host, (size_t)N, cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaMemcpyAsync(c->mask, solid_host, (size_t)N,
+                                  cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = lbm::build_geometry(c, s);
   if (e != cudaSuccess) {
     delete c;
@@ -314,7 +309,7 @@ lbm_status lbm_step(lbm_handle c, int nsteps, void *stream) {
   if (!c->state_set) return fail(c, LBM_ERR_STATE, "init the state first");
   cudaStream_t s = (cudaStream_t)stream;
   for (int k = 0; k < nsteps; ++k) {
-    lbm::launch_step(c->Q, c->storage, c->d, s, c->side, k == nsteps - 1);
+    lbm::launch_step(c->Q, c->storage, c->d, s, k == nsteps - 1);
     swap_buffers(c);
   }
   cudaError_t e = cudaGetLastError();
@@ -336,8 +331,7 @@ lbm_status lbm_step_timed(lbm_handle c, int nsteps, void *stream,
     return cuda_fail(c, e, "step_timed events");
   }
   for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
-    lbm::launch_step_events(c->Q, c->storage, c->d, s, c->side, k == nsteps - 1,
-                            ev);
+    lbm::launch_step_events(c->Q, c->storage, c->d, s, k == nsteps - 1, ev);
     swap_buffers(c);
     e = cudaEventSynchronize(ev[5]);
     for (int p = 0; p < 5 && e == cudaSuccess; ++p) {

@@ -88,15 +88,6 @@ struct Dom {
 
 }  // namespace lbm
 
-namespace lbm {
-// A second stream for work that overlaps the main pass (the Zou-He planes'
-// stream pass), forked from and joined back into the caller's stream.
-struct Side {
-  cudaStream_t s = nullptr;
-  cudaEvent_t fork = nullptr, join = nullptr;
-};
-}  // namespace lbm
-
 struct lbm_ctx {
   int Q = 0;
   int nx = 0, ny = 0, nz = 0;
@@ -120,11 +111,5 @@ struct lbm_ctx {
   unsigned long long *counters = nullptr;
   int *zh_lists = nullptr;                // [3][NFp]: plane nodes per axis
   long long zh_count[3] = {0, 0, 0};
-  lbm::Side side;
   char err[256] = {0};
-  ~lbm_ctx() {
-    if (side.fork) cudaEventDestroy(side.fork);
-    if (side.join) cudaEventDestroy(side.join);
-    if (side.s) cudaStreamDestroy(side.s);
-  }
 };

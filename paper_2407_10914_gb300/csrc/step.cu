@@ -1,8 +1,8 @@
 // The time step as five dependent passes. Each pass needs the previous one's
 // values at lattice neighbours:
-//   1 k_stream     (fluid)  pull of Eq. (1), App. B on the Zou-He planes
-//                  (k_stream_zh), Eqs. (7)-(9): stores f^t, (rho^r, rho^b)
-//                  and the phase field
+//   1 k_stream     (fluid)  pull of Eq. (1), Eqs. (7)-(9): stores f^t,
+//                  (rho^r, rho^b) and the phase field; k_zh_fix then applies
+//                  App. B on the Zou-He planes
 //   2 k_phi_solid  (solid-boundary) Eq. (34)
 //   3 k_gradient   (fluid)  Eqs. (6), (27) and wetting, Eqs. (28)-(33)
 //   4 k_nc_solid   (solid-boundary) Eq. (35)
@@ -40,56 +40,109 @@ __device__ __forceinline__ void store_streamed(const Dom &d, int k,
   d.mf[k] = m;
 }
 
-// Streamed populations of a fluid node off the Zou-He planes (Eq. 1), their
-// colour densities and the encoded phase field (Eqs. 7-9).
+// Streamed populations of a fluid node (Eq. 1), their colour densities and
+// the encoded phase field (Eqs. 7-9). On the Zou-He planes the populations
+// from outside the box are placeholders until k_zh_fix.
 template <int Q, int ST>
 __global__ void __launch_bounds__(BLOCK) k_stream(Dom d) {
   const int k = blockIdx.x * BLOCK + threadIdx.x;
   if (k >= d.NF) return;
-  if (d.c.zou_he && (__ldg(d.fflag + k) & (6u << (2 * d.c.axis)))) return;
   float ft[Q], rr, rb;
   pull_sums<Q, ST>(d, k, __ldg(d.S_src + k), ft, rr, rb);
   store_streamed<Q, ST>(d, k, ft, rr, rb, m_of(rr, rb));
 }
 
-// The same on the Zou-He planes (one thread per node of their list): the
-// per-colour unknowns of App. B, then the sums. The phase field there is
-// zeta^r - zeta^b on the inlet plane and, on the outlet plane, phi(x - a)
-// (Eq. 39) from the streamed populations of that node (the node's own if
-// that node is solid); the outlet's chi^s of (B.12)-(B.13) use it.
+// App. B on the Zou-He planes (one thread per node of their list), after
+// k_stream. Its per-colour rules are linear in the populations, and the
+// collision needs only f^t = f^r + f^b and rho^r, rho^b, so the unknown
+// populations are rebuilt in totals: with K0 the sum of the known f^t with
+// e.a = 0, Kin that of the known ones with e.a pointing into the box, and
+// N_t = 1/2 sum_{e.a=0} (e.t) f^t (t != a),
+//   inlet  (B.1-B.8):  j = rho_in - (K0 + 2 Kin),
+//                      f_i = f_opp(i) + 6 w_i j - sum_t (e_i.t) N_t, e_i.a = +1;
+//   outlet (B.9-B.18): j = (K0 + 2 Kin) - rho_out,
+//                      f_i = f_opp(i) - 6 w_i j - sum_t (e_i.t) N_t, e_i.a = -1
+// (chi^r + chi^b = 1). Summing the per-colour rules over i gives the colour
+// densities: rho^s = rho_in zeta^s at the inlet, and at the outlet
+// rho^s = K0^s + 2 Kin^s - j chi^s with chi^r = (1 + phi_out)/2, where the
+// red sums K0^r, Kin^r come from the pull's colour split. The phase field
+// is zeta^r - zeta^b at the inlet and phi(x - a), Eq. (39), at the outlet
+// (the node's own value if that node is solid).
 template <int Q, int ST>
-__global__ void __launch_bounds__(BLOCK) k_stream_zh(Dom d) {
-  const int j = blockIdx.x * BLOCK + threadIdx.x;
-  if (j >= d.n_zh) return;
-  const int k = __ldg(d.zh_list + j);
+__global__ void __launch_bounds__(BLOCK) k_zh_fix(Dom d) {
+  const int jz = blockIdx.x * BLOCK + threadIdx.x;
+  if (jz >= d.n_zh) return;
+  const int k = __ldg(d.zh_list + jz);
   const int a = d.c.axis;
-  const uint8_t fl = __ldg(d.fflag + k);
-  const float4 Sown = __ldg(d.S_src + k);
-  float fr[Q], fb[Q];
-  pull_nb<Q, ST>(d, k, Sown, fr, fb);
-  float m;
-  if (fl & (2u << (2 * a))) {
-    m = d.c.m_in;
-    zou_he_inlet<Q>(fr, d.c.rho_in_r, a);
-    zou_he_inlet<Q>(fb, d.c.rho_in_b, a);
-  } else {
-    const uint32_t e = nb_f(d, 2 * a + 2, k);  // the node at x - a
-    float rr, rb;
-    if ((entry_cls(e) & 2) && !entry_out(e)) {
-      float ft[Q];
-      const int kb = entry_idx(e);
-      pull_sums<Q, ST>(d, kb, __ldg(d.S_src + kb), ft, rr, rb);
-    } else {
-      sum_colours<Q>(fr, fb, rr, rb);
-    }
-    m = m_of(rr, rb);
-    zou_he_outlet<Q>(fr, fb, d.c.rho_out, m_phi(m), a);
-  }
-  float rr, rb;
-  sum_colours<Q>(fr, fb, rr, rb);
+  const bool inlet = __ldg(d.fflag + k) & (2u << (2 * a));
+  const int in_dir = inlet ? -1 : 1;  // e.a of the known, inward populations
+  float ft[Q];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) fr[i] += fb[i];  // f^t
-  store_streamed<Q, ST>(d, k, fr, rr, rb, m);
+  for (int i = 0; i < Q; ++i) ft[i] = TIO<Q, ST>::load_from(d, d.U, i, k);
+  float K0 = 0.f, Kin = 0.f, N[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int ea = Lattice<Q>::e(i, a);
+    if (ea == 0) {
+      K0 += ft[i];
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+        if (t != a) N[t] += 0.5f * (float)Lattice<Q>::e(i, t) * ft[i];
+    } else if (ea == in_dir) {
+      Kin += ft[i];
+    }
+  }
+  float rr, rb, m, jt;
+  if (inlet) {
+    jt = d.c.rho_in_r + d.c.rho_in_b - (K0 + 2.f * Kin);
+    rr = d.c.rho_in_r;
+    rb = d.c.rho_in_b;
+    m = d.c.m_in;
+  } else {
+    jt = (K0 + 2.f * Kin) - d.c.rho_out;
+    const uint32_t e = nb_f(d, 2 * a + 2, k);  // the node at x - a
+    const float2 Rk = d.R[k];
+    m = ((entry_cls(e) & 2) && !entry_out(e)) ? d.mf[entry_idx(e)]
+                                               : m_of(Rk.x, Rk.y);
+    // red parts of the known populations (e.a >= 0), as the pull split them
+    const float4 Sown = __ldg(d.S_src + k);
+    float K0r = 0.f, Kinr = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int ea = Lattice<Q>::e(i, a);
+      if (ea < 0) continue;
+      float fr, fb;
+      if (i == 0) {
+        rebuild<Q>(ft[0], Sown, 0, fr, fb);
+      } else {
+        const uint32_t es = nb_f(d, Lattice<Q>::opp(i), k);
+        const bool fl = (entry_cls(es) & 2) && !entry_out(es);
+        const float4 S = fl ? __ldg(d.S_src + entry_idx(es)) : Sown;
+        const float ev = (float)Lattice<Q>::ex(i) * S.y +
+                         (float)Lattice<Q>::ey(i) * S.z +
+                         (float)Lattice<Q>::ez(i) * S.w;
+        rebuild_ev<Q>(ft[i], S.x, fl ? ev : -ev, i, fr, fb);
+      }
+      if (ea == 0) K0r += fr;
+      else Kinr += fr;
+    }
+    const float chi_r = 0.5f * (1.f + m_phi(m));
+    rr = K0r + 2.f * Kinr - jt * chi_r;
+    rb = (K0 - K0r) + 2.f * (Kin - Kinr) - jt * (1.f - chi_r);
+    jt = -jt;  // the outlet rule subtracts 6 w_i j
+  }
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if (Lattice<Q>::e(i, a) != -in_dir) continue;
+    float corr = 0.f;
+#pragma unroll
+    for (int t = 0; t < 3; ++t)
+      if (t != a) corr += (float)Lattice<Q>::e(i, t) * N[t];
+    TIO<Q, ST>::store(d, d.U, i, k,
+                      ft[Lattice<Q>::opp(i)] + 6.f * Lattice<Q>::w(i) * jt - corr);
+  }
+  d.R[k] = make_float2(rr, rb);
+  d.mf[k] = m;
 }
 
 // Eq. (34): phi at a solid-boundary node = w-weighted mean over its fluid
@@ -233,21 +286,14 @@ __global__ void __launch_bounds__(BLOCK, 4) k_collide(Dom d) {
 }
 
 template <int Q, int ST>
-static void launch_step_t(const Dom &d, cudaStream_t s, const Side &side,
-                          bool macros, cudaEvent_t *ev) {
+static void launch_step_t(const Dom &d, cudaStream_t s, bool macros,
+                          cudaEvent_t *ev) {
   const unsigned g = (unsigned)((d.NF + BLOCK - 1) / BLOCK);
   const unsigned gs = (unsigned)((d.NS + BLOCK - 1) / BLOCK);
   const unsigned gz = (unsigned)((d.n_zh + BLOCK - 1) / BLOCK);
   if (ev) cudaEventRecord(ev[0], s);
-  if (d.n_zh > 0) {
-    // the planes' strided gathers overlap the bulk pass
-    cudaEventRecord(side.fork, s);
-    cudaStreamWaitEvent(side.s, side.fork, 0);
-    k_stream_zh<Q, ST><<<gz, BLOCK, 0, side.s>>>(d);
-    cudaEventRecord(side.join, side.s);
-  }
   k_stream<Q, ST><<<g, BLOCK, 0, s>>>(d);
-  if (d.n_zh > 0) cudaStreamWaitEvent(s, side.join, 0);
+  if (d.n_zh > 0) k_zh_fix<Q, ST><<<gz, BLOCK, 0, s>>>(d);
   if (ev) cudaEventRecord(ev[1], s);
   if (d.NS > 0) k_phi_solid<Q><<<gs, BLOCK, 0, s>>>(d);
   if (ev) cudaEventRecord(ev[2], s);
@@ -263,26 +309,26 @@ static void launch_step_t(const Dom &d, cudaStream_t s, const Side &side,
 }
 
 static void dispatch(int Q, int storage, const Dom &d, cudaStream_t s,
-                     const Side &side, bool macros, cudaEvent_t *ev) {
+                     bool macros, cudaEvent_t *ev) {
   if (Q == 19) {
-    if (storage == LBM_STORAGE_FP32) launch_step_t<19, LBM_STORAGE_FP32>(d, s, side, macros, ev);
-    if (storage == LBM_STORAGE_FP16) launch_step_t<19, LBM_STORAGE_FP16>(d, s, side, macros, ev);
-    if (storage == LBM_STORAGE_BF16) launch_step_t<19, LBM_STORAGE_BF16>(d, s, side, macros, ev);
+    if (storage == LBM_STORAGE_FP32) launch_step_t<19, LBM_STORAGE_FP32>(d, s, macros, ev);
+    if (storage == LBM_STORAGE_FP16) launch_step_t<19, LBM_STORAGE_FP16>(d, s, macros, ev);
+    if (storage == LBM_STORAGE_BF16) launch_step_t<19, LBM_STORAGE_BF16>(d, s, macros, ev);
   } else {
-    if (storage == LBM_STORAGE_FP32) launch_step_t<9, LBM_STORAGE_FP32>(d, s, side, macros, ev);
-    if (storage == LBM_STORAGE_FP16) launch_step_t<9, LBM_STORAGE_FP16>(d, s, side, macros, ev);
-    if (storage == LBM_STORAGE_BF16) launch_step_t<9, LBM_STORAGE_BF16>(d, s, side, macros, ev);
+    if (storage == LBM_STORAGE_FP32) launch_step_t<9, LBM_STORAGE_FP32>(d, s, macros, ev);
+    if (storage == LBM_STORAGE_FP16) launch_step_t<9, LBM_STORAGE_FP16>(d, s, macros, ev);
+    if (storage == LBM_STORAGE_BF16) launch_step_t<9, LBM_STORAGE_BF16>(d, s, macros, ev);
   }
 }
 
 void launch_step(int Q, int storage, const Dom &d, cudaStream_t s,
-                 const Side &side, bool macros) {
-  dispatch(Q, storage, d, s, side, macros, nullptr);
+                 bool macros) {
+  dispatch(Q, storage, d, s, macros, nullptr);
 }
 
 void launch_step_events(int Q, int storage, const Dom &d, cudaStream_t s,
-                        const Side &side, bool macros, cudaEvent_t *ev) {
-  dispatch(Q, storage, d, s, side, macros, ev);
+                        bool macros, cudaEvent_t *ev) {
+  dispatch(Q, storage, d, s, macros, ev);
 }
 
 }  // namespace lbm

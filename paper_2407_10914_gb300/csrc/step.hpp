@@ -7,17 +7,16 @@
 
 namespace lbm {
 
-// One time step: the five passes of step.cu on stream s (the Zou-He
-// planes' stream pass on side.s, joined back before the next pass).
-// `macros` also stores rho and u of this step.
+// One time step: the five passes of step.cu on stream s. `macros` also
+// stores rho and u of this step.
 void launch_step(int Q, int storage, const Dom &d, cudaStream_t s,
-                 const Side &side, bool macros);
+                 bool macros);
 
 // The same step with an event recorded before each pass and after the last
 // (ev[0..5]); passes that do not run (no solid-boundary nodes) record
 // back-to-back events.
 void launch_step_events(int Q, int storage, const Dom &d, cudaStream_t s,
-                        const Side &side, bool macros, cudaEvent_t *ev);
+                        bool macros, cudaEvent_t *ev);
 
 // Geometry set-up (geometry.cu): classes, the compact lists and the map,
 // Eq. (25) smoothing, Eq. (26) normals and the counts.

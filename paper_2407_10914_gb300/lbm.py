@@ -171,7 +171,7 @@ def lbm_step(h, nsteps, stream):
     _check(load_library().lbm_step(h, int(nsteps), stream), h, "lbm_step")
 
 
-PASSES = ("phase", "phi_solid", "gradient", "nc_solid", "collide")
+PASSES = ("stream", "phi_solid", "gradient", "nc_solid", "collide")
 
 
 def lbm_step_timed(h, nsteps, stream) -> dict:
