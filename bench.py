@@ -53,6 +53,11 @@ def pass_bytes(Q: int, bpp: int) -> dict:
         # T_i of the sources (each once), (q, v) 16 B, table, flags 1 B;
         # writes f^t (Q planes), (rho^r, rho^b) 8 B, phase field 4 B
         "stream": Q * bpp + 16 + tab + 1 + Q * bpp + 8 + 4,
+        # U of the node (Q planes), flags, table entry of x - a, phase of
+        # that node; at the outlet the colour split of the known
+        # populations re-reads about 14 table entries and (q, v); writes
+        # 5 planes, (rho^r, rho^b), phase
+        "zh_fix": Q * bpp + 1 + 4 + 4 + 7 * (4 + 16) + 5 * bpp + 8 + 4,
         # links + offsets, neighbour phase 4 B; write 4 B
         "phi_solid": 5 * 4 + 8 + 4 + 4,
         # table, phase field 4 B, flags, wall normal 16 B (fluid-boundary
@@ -296,7 +301,8 @@ def run_ours(args):
     pass_ms = s.step_timed(k2)
     bpp = BYTES_POP[args.storage]
     pb = pass_bytes(Q, bpp)
-    n_of = {"stream": nf, "phi_solid": n_sbnd, "gradient": nf,
+    n_zh = s.n_zou_he
+    n_of = {"stream": nf, "zh_fix": n_zh, "phi_solid": n_sbnd, "gradient": nf,
             "nc_solid": n_sbnd, "collide": nf}
     peak, peak_src = measured_peaks()
     passes_out = {}
@@ -310,7 +316,8 @@ def run_ours(args):
                          "GBps": round(b / (t1 * 1e-3) / 1e9, 1),
                          "frac": round(b / (t1 * 1e-3) / 1e9 / peak, 4)}
     dom = max(passes_out, key=lambda p: passes_out[p]["ms"])
-    kern = {"stream": "k_stream", "phi_solid": "k_phi_solid",
+    kern = {"stream": "k_stream", "zh_fix": "k_zh_fix",
+            "phi_solid": "k_phi_solid",
             "gradient": "k_gradient", "nc_solid": "k_nc_solid",
             "collide": "k_collide"}[dom]
     alg_bytes = pb[dom] * n_of[dom]
@@ -318,8 +325,7 @@ def run_ours(args):
     achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
     traffic = recorded_traffic(kern, name)
     step_bytes = (2 * 2 * Q * bpp + 4) * nf  # populations read+written + link bits
-    zou_he = int(case.params.get("zou_he", 0))
-    launches_per_step = 3 + (2 if n_sbnd > 0 else 0) + (1 if zou_he else 0)
+    launches_per_step = 3 + (2 if n_sbnd > 0 else 0) + (1 if n_zh > 0 else 0)
 
     e2e = None
     if not args.no_e2e:

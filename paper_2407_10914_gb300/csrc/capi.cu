@@ -322,10 +322,11 @@ lbm_status lbm_step_timed(lbm_handle c, int nsteps, void *stream,
   if (!c || nsteps < 0 || !pass_ms) return LBM_ERR_ARG;
   if (!c->state_set) return fail(c, LBM_ERR_STATE, "init the state first");
   cudaStream_t s = (cudaStream_t)stream;
-  cudaEvent_t ev[6];
+  cudaEvent_t ev[LBM_N_PASSES + 1];
   int made = 0;
   cudaError_t e = cudaSuccess;
-  for (; made < 6 && e == cudaSuccess; ++made) e = cudaEventCreate(&ev[made]);
+  for (; made < LBM_N_PASSES + 1 && e == cudaSuccess; ++made)
+    e = cudaEventCreate(&ev[made]);
   if (e != cudaSuccess) {
     for (int k = 0; k + 1 < made; ++k) cudaEventDestroy(ev[k]);
     return cuda_fail(c, e, "step_timed events");
@@ -333,14 +334,14 @@ lbm_status lbm_step_timed(lbm_handle c, int nsteps, void *stream,
   for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
     lbm::launch_step_events(c->Q, c->storage, c->d, s, k == nsteps - 1, ev);
     swap_buffers(c);
-    e = cudaEventSynchronize(ev[5]);
-    for (int p = 0; p < 5 && e == cudaSuccess; ++p) {
+    e = cudaEventSynchronize(ev[LBM_N_PASSES]);
+    for (int p = 0; p < LBM_N_PASSES && e == cudaSuccess; ++p) {
       float ms = 0.f;
       e = cudaEventElapsedTime(&ms, ev[p], ev[p + 1]);
       pass_ms[p] += ms;
     }
   }
-  for (int k = 0; k < 6; ++k) cudaEventDestroy(ev[k]);
+  for (int k = 0; k < LBM_N_PASSES + 1; ++k) cudaEventDestroy(ev[k]);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "step_timed");
   return LBM_OK;

@@ -293,19 +293,20 @@ static void launch_step_t(const Dom &d, cudaStream_t s, bool macros,
   const unsigned gz = (unsigned)((d.n_zh + BLOCK - 1) / BLOCK);
   if (ev) cudaEventRecord(ev[0], s);
   k_stream<Q, ST><<<g, BLOCK, 0, s>>>(d);
-  if (d.n_zh > 0) k_zh_fix<Q, ST><<<gz, BLOCK, 0, s>>>(d);
   if (ev) cudaEventRecord(ev[1], s);
-  if (d.NS > 0) k_phi_solid<Q><<<gs, BLOCK, 0, s>>>(d);
+  if (d.n_zh > 0) k_zh_fix<Q, ST><<<gz, BLOCK, 0, s>>>(d);
   if (ev) cudaEventRecord(ev[2], s);
-  k_gradient<Q><<<g, BLOCK, 0, s>>>(d);
+  if (d.NS > 0) k_phi_solid<Q><<<gs, BLOCK, 0, s>>>(d);
   if (ev) cudaEventRecord(ev[3], s);
-  if (d.NS > 0) k_nc_solid<Q><<<gs, BLOCK, 0, s>>>(d);
+  k_gradient<Q><<<g, BLOCK, 0, s>>>(d);
   if (ev) cudaEventRecord(ev[4], s);
+  if (d.NS > 0) k_nc_solid<Q><<<gs, BLOCK, 0, s>>>(d);
+  if (ev) cudaEventRecord(ev[5], s);
   if (macros)
     k_collide<Q, ST, true><<<g, BLOCK, 0, s>>>(d);
   else
     k_collide<Q, ST, false><<<g, BLOCK, 0, s>>>(d);
-  if (ev) cudaEventRecord(ev[5], s);
+  if (ev) cudaEventRecord(ev[6], s);
 }
 
 static void dispatch(int Q, int storage, const Dom &d, cudaStream_t s,

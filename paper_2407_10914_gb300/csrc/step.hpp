@@ -12,9 +12,9 @@ namespace lbm {
 void launch_step(int Q, int storage, const Dom &d, cudaStream_t s,
                  bool macros);
 
-// The same step with an event recorded before each pass and after the last
-// (ev[0..5]); passes that do not run (no solid-boundary nodes) record
-// back-to-back events.
+// The same step with an event recorded before each of its six kernels and
+// after the last (ev[0..6]); kernels that do not run (no Zou-He planes, no
+// solid-boundary nodes) get back-to-back events.
 void launch_step_events(int Q, int storage, const Dom &d, cudaStream_t s,
                         bool macros, cudaEvent_t *ev);
 

@@ -171,11 +171,11 @@ def lbm_step(h, nsteps, stream):
     _check(load_library().lbm_step(h, int(nsteps), stream), h, "lbm_step")
 
 
-PASSES = ("stream", "phi_solid", "gradient", "nc_solid", "collide")
+PASSES = ("stream", "zh_fix", "phi_solid", "gradient", "nc_solid", "collide")
 
 
 def lbm_step_timed(h, nsteps, stream) -> dict:
-    ms = (C.c_double * 5)()
+    ms = (C.c_double * len(PASSES))()
     _check(load_library().lbm_step_timed(h, int(nsteps), stream, ms), h,
            "lbm_step_timed")
     return dict(zip(PASSES, ms[:]))
@@ -261,6 +261,8 @@ class Session:
                                    STORAGE[storage], self.workspace,
                                    self.stream())
         self.counts = lbm_counts(self.h)
+        self._solid = solid
+        self.n_zou_he = 0
 
     def stream(self):
         return _stream(self.torch)
@@ -277,6 +279,13 @@ class Session:
 
     def set_params(self, **kw):
         lbm_set_params(self.h, make_params(**kw))
+        # fluid nodes on the two Zou-He planes of the flow axis (host count)
+        self.n_zou_he = 0
+        if kw.get("zou_he"):
+            ax = 2 - int(kw.get("flow_axis", 0))  # numpy axis of (z, y, x)
+            fl = self._solid == 0
+            self.n_zou_he = int(np.take(fl, 0, axis=ax).sum()
+                                + np.take(fl, -1, axis=ax).sum())
 
     def init_state(self, phi0):
         t = self.torch.as_tensor(np.asarray(phi0, np.float32).reshape(self.shape)
