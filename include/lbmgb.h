@@ -63,7 +63,9 @@ enum {
 /* Population storage (chosen at lbm_init_geometry). */
 enum {
   LBM_STORAGE_FP32 = 0, /* f^r, f^b as float32                              */
-  LBM_STORAGE_FP16 = 1, /* T = f^r + f^b - w rho0 and D = f^r - f^b, fp16   */
+  LBM_STORAGE_FP16 = 1, /* f''_i / w_i - rho0 in fp16 (f''_i = f^r + f^b
+                           after recolouring); the colour split (q, v) and
+                           all arithmetic stay float32                      */
   LBM_STORAGE_BF16 = 2  /* the same offsets in bfloat16                     */
 };
 
@@ -200,6 +202,76 @@ const char *lbm_last_error(lbm_handle h);
 
 /* Release the handle (host memory only; the workspace stays the caller's). */
 void lbm_destroy(lbm_handle h);
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent domains ("cases", e.g. a sweep of sessile drops
+ * over contact angles and box sizes) stepped together. Each case is a
+ * handle with its own geometry, parameters and state, all of one lattice
+ * and one storage type. The paper runs one domain at a time; the batch
+ * changes the scheduling only. Every case's results are those of lbm_step()
+ * on that handle, bit for bit. Step a batch's cases only through the batch
+ * while it exists, or expect the batch to re-read them (see lbm_batch_step).
+ * The handles must outlive the batch.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_batch_s *lbm_batch;
+
+/* Device workspace (bytes) of a batch of ncases cases: the case table, a
+ * control block and the work plans, a few hundred bytes per case. 0 if
+ * ncases < 1. */
+size_t lbm_batch_workspace_bytes(int ncases);
+
+/* Batch of ncases distinct handles (host array, copied), each with
+ * parameters and state set, all with the same lattice and storage.
+ * dev_workspace: caller-owned device memory of ws_bytes >=
+ * lbm_batch_workspace_bytes(ncases), 256-byte aligned, kept until
+ * lbm_batch_destroy(). Synchronises `stream`. Starts in mode 0 with 256
+ * threads per block. */
+lbm_status lbm_batch_create(lbm_batch *out, const lbm_handle *cases,
+                            int ncases, void *dev_workspace, size_t ws_bytes,
+                            void *stream);
+
+/* Scheduling of lbm_batch_step():
+ *   mode 0: one kernel launch per pass of a step, covering every case;
+ *   mode 1: one persistent launch for all passes of all steps of a call.
+ *     Blocks take (step, pass, case, chunk) work items in step-and-pass
+ *     order, and each item waits until its case has finished the previous
+ *     pass (a per-case completion count), so cases advance independently.
+ *     Each wait is bounded by time (2 s); when one runs out, every block
+ *     stops and lbm_batch_status() reports LBM_ERR_TIMEOUT.
+ * threads: 128 or 256 threads per block. chunk (mode 1): blocks' worth of
+ * nodes per work item, 1..64. Drops the recorded graphs; synchronises
+ * `stream`. The results do not depend on the configuration. */
+lbm_status lbm_batch_set_config(lbm_batch b, int mode, int threads, int chunk,
+                                void *stream);
+
+/* Advance every case by nsteps steps, asynchronously on `stream`. The
+ * kernels of one call are recorded once per (nsteps, configuration) into a
+ * CUDA graph on a stream the batch owns, and the graph is launched on
+ * `stream`. The last step stores each case's macros, as lbm_step() does.
+ * If a case was changed or stepped outside the batch since the last call,
+ * the case table is written again first (synchronising `stream`). */
+lbm_status lbm_batch_step(lbm_batch b, int nsteps, void *stream);
+
+/* Synchronise `stream` and report whether a bounded wait of a mode-1
+ * launch ran out since the last call: LBM_ERR_TIMEOUT (the flag is then
+ * cleared; the cases' states are partly stepped and must be reset) or
+ * LBM_OK. While the flag is set, further mode-1 launches stop at once. */
+lbm_status lbm_batch_status(lbm_batch b, void *stream);
+
+/* Health check of the bounded wait: runs the persistent kernel's wait on a
+ * count that nothing raises, with a limit of limit_ms (0 < limit_ms <=
+ * 10000). Returns LBM_OK when the wait gave up and set the error flag as
+ * designed (the flag is cleared again), and the elapsed device time in
+ * *waited_ms (may be NULL); LBM_ERR_STATE if it did not give up.
+ * Synchronises `stream`. */
+lbm_status lbm_batch_check_wait(lbm_batch b, double limit_ms,
+                                double *waited_ms, void *stream);
+
+/* Message of the last failed call on this batch ("" if none). */
+const char *lbm_batch_last_error(lbm_batch b);
+
+/* Release the batch (host side; the workspace stays the caller's). */
+void lbm_batch_destroy(lbm_batch b);
 
 #ifdef __cplusplus
 }

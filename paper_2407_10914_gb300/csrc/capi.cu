@@ -120,14 +120,7 @@ bool valid_shape(int lattice, int nx, int ny, int nz) {
   return N < (1LL << 31);  // box indices are stored as int32
 }
 
-void swap_buffers(lbm_ctx *c) {
-  const void *t = c->d.T_src;
-  c->d.T_src = c->d.T_dst;
-  c->d.T_dst = const_cast<void *>(t);
-  const float4 *u = c->d.S_src;
-  c->d.S_src = c->d.S_dst;
-  c->d.S_dst = const_cast<float4 *>(u);
-}
+void swap_buffers(lbm_ctx *c) { lbm::swap_state(c); }
 
 }  // namespace
 
@@ -291,6 +284,7 @@ lbm_status lbm_set_params(lbm_handle c, const lbm_params *p) {
   }
   for (int a = 0; a < 3; ++a) k.g[a] = (float)p->g[a];
   c->params_set = true;
+  ++c->gen;
   return LBM_OK;
 }
 
@@ -301,6 +295,7 @@ lbm_status lbm_init_state(lbm_handle c, const float *phi0, void *stream) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "init_state");
   c->state_set = true;
+  ++c->gen;
   return LBM_OK;
 }
 
@@ -312,6 +307,7 @@ lbm_status lbm_step(lbm_handle c, int nsteps, void *stream) {
     lbm::launch_step(c->Q, c->storage, c->d, s, k == nsteps - 1);
     swap_buffers(c);
   }
+  ++c->gen;
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "step");
   return LBM_OK;
@@ -331,6 +327,7 @@ lbm_status lbm_step_timed(lbm_handle c, int nsteps, void *stream,
     for (int k = 0; k + 1 < made; ++k) cudaEventDestroy(ev[k]);
     return cuda_fail(c, e, "step_timed events");
   }
+  ++c->gen;
   for (int k = 0; k < nsteps && e == cudaSuccess; ++k) {
     lbm::launch_step_events(c->Q, c->storage, c->d, s, k == nsteps - 1, ev);
     swap_buffers(c);
@@ -409,6 +406,7 @@ lbm_status lbm_set_populations(lbm_handle c, const float *src, void *stream) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "set_populations");
   c->state_set = true;
+  ++c->gen;
   return LBM_OK;
 }
 

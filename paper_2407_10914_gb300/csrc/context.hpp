@@ -111,5 +111,21 @@ struct lbm_ctx {
   unsigned long long *counters = nullptr;
   int *zh_lists = nullptr;                // [3][NFp]: plane nodes per axis
   long long zh_count[3] = {0, 0, 0};
+  // bumped by every call that changes the parameters or the state outside a
+  // batch (set_params, init_state, set_populations, step): a batch holding
+  // this domain refreshes its copy of the kernel arguments when it changes
+  unsigned long long gen = 0;
   char err[256] = {0};
 };
+
+namespace lbm {
+// After a step the destination buffers hold the current state.
+inline void swap_state(lbm_ctx *c) {
+  const void *t = c->d.T_src;
+  c->d.T_src = c->d.T_dst;
+  c->d.T_dst = const_cast<void *>(t);
+  const float4 *u = c->d.S_src;
+  c->d.S_src = c->d.S_dst;
+  c->d.S_dst = const_cast<float4 *>(u);
+}
+}  // namespace lbm

@@ -1,0 +1,274 @@
+// The work of one node in each pass of the time step, shared by the
+// per-domain kernels (step.cu) and the batched kernels (batch.cu). The
+// passes, in order; each needs the previous one's values at lattice
+// neighbours:
+//   stream_node     (fluid)  pull of Eq. (1), Eqs. (7)-(9): stores f^t,
+//                   (rho^r, rho^b) and the phase field;
+//   zh_fix_node     (Zou-He plane nodes) App. B in totals;
+//   phi_solid_node  (solid-boundary) Eq. (34);
+//   gradient_node   (fluid)  Eqs. (6), (27) and wetting, Eqs. (28)-(33);
+//   nc_solid_node   (solid-boundary) Eq. (35);
+//   collide_node    (fluid)  Eq. (12), (5), (36); Eq. (2) single-rate on
+//                   the stored f^t; stores f'' and (q, v), the recoloured
+//                   state of Eqs. (20)-(21).
+// Every lattice neighbour of a fluid node is one entry of its precomputed
+// neighbour table (geometry.cu). COH selects loads that bypass L1 for the
+// values that change within a step (see ldv).
+#pragma once
+
+#include "tiles.cuh"
+
+namespace lbm {
+
+__device__ __forceinline__ uint32_t nb_f(const Dom &d, int dir, int k) {
+  return __ldg(d.nbf + (long long)(dir - 1) * d.NFp + k);
+}
+
+// Weight of a solid-boundary link (bit 31: diagonal direction).
+template <int Q>
+__device__ __forceinline__ float link_w(uint32_t l) {
+  return (l >> 31) ? Lattice<Q>::w(Q - 1) : Lattice<Q>::w(1);
+}
+
+// Streamed populations of fluid node k (Eq. 1), their colour densities and
+// the encoded phase field (Eqs. 7-9). On the Zou-He planes the populations
+// from outside the box are placeholders until zh_fix_node.
+template <int Q, int ST, bool COH>
+__device__ __forceinline__ void stream_node(const Dom &d, int k) {
+  float ft[Q], rr, rb;
+  pull_sums<Q, ST, COH>(d, k, ldv<COH>(d.S_src + k), ft, rr, rb);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) TIO<Q, ST>::store(d, d.U, i, k, ft[i]);
+  d.R[k] = make_float2(rr, rb);
+  d.mf[k] = m_of(rr, rb);
+}
+
+// App. B on the Zou-He planes (node jz of their list), after stream_node.
+// Its per-colour rules are linear in the populations, and the collision
+// needs only f^t = f^r + f^b and rho^r, rho^b, so the unknown populations
+// are rebuilt in totals: with K0 the sum of the known f^t with e.a = 0, Kin
+// that of the known ones with e.a pointing into the box, and
+// N_t = 1/2 sum_{e.a=0} (e.t) f^t (t != a),
+//   inlet  (B.1-B.8):  j = rho_in - (K0 + 2 Kin),
+//                      f_i = f_opp(i) + 6 w_i j - sum_t (e_i.t) N_t, e_i.a = +1;
+//   outlet (B.9-B.18): j = (K0 + 2 Kin) - rho_out,
+//                      f_i = f_opp(i) - 6 w_i j - sum_t (e_i.t) N_t, e_i.a = -1
+// (chi^r + chi^b = 1). Summing the per-colour rules over i gives the colour
+// densities: rho^s = rho_in zeta^s at the inlet, and at the outlet
+// rho^s = K0^s + 2 Kin^s - j chi^s with chi^r = (1 + phi_out)/2, where the
+// red sums K0^r, Kin^r come from the pull's colour split. The phase field
+// is zeta^r - zeta^b at the inlet and phi(x - a), Eq. (39), at the outlet
+// (the node's own value if that node is solid).
+template <int Q, int ST, bool COH>
+__device__ __forceinline__ void zh_fix_node(const Dom &d, int jz) {
+  // U and R of the node are read and then rewritten by this thread: never
+  // through the read-only path
+  using IO = TIO<Q, ST, true>;
+  const int k = __ldg(d.zh_list + jz);
+  const int a = d.c.axis;
+  const bool inlet = __ldg(d.fflag + k) & (2u << (2 * a));
+  const int in_dir = inlet ? -1 : 1;  // e.a of the known, inward populations
+  float ft[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) ft[i] = IO::load_from(d, d.U, i, k);
+  float K0 = 0.f, Kin = 0.f, N[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    const int ea = Lattice<Q>::e(i, a);
+    if (ea == 0) {
+      K0 += ft[i];
+#pragma unroll
+      for (int t = 0; t < 3; ++t)
+        if (t != a) N[t] += 0.5f * (float)Lattice<Q>::e(i, t) * ft[i];
+    } else if (ea == in_dir) {
+      Kin += ft[i];
+    }
+  }
+  float rr, rb, m, jt;
+  if (inlet) {
+    jt = d.c.rho_in_r + d.c.rho_in_b - (K0 + 2.f * Kin);
+    rr = d.c.rho_in_r;
+    rb = d.c.rho_in_b;
+    m = d.c.m_in;
+  } else {
+    jt = (K0 + 2.f * Kin) - d.c.rho_out;
+    const uint32_t e = nb_f(d, 2 * a + 2, k);  // the node at x - a
+    const float2 Rk = ldv<true>(d.R + k);
+    m = ((entry_cls(e) & 2) && !entry_out(e)) ? ldv<COH>(d.mf + entry_idx(e))
+                                               : m_of(Rk.x, Rk.y);
+    // red parts of the known populations (e.a >= 0), as the pull split them
+    const float4 Sown = ldv<COH>(d.S_src + k);
+    float K0r = 0.f, Kinr = 0.f;
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+      const int ea = Lattice<Q>::e(i, a);
+      if (ea < 0) continue;
+      float fr, fb;
+      if (i == 0) {
+        rebuild<Q>(ft[0], Sown, 0, fr, fb);
+      } else {
+        const uint32_t es = nb_f(d, Lattice<Q>::opp(i), k);
+        const bool fl = (entry_cls(es) & 2) && !entry_out(es);
+        const float4 S = fl ? ldv<COH>(d.S_src + entry_idx(es)) : Sown;
+        const float ev = (float)Lattice<Q>::ex(i) * S.y +
+                         (float)Lattice<Q>::ey(i) * S.z +
+                         (float)Lattice<Q>::ez(i) * S.w;
+        rebuild_ev<Q>(ft[i], S.x, fl ? ev : -ev, i, fr, fb);
+      }
+      if (ea == 0) K0r += fr;
+      else Kinr += fr;
+    }
+    const float chi_r = 0.5f * (1.f + m_phi(m));
+    rr = K0r + 2.f * Kinr - jt * chi_r;
+    rb = (K0 - K0r) + 2.f * (Kin - Kinr) - jt * (1.f - chi_r);
+    jt = -jt;  // the outlet rule subtracts 6 w_i j
+  }
+#pragma unroll
+  for (int i = 0; i < Q; ++i) {
+    if (Lattice<Q>::e(i, a) != -in_dir) continue;
+    float corr = 0.f;
+#pragma unroll
+    for (int t = 0; t < 3; ++t)
+      if (t != a) corr += (float)Lattice<Q>::e(i, t) * N[t];
+    IO::store(d, d.U, i, k,
+              ft[Lattice<Q>::opp(i)] + 6.f * Lattice<Q>::w(i) * jt - corr);
+  }
+  d.R[k] = make_float2(rr, rb);
+  d.mf[k] = m;
+}
+
+// Eq. (34): phi at solid-boundary node j = w-weighted mean over its fluid
+// lattice neighbours, kept in the encoded form: the mean of phi - s for the
+// sign s of the mean.
+template <int Q, bool COH>
+__device__ __forceinline__ void phi_solid_node(const Dom &d, int j) {
+  float den = 0.f, sphi = 0.f, ex_pos = 0.f, ex_neg = 0.f;
+  const int e = __ldg(d.soff + j + 1);
+  for (int p = __ldg(d.soff + j); p < e; ++p) {
+    const uint32_t l = __ldg(d.slink + p);
+    const float w = link_w<Q>(l);
+    const float m = ldv<COH>(d.mf + (l & 0x7FFFFFFFu));
+    den += w;
+    sphi += w * m_phi(m);
+    ex_pos += w * m_excess(m, false);
+    ex_neg += w * m_excess(m, true);
+  }
+  const bool blue = sphi < 0.f;
+  const float ex = (blue ? ex_neg : ex_pos) / den;  // phi_s - s
+  d.ms[j] = m_pack(blue, blue ? 0.5f * ex : -0.5f * ex);
+}
+
+// Eq. (6) (c = dt = 1) and Eq. (27) at fluid node k, with phi(x + e_i) -
+// s(x) in place of phi(x + e_i) (the same sum since sum_i w_i e_i = 0),
+// off-box neighbours clamped; at fluid-boundary nodes the wetting scheme
+// turns n_c, keeping |C|. Stored: (n_c, |C|), or zero where |C| <= EPS_C
+// (no interface).
+template <int Q, bool COH>
+__device__ __forceinline__ void gradient_node(const Dom &d, int k) {
+  const bool own_blue = m_blue(ldv<COH>(d.mf + k));
+  float G[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const uint32_t e = nb_f(d, i, k);
+    const int idx = entry_idx(e);
+    const float m = (entry_cls(e) & 2) ? ldv<COH>(d.mf + idx) : ldv<COH>(d.ms + idx);
+    const float p = 3.f * Lattice<Q>::w(i) * m_excess(m, own_blue);
+    G[0] += (float)Lattice<Q>::ex(i) * p;
+    G[1] += (float)Lattice<Q>::ey(i) * p;
+    G[2] += (float)Lattice<Q>::ez(i) * p;
+  }
+  const float mag = sqrtf(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
+  if (!(mag > EPS_C)) {
+    d.ncf[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  const float im = 1.f / mag;
+  float nc[3] = {G[0] * im, G[1] * im, G[2] * im};
+  if (d.c.wetting && (__ldg(d.fflag + k) & 1u)) {
+    const float4 w4 = __ldg(d.nw + k);
+    const float nw[3] = {w4.x, w4.y, w4.z};
+    if (nw[0] != 0.f || nw[1] != 0.f || nw[2] != 0.f) {
+      if (d.c.wetting == 1)
+        scheme1(nc, nw, d.c.cos_t);
+      else
+        scheme2(nc, nw, d.c.cos_t, d.c.sin_t);
+    }
+  }
+  d.ncf[k] = make_float4(nc[0], nc[1], nc[2], mag);
+}
+
+// Eq. (35): n_c at solid-boundary node j = w-weighted mean of the fluid
+// neighbours' (post-wetting) n_c, not renormalised.
+template <int Q, bool COH>
+__device__ __forceinline__ void nc_solid_node(const Dom &d, int j) {
+  float num[3] = {0.f, 0.f, 0.f}, den = 0.f;
+  const int e = __ldg(d.soff + j + 1);
+  for (int p = __ldg(d.soff + j); p < e; ++p) {
+    const uint32_t l = __ldg(d.slink + p);
+    const float w = link_w<Q>(l);
+    const float4 v = ldv<COH>(d.ncf + (l & 0x7FFFFFFFu));
+    num[0] += w * v.x;
+    num[1] += w * v.y;
+    num[2] += w * v.z;
+    den += w;
+  }
+  const float id = 1.f / den;
+  d.ncs[j] = make_float4(num[0] * id, num[1] * id, num[2] * id, 0.f);
+}
+
+// Eq. (12) with d_b n_a by the Eq. (6) stencil on each component (off-box
+// neighbours clamped); returns kappa and the node's (n_c, |C|).
+template <int Q, bool COH>
+__device__ __forceinline__ float curvature(const Dom &d, int k, float4 &c4) {
+  float dn[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    const uint32_t e = nb_f(d, i, k);
+    const int idx = entry_idx(e);
+    const float4 v = (entry_cls(e) & 2) ? ldv<COH>(d.ncf + idx) : ldv<COH>(d.ncs + idx);
+    const float w3 = 3.f * Lattice<Q>::w(i);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int eb = Lattice<Q>::e(i, b);
+      if (eb == 0) continue;
+      dn[0][b] += w3 * (float)eb * v.x;
+      dn[1][b] += w3 * (float)eb * v.y;
+      dn[2][b] += w3 * (float)eb * v.z;
+    }
+  }
+  c4 = ldv<COH>(d.ncf + k);
+  const float nx_ = c4.x, ny_ = c4.y, nz_ = c4.z;
+  return (nx_ * nx_ - 1.f) * dn[0][0] + (ny_ * ny_ - 1.f) * dn[1][1] +
+         (nz_ * nz_ - 1.f) * dn[2][2] + (dn[0][1] + dn[1][0]) * nx_ * ny_ +
+         (dn[0][2] + dn[2][0]) * nx_ * nz_ + (dn[2][1] + dn[1][2]) * nz_ * ny_;
+}
+
+// Eq. (5) F = 1/2 gamma kappa C (C = |C| n_c) plus rho g (Eq. 36), the
+// collision (Eq. 2) of the stored f^t, and the store of the recoloured
+// state of fluid node k: f''_i and (q, v) with q the encoded rho^r/rho and
+// v = beta rho^r rho^b / rho n (Eqs. 20-21). The relaxation rate follows
+// the node's phase field (Eq. 39's value on the outlet plane).
+template <int Q, int ST, bool MACROS, bool COH>
+__device__ __forceinline__ void collide_node(const Dom &d, int k) {
+  using IO = TIO<Q, ST, COH>;
+  float4 c4;
+  const float kappa = curvature<Q, COH>(d, k, c4);
+  float ft[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) ft[i] = IO::load_from(d, d.U, i, k);
+  const float2 R = ldv<COH>(d.R + k);
+  const float rr = R.x, rb = R.y;
+  const float rho = rr + rb;
+  const float hk = 0.5f * d.c.gamma * kappa * c4.w;
+  const float F[3] = {hk * c4.x + rho * d.c.g[0], hk * c4.y + rho * d.c.g[1],
+                      hk * c4.z + rho * d.c.g[2]};
+  float u[3];
+  collide<Q>(d.c, ft, rho, F, m_phi(ldv<COH>(d.mf + k)), u);
+#pragma unroll
+  for (int i = 0; i < Q; ++i) IO::store(d, d.T_dst, i, k, ft[i]);
+  const float seg = d.c.beta * rr * rb / rho;
+  d.S_dst[k] = make_float4(m_of(rr, rb), seg * c4.x, seg * c4.y, seg * c4.z);
+  if (MACROS) d.macro[k] = make_float4(u[0], u[1], u[2], rho);
+}
+
+}  // namespace lbm

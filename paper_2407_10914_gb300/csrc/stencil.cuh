@@ -80,24 +80,37 @@ __device__ __forceinline__ float weight_of(int p) {
                 : (p <= (Q == 19 ? 6 : 4) ? Lattice<Q>::w(1) : Lattice<Q>::w(Q - 1));
 }
 
+// Loads of values that change from step to step. A kernel that never
+// writes what it reads takes them through the read-only path (__ldg). The
+// persistent batch kernel runs several passes in one launch, so it reads
+// values that other blocks wrote earlier in the same launch; it loads them
+// from L2, bypassing L1 (__ldcg): COH = true.
+template <bool COH, class T>
+__device__ __forceinline__ T ldv(const T *p) {
+  if constexpr (COH)
+    return __ldcg(p);
+  else
+    return __ldg(p);
+}
+
 // f''_i planes: float32, or 16-bit (f''_i/w_i - rho0) so that the stored
 // numbers are O(1e-2) deviations; arithmetic stays FP32.
-template <int Q, int ST>
+template <int Q, int ST, bool COH = false>
 struct TIO;
 
-template <int Q>
-struct TIO<Q, LBM_STORAGE_FP32> {
+template <int Q, bool COH>
+struct TIO<Q, LBM_STORAGE_FP32, COH> {
   __device__ __forceinline__ static float load_from(const Dom &d,
                                                    const void *buf, int i,
                                                    int k) {
-    return __ldg((const float *)buf + (long long)i * d.NFp + k);
+    return ldv<COH>((const float *)buf + (long long)i * d.NFp + k);
   }
   __device__ __forceinline__ static float load(const Dom &d, int i, int k) {
     return load_from(d, d.T_src, i, k);
   }
   // plane p chosen at run time, p in {i, opp(i)} (equal weights)
   __device__ __forceinline__ static float load_dyn(const Dom &d, int p, int k) {
-    return __ldg((const float *)d.T_src + (long long)p * d.NFp + k);
+    return ldv<COH>((const float *)d.T_src + (long long)p * d.NFp + k);
   }
   __device__ __forceinline__ static void store(const Dom &d, void *T, int i,
                                                int k, float v) {
@@ -105,12 +118,12 @@ struct TIO<Q, LBM_STORAGE_FP32> {
   }
 };
 
-template <int Q>
-struct TIO<Q, LBM_STORAGE_FP16> {
+template <int Q, bool COH>
+struct TIO<Q, LBM_STORAGE_FP16, COH> {
   __device__ __forceinline__ static float load_from(const Dom &d,
                                                    const void *buf, int i,
                                                    int k) {
-    const __half h = ((const __half *)buf)[(long long)i * d.NFp + k];
+    const __half h = ldv<COH>((const __half *)buf + (long long)i * d.NFp + k);
     return Lattice<Q>::w(i) * (__half2float(h) + d.c.rho0);
   }
   __device__ __forceinline__ static float load(const Dom &d, int i, int k) {
@@ -118,7 +131,7 @@ struct TIO<Q, LBM_STORAGE_FP16> {
   }
   // plane p at run time with the weight of w(p) = w(i) supplied by caller's i
   __device__ __forceinline__ static float load_dyn(const Dom &d, int p, int k) {
-    const __half h = ((const __half *)d.T_src)[(long long)p * d.NFp + k];
+    const __half h = ldv<COH>((const __half *)d.T_src + (long long)p * d.NFp + k);
     return weight_of<Q>(p) * (__half2float(h) + d.c.rho0);
   }
   __device__ __forceinline__ static void store(const Dom &d, void *T, int i,
@@ -128,13 +141,13 @@ struct TIO<Q, LBM_STORAGE_FP16> {
   }
 };
 
-template <int Q>
-struct TIO<Q, LBM_STORAGE_BF16> {
+template <int Q, bool COH>
+struct TIO<Q, LBM_STORAGE_BF16, COH> {
   __device__ __forceinline__ static float load_from(const Dom &d,
                                                    const void *buf, int i,
                                                    int k) {
     const __nv_bfloat16 h =
-        ((const __nv_bfloat16 *)buf)[(long long)i * d.NFp + k];
+        ldv<COH>((const __nv_bfloat16 *)buf + (long long)i * d.NFp + k);
     return Lattice<Q>::w(i) * (__bfloat162float(h) + d.c.rho0);
   }
   __device__ __forceinline__ static float load(const Dom &d, int i, int k) {
@@ -142,7 +155,7 @@ struct TIO<Q, LBM_STORAGE_BF16> {
   }
   __device__ __forceinline__ static float load_dyn(const Dom &d, int p, int k) {
     const __nv_bfloat16 h =
-        ((const __nv_bfloat16 *)d.T_src)[(long long)p * d.NFp + k];
+        ldv<COH>((const __nv_bfloat16 *)d.T_src + (long long)p * d.NFp + k);
     return weight_of<Q>(p) * (__bfloat162float(h) + d.c.rho0);
   }
   __device__ __forceinline__ static void store(const Dom &d, void *T, int i,

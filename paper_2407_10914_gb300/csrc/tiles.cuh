@@ -161,21 +161,22 @@ __device__ __forceinline__ uint32_t clamped_entry(const Dom &d,
 // Eq. (1) propagation through the neighbour table: f^s_i(x) = f^s_i'(x - e_i)
 // from a fluid source (entry of direction opp(i), which points to x - e_i),
 // else the halfway bounce-back f^s_opp(i)'(x).
-template <int Q, int ST>
+template <int Q, int ST, bool COH = false>
 __device__ __forceinline__ void pull_nb(const Dom &d, int k, float4 Sown,
                                         float *fr, float *fb) {
+  using IO = TIO<Q, ST, COH>;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     if (i == 0) {
-      rebuild<Q>(TIO<Q, ST>::load(d, 0, k), Sown, 0, fr[0], fb[0]);
+      rebuild<Q>(IO::load(d, 0, k), Sown, 0, fr[0], fb[0]);
       continue;
     }
     const uint32_t e =
         __ldg(d.nbf + (long long)(Lattice<Q>::opp(i) - 1) * d.NFp + k);
     const bool fl = (entry_cls(e) & 2) && !entry_out(e);
     const int src = fl ? entry_idx(e) : k;
-    const float T = TIO<Q, ST>::load_dyn(d, fl ? i : Lattice<Q>::opp(i), src);
-    const float4 S = fl ? __ldg(d.S_src + src) : Sown;
+    const float T = IO::load_dyn(d, fl ? i : Lattice<Q>::opp(i), src);
+    const float4 S = fl ? ldv<COH>(d.S_src + src) : Sown;
     const float ev = (float)Lattice<Q>::ex(i) * S.y +
                      (float)Lattice<Q>::ey(i) * S.z +
                      (float)Lattice<Q>::ez(i) * S.w;
@@ -187,24 +188,25 @@ __device__ __forceinline__ void pull_nb(const Dom &d, int k, float4 Sown,
 // planes: f^t_i = f^r_i + f^b_i (which is f''_i of the source, no colour
 // rebuild) and the colour densities rho^r, rho^b (the rebuilt colours
 // summed as they arrive), so no per-colour arrays stay live.
-template <int Q, int ST>
+template <int Q, int ST, bool COH = false>
 __device__ __forceinline__ void pull_sums(const Dom &d, int k, float4 Sown,
                                           float *ft, float &rr, float &rb) {
+  using IO = TIO<Q, ST, COH>;
   rr = 0.f;
   rb = 0.f;
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     float fr, fb;
     if (i == 0) {
-      ft[0] = TIO<Q, ST>::load(d, 0, k);
+      ft[0] = IO::load(d, 0, k);
       rebuild<Q>(ft[0], Sown, 0, fr, fb);
     } else {
       const uint32_t e =
           __ldg(d.nbf + (long long)(Lattice<Q>::opp(i) - 1) * d.NFp + k);
       const bool fl = (entry_cls(e) & 2) && !entry_out(e);
       const int src = fl ? entry_idx(e) : k;
-      ft[i] = TIO<Q, ST>::load_dyn(d, fl ? i : Lattice<Q>::opp(i), src);
-      const float4 S = fl ? __ldg(d.S_src + src) : Sown;
+      ft[i] = IO::load_dyn(d, fl ? i : Lattice<Q>::opp(i), src);
+      const float4 S = fl ? ldv<COH>(d.S_src + src) : Sown;
       const float ev = (float)Lattice<Q>::ex(i) * S.y +
                        (float)Lattice<Q>::ey(i) * S.z +
                        (float)Lattice<Q>::ez(i) * S.w;

@@ -32,7 +32,11 @@ EXPORTS = ("lbm_workspace_bytes", "lbm_init_geometry", "lbm_set_params",
            "lbm_reduce",
            "lbm_get_populations", "lbm_set_populations", "lbm_get_geometry",
            "lbm_counts", "lbm_colour_mass_noalloc", "lbm_last_error",
-           "lbm_destroy")
+           "lbm_destroy",
+           "lbm_batch_workspace_bytes", "lbm_batch_create",
+           "lbm_batch_set_config", "lbm_batch_step", "lbm_batch_status",
+           "lbm_batch_check_wait", "lbm_batch_last_error",
+           "lbm_batch_destroy")
 
 
 class LbmError(RuntimeError):
@@ -96,6 +100,24 @@ def load_library(path: str = LIB_PATH):
     L.lbm_last_error.argtypes = [vp]
     L.lbm_destroy.restype = None
     L.lbm_destroy.argtypes = [vp]
+    L.lbm_batch_workspace_bytes.restype = sz
+    L.lbm_batch_workspace_bytes.argtypes = [C.c_int]
+    L.lbm_batch_create.restype = C.c_int
+    L.lbm_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int, vp,
+                                   sz, vp]
+    L.lbm_batch_set_config.restype = C.c_int
+    L.lbm_batch_set_config.argtypes = [vp, C.c_int, C.c_int, C.c_int, vp]
+    L.lbm_batch_step.restype = C.c_int
+    L.lbm_batch_step.argtypes = [vp, C.c_int, vp]
+    L.lbm_batch_status.restype = C.c_int
+    L.lbm_batch_status.argtypes = [vp, vp]
+    L.lbm_batch_check_wait.restype = C.c_int
+    L.lbm_batch_check_wait.argtypes = [vp, C.c_double, C.POINTER(C.c_double),
+                                       vp]
+    L.lbm_batch_last_error.restype = C.c_char_p
+    L.lbm_batch_last_error.argtypes = [vp]
+    L.lbm_batch_destroy.restype = None
+    L.lbm_batch_destroy.argtypes = [vp]
     _lib = L
     return L
 
@@ -339,3 +361,101 @@ def session_for(case, storage: str = "fp32") -> Session:
     s.set_params(**case.params)
     s.init_state(case.phi0.astype(np.float32))
     return s
+
+
+# ------------------------------------------------------------------ batches
+def _bcheck(st: int, b=None, what: str = ""):
+    if st != LBM_OK:
+        msg = load_library().lbm_batch_last_error(b).decode() if b else ""
+        raise LbmError(f"{what}: {STATUS.get(st, st)} {msg}")
+
+
+def lbm_batch_workspace_bytes(ncases: int) -> int:
+    return int(load_library().lbm_batch_workspace_bytes(int(ncases)))
+
+
+def lbm_batch_create(handles, workspace, stream):
+    arr = (C.c_void_p * len(handles))(*[h.value if isinstance(h, C.c_void_p)
+                                        else h for h in handles])
+    out = C.c_void_p()
+    _bcheck(load_library().lbm_batch_create(
+        C.byref(out), arr, len(handles), C.c_void_p(workspace.data_ptr()),
+        workspace.numel() * workspace.element_size(), stream),
+        None, "lbm_batch_create")
+    return out
+
+
+def lbm_batch_set_config(b, mode: int, threads: int, chunk: int, stream):
+    _bcheck(load_library().lbm_batch_set_config(b, int(mode), int(threads),
+                                                int(chunk), stream),
+            b, "lbm_batch_set_config")
+
+
+def lbm_batch_step(b, nsteps: int, stream):
+    _bcheck(load_library().lbm_batch_step(b, int(nsteps), stream), b,
+            "lbm_batch_step")
+
+
+def lbm_batch_status(b, stream) -> int:
+    """The status code (LBM_OK or LBM_ERR_TIMEOUT), without raising."""
+    return int(load_library().lbm_batch_status(b, stream))
+
+
+def lbm_batch_check_wait(b, limit_ms: float, stream) -> float:
+    waited = C.c_double()
+    _bcheck(load_library().lbm_batch_check_wait(b, float(limit_ms),
+                                                C.byref(waited), stream),
+            b, "lbm_batch_check_wait")
+    return waited.value
+
+
+def lbm_batch_last_error(b) -> str:
+    return load_library().lbm_batch_last_error(b).decode()
+
+
+def lbm_batch_destroy(b):
+    load_library().lbm_batch_destroy(b)
+
+
+class Batch:
+    """Many Sessions stepped together (``lbm_batch_*``). Keeps the Sessions
+    alive; their results equal stepping each Session on its own."""
+
+    def __init__(self, sessions):
+        if not sessions:
+            raise LbmError("empty batch")
+        self.sessions = list(sessions)
+        torch = self.sessions[0].torch
+        self.torch = torch
+        dev = self.sessions[0].device
+        ws = lbm_batch_workspace_bytes(len(self.sessions))
+        self.workspace = torch.empty(ws, dtype=torch.uint8, device=dev)
+        self.b = lbm_batch_create([s.h for s in self.sessions],
+                                  self.workspace, self.stream())
+        self.config = (0, 256, 4)
+
+    def stream(self):
+        return _stream(self.torch)
+
+    def __del__(self):
+        b = getattr(self, "b", None)
+        if b:
+            lbm_batch_destroy(b)
+            self.b = None
+
+    @property
+    def n_fluid(self) -> int:
+        return sum(s.n_fluid for s in self.sessions)
+
+    def set_config(self, mode: int, threads: int = 256, chunk: int = 4):
+        lbm_batch_set_config(self.b, mode, threads, chunk, self.stream())
+        self.config = (int(mode), int(threads), int(chunk))
+
+    def step(self, n: int = 1):
+        lbm_batch_step(self.b, n, self.stream())
+
+    def status(self) -> int:
+        return lbm_batch_status(self.b, self.stream())
+
+    def check_wait(self, limit_ms: float) -> float:
+        return lbm_batch_check_wait(self.b, limit_ms, self.stream())

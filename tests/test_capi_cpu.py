@@ -69,3 +69,23 @@ def test_init_geometry_rejects_bad_arguments(lib):
     assert lib.lbm_init_geometry(C.byref(h), 19, 2, 2, 2, sp, 7, 0, fake_ws,
                                  16, None) == -6
     assert not h.value
+
+
+def test_batch_entry_points_host_only(lib):
+    """Batch sizes and argument checks that need no GPU."""
+    from paper_2407_10914_gb300 import lbm
+    n1 = lbm.lbm_batch_workspace_bytes(1)
+    n96 = lbm.lbm_batch_workspace_bytes(96)
+    assert lbm.lbm_batch_workspace_bytes(0) == 0
+    assert 0 < n1 < n96 < 96 * 4096
+    out = C.c_void_p()
+    arr = (C.c_void_p * 1)(None)
+    # a null handle, no cases, a null workspace: rejected before any CUDA call
+    assert lib.lbm_batch_create(C.byref(out), arr, 1, C.c_void_p(256), n1,
+                                None) == -1
+    assert lib.lbm_batch_create(C.byref(out), arr, 0, C.c_void_p(256), n1,
+                                None) == -1
+    assert lib.lbm_batch_create(None, arr, 1, C.c_void_p(256), n1, None) == -1
+    assert lib.lbm_batch_step(None, 1, None) == -1
+    assert lib.lbm_batch_set_config(None, 0, 256, 1, None) == -1
+    assert lib.lbm_batch_last_error(None) == b"null batch"
