@@ -82,6 +82,10 @@ def parse():
     ap.add_argument("--size", type=int, default=256)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the 96-drop batched sweep object")
+    ap.add_argument("--batched-cases", type=int, default=96)
+    ap.add_argument("--batched-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -331,6 +335,10 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = end_to_end(args, case, torch, lbm)
 
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(args, torch, lbm)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(case, 32, 6, 0)
@@ -376,6 +384,8 @@ def run_ours(args):
         }
         if e2e:
             line["e2e"] = e2e
+        if batched:
+            line["batched"] = batched
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)
@@ -431,6 +441,57 @@ def end_to_end(args, case, torch, lbm):
             "final_sw": sw, "seconds": round(dt, 3),
             "note": "geometry set-up, phi0 upload, per-step S_w read-back "
                     "and the final phi download inside the timed region"}
+
+
+def run_batched(args, torch, lbm):
+    """The contact-angle sweep: 96 D3Q19 sessile drops in boxes of 48^3 to
+    128^3 (Scheme-I and Scheme-II, theta 30-150 deg), stepped together by
+    one batch. The schedule is chosen by the autotuner (its trials are
+    reported too); the value is fluid-node updates per second over all
+    cases, CUDA events around `batched-steps` steps."""
+    from paper_2407_10914_gb300 import autotune
+    from paper_2407_10914_gb300 import workloads as W
+    t0 = time.time()
+    cases = W.batched_droplets(count=args.batched_cases)
+    sess = []
+    for c in cases:
+        s = lbm.Session(c.lattice, c.solid, c.periodic, args.storage)
+        s.set_params(**c.params)
+        s.init_state(c.phi0.astype(np.float32))
+        sess.append(s)
+    b = lbm.Batch(sess)
+    setup_s = time.time() - t0
+    tune = autotune.tune(b, trial_steps=4, use_cache=False)
+    stream = torch.cuda.current_stream()
+    b.step(1)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.step(args.batched_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.batched_steps
+    if b.status() != 0:
+        raise SystemExit("batched sweep: a persistent-kernel wait ran out")
+    nf = b.n_fluid
+    sides = sorted(int(c.solid.shape[0]) for c in cases)
+    out = {
+        "workload": f"batch{len(cases)}_sessile_drops_{args.storage}",
+        "cases": len(cases), "box_sides": [sides[0], sides[-1]],
+        "fluid_nodes": nf,
+        "nodes": int(sum(c.n_nodes for c in cases)),
+        "value": round(nf / (ms * 1e-3) / 1e6, 2), "unit": "MLUPS",
+        "ms_per_step": round(ms, 4), "steps": args.batched_steps,
+        "schedule": {"mode": ["level launches", "persistent"][tune["config"][0]],
+                     "threads": tune["config"][1], "chunk": tune["config"][2]},
+        "tuning_ms_per_step": tune.get("trials"),
+        "setup_s": round(setup_s, 1),
+        "parity": "bit-identical to stepping each case alone (tests/test_gpu_batch.py)",
+    }
+    del b, sess
+    torch.cuda.empty_cache()
+    return out
 
 
 def main():

@@ -110,4 +110,4 @@ def tune(batch, trial_steps: int = 8, cache_path: Optional[str] = None,
     if use_cache:
         store_cache(path, key, entry)
     return {"config": best, "key": key, "cached": False, "steps_used": used,
-            "ms_per_step": timings[best]}
+            "ms_per_step": timings[best], "trials": entry["trials"]}
