@@ -11,6 +11,11 @@
 // Sec. II.B.3, over plain loops, in double precision. OpenMP only splits the
 // node loops; nothing is blocked, fused or reordered.
 //
+// The step is templated on its scalar: double for the oracle itself, and a
+// forward-mode dual number (value and derivatives with respect to the
+// contact angle and the body acceleration g_x) for the tangent-linear
+// reference of the adjoint (orc_tlm_*). Both run the same code.
+//
 // Layout (the public convention of this project, stated independently here):
 //   node n = x + nx*(y + ny*z), x fastest;
 //   populations f[(s*Q + i)*N + n], s = 0 red ("r"), s = 1 blue ("b");
@@ -64,6 +69,72 @@ const int E_D3Q19[19][3] = {
     {-1, -1, 0}, {1, 0, 1},  {-1, 0, 1}, {1, 0, -1}, {-1, 0, -1},
     {0, 1, 1},  {0, -1, 1},  {0, 1, -1}, {0, -1, -1}};
 
+// Forward-mode derivatives for the tangent-linear run: a value and its
+// derivatives along two directions (the contact angle in radians and the
+// body acceleration g_x). Every operation applies the chain rule; a
+// comparison looks at the value only, so a branch follows the value's path.
+struct Dual {
+  double v = 0.0;
+  double d[2] = {0.0, 0.0};
+  Dual() = default;
+  Dual(double x) : v(x) {}  // a constant: zero derivatives
+  Dual(double x, double d0, double d1) : v(x), d{d0, d1} {}
+  Dual &operator+=(const Dual &b) { return *this = *this + b; }
+  Dual &operator-=(const Dual &b) { return *this = *this - b; }
+  Dual &operator*=(const Dual &b) { return *this = *this * b; }
+  Dual &operator/=(const Dual &b) { return *this = *this / b; }
+  friend Dual operator+(const Dual &a, const Dual &b) {
+    return Dual(a.v + b.v, a.d[0] + b.d[0], a.d[1] + b.d[1]);
+  }
+  friend Dual operator-(const Dual &a, const Dual &b) {
+    return Dual(a.v - b.v, a.d[0] - b.d[0], a.d[1] - b.d[1]);
+  }
+  friend Dual operator-(const Dual &a) { return Dual(-a.v, -a.d[0], -a.d[1]); }
+  friend Dual operator*(const Dual &a, const Dual &b) {
+    return Dual(a.v * b.v, a.d[0] * b.v + a.v * b.d[0],
+                a.d[1] * b.v + a.v * b.d[1]);
+  }
+  friend Dual operator/(const Dual &a, const Dual &b) {
+    const double q = a.v / b.v;
+    return Dual(q, (a.d[0] - q * b.d[0]) / b.v, (a.d[1] - q * b.d[1]) / b.v);
+  }
+  friend bool operator<(const Dual &a, const Dual &b) { return a.v < b.v; }
+  friend bool operator>(const Dual &a, const Dual &b) { return a.v > b.v; }
+  friend bool operator<=(const Dual &a, const Dual &b) { return a.v <= b.v; }
+  friend bool operator>=(const Dual &a, const Dual &b) { return a.v >= b.v; }
+  friend bool operator==(const Dual &a, const Dual &b) { return a.v == b.v; }
+  friend bool operator!=(const Dual &a, const Dual &b) { return a.v != b.v; }
+};
+
+// d/dx of sqrt, acos, sin, cos, |x|; the plain double versions alongside so
+// that templated code calls one name for both.
+inline Dual sqrt(const Dual &a) {
+  const double r = std::sqrt(a.v);
+  return Dual(r, a.d[0] / (2.0 * r), a.d[1] / (2.0 * r));
+}
+inline Dual acos(const Dual &a) {
+  const double k = -1.0 / std::sqrt(1.0 - a.v * a.v);
+  return Dual(std::acos(a.v), k * a.d[0], k * a.d[1]);
+}
+inline Dual sin(const Dual &a) {
+  const double c = std::cos(a.v);
+  return Dual(std::sin(a.v), c * a.d[0], c * a.d[1]);
+}
+inline Dual cos(const Dual &a) {
+  const double s = -std::sin(a.v);
+  return Dual(std::cos(a.v), s * a.d[0], s * a.d[1]);
+}
+inline Dual fabs(const Dual &a) { return a.v < 0.0 ? -a : a; }
+inline double sqrt(double a) { return std::sqrt(a); }
+inline double acos(double a) { return std::acos(a); }
+inline double sin(double a) { return std::sin(a); }
+inline double cos(double a) { return std::cos(a); }
+inline double fabs(double a) { return std::fabs(a); }
+template <class R>
+R clamp1(const R &x) {  // x limited to [-1, 1]
+  return x < R(-1.0) ? R(-1.0) : (x > R(1.0) ? R(1.0) : x);
+}
+
 Lattice make_lattice(int q) {
   Lattice L;
   if (q == 19) {
@@ -116,7 +187,10 @@ typedef struct {
 
 namespace {
 
-struct Oracle {
+// R: the scalar of everything the step computes (double for the oracle,
+// Dual for its tangent-linear run). The geometry stays double.
+template <class R>
+struct OracleT {
   Lattice L;
   int nx, ny, nz;
   long N;
@@ -125,11 +199,13 @@ struct Oracle {
   std::vector<uint8_t> solid, cls;
   std::vector<double> gsm;   // smoothed indicator g^(3), Eq. (25)
   std::vector<double> nw;    // wall normal, Eq. (26), 3N
-  std::vector<double> f, ftmp;  // stored post-recolouring populations, 2QN
-  std::vector<double> rho_r, rho_b, phi;  // per node macros of the step
-  std::vector<double> C, nc;  // colour gradient and unit normal, 3N
-  std::vector<double> kappa, F;  // curvature and force (3N)
-  std::vector<double> u;         // velocity of Eq. (22), 3N
+  std::vector<R> f, ftmp;  // stored post-recolouring populations, 2QN
+  std::vector<R> rho_r, rho_b, phi;  // per node macros of the step
+  std::vector<R> C, nc;  // colour gradient and unit normal, 3N
+  std::vector<R> kappa, F;  // curvature and force (3N)
+  std::vector<R> u;         // velocity of Eq. (22), 3N
+  R theta;                  // contact angle (radians) of p.theta_deg
+  R g[3];                   // body acceleration p.g
   long n_fluid = 0;
 
   int dim(int a) const { return a == 0 ? nx : (a == 1 ? ny : nz); }
@@ -168,7 +244,15 @@ struct Oracle {
 
   bool is_fluid(long n) const { return n >= 0 && !solid[n]; }
   bool is_solid(long n) const { return n >= 0 && solid[n]; }
-  double &fp(int s, int i, long n) { return f[((long)s * L.Q + i) * N + n]; }
+  R &fp(int s, int i, long n) { return f[((long)s * L.Q + i) * N + n]; }
+
+  // Parameters; theta and g carry the derivative seeds of the tangent-linear
+  // run (direction 0: theta, direction 1: g_x).
+  void set_params(const orc_params &q, const R &th, const R gg[3]) {
+    p = q;
+    theta = th;
+    for (int a = 0; a < 3; ++a) g[a] = gg[a];
+  }
 
   // ---------------------------------------------------------------- geometry
   // Node classes from the solid image: a fluid node with a solid lattice
@@ -254,8 +338,8 @@ struct Oracle {
         int d[3] = {-L.e[i][0], -L.e[i][1], -L.e[i][2]};
         long src = neighbour(n, d, false);
         for (int s = 0; s < 2; ++s) {
-          double v = is_fluid(src) ? f[((long)s * L.Q + i) * N + src]
-                                   : f[((long)s * L.Q + L.opp[i]) * N + n];
+          R v = is_fluid(src) ? f[((long)s * L.Q + i) * N + src]
+                              : f[((long)s * L.Q + L.opp[i]) * N + n];
           ftmp[((long)s * L.Q + i) * N + n] = v;
         }
       }
@@ -267,7 +351,7 @@ struct Oracle {
 #pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
       if (solid[n]) continue;
-      double r = 0.0, b = 0.0;
+      R r = 0.0, b = 0.0;
       for (int i = 0; i < L.Q; ++i) {
         r += ftmp[(0L * L.Q + i) * N + n];
         b += ftmp[(1L * L.Q + i) * N + n];
@@ -304,10 +388,10 @@ struct Oracle {
       if (c[a] == 0) inlet.push_back(n);
       if (c[a] == na - 1) outlet.push_back(n);
     }
-    auto F_ = [&](int s, int i, long n) -> double & {
+    auto F_ = [&](int s, int i, long n) -> R & {
       return ftmp[((long)s * L.Q + i) * N + n];
     };
-    auto transverse = [&](int s, long n, double Nt[3]) {
+    auto transverse = [&](int s, long n, R Nt[3]) {
       for (int t = 0; t < 3; ++t) Nt[t] = 0.0;
       for (int j = 0; j < L.Q; ++j) {
         if (L.e[j][a] != 0) continue;
@@ -316,7 +400,7 @@ struct Oracle {
       }
     };
     // phase field of the outlet nodes from the plane behind them, Eq. (39)
-    std::vector<double> phi_out(outlet.size());
+    std::vector<R> phi_out(outlet.size());
     for (size_t k = 0; k < outlet.size(); ++k) {
       long n = outlet[k];
       int d[3] = {0, 0, 0};
@@ -326,17 +410,17 @@ struct Oracle {
     }
     for (long n : inlet) {
       for (int s = 0; s < 2; ++s) {
-        double known = 0.0;
+        R known = 0.0;
         for (int i = 0; i < L.Q; ++i) {
           if (L.e[i][a] == 0) known += F_(s, i, n);
           if (L.e[i][a] == -1) known += 2.0 * F_(s, i, n);
         }
-        double j = p.rho_in * zeta[s] - known;
-        double Nt[3];
+        R j = p.rho_in * zeta[s] - known;
+        R Nt[3];
         transverse(s, n, Nt);
         for (int i = 0; i < L.Q; ++i) {
           if (L.e[i][a] != 1) continue;
-          double corr = 0.0;
+          R corr = 0.0;
           for (int t = 0; t < 3; ++t)
             if (t != a) corr += L.e[i][t] * Nt[t];
           F_(s, i, n) = F_(s, L.opp[i], n) + 6.0 * L.w[i] * j - corr;
@@ -345,20 +429,20 @@ struct Oracle {
     }
     for (size_t k = 0; k < outlet.size(); ++k) {
       long n = outlet[k];
-      double known = 0.0;
+      R known = 0.0;
       for (int i = 0; i < L.Q; ++i) {
-        double ft = F_(0, i, n) + F_(1, i, n);
+        R ft = F_(0, i, n) + F_(1, i, n);
         if (L.e[i][a] == 0) known += ft;
         if (L.e[i][a] == 1) known += 2.0 * ft;
       }
-      double jt = -p.rho_out + known;
-      double chi[2] = {0.5 * (1.0 + phi_out[k]), 0.5 * (1.0 - phi_out[k])};
+      R jt = -p.rho_out + known;
+      R chi[2] = {0.5 * (1.0 + phi_out[k]), 0.5 * (1.0 - phi_out[k])};
       for (int s = 0; s < 2; ++s) {
-        double Nt[3];
+        R Nt[3];
         transverse(s, n, Nt);
         for (int i = 0; i < L.Q; ++i) {
           if (L.e[i][a] != -1) continue;
-          double corr = 0.0;
+          R corr = 0.0;
           for (int t = 0; t < 3; ++t)
             if (t != a) corr += L.e[i][t] * Nt[t];
           F_(s, i, n) = F_(s, L.opp[i], n) - 6.0 * L.w[i] * jt * chi[s] - corr;
@@ -367,7 +451,7 @@ struct Oracle {
     }
     // densities of the rebuilt nodes, then the phase-field overrides
     auto resum = [&](long n) {
-      double r = 0.0, b = 0.0;
+      R r = 0.0, b = 0.0;
       for (int i = 0; i < L.Q; ++i) {
         r += F_(0, i, n);
         b += F_(1, i, n);
@@ -391,7 +475,8 @@ struct Oracle {
 #pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
       if (cls[n] != CLS_SOLID_BND) continue;
-      double num = 0.0, den = 0.0;
+      R num = 0.0;
+        double den = 0.0;
       for (int i = 1; i < L.Q; ++i) {
         long m = neighbour(n, L.e[i], false);
         if (!is_fluid(m)) continue;
@@ -409,24 +494,24 @@ struct Oracle {
 #pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
       if (solid[n]) continue;
-      double G[3] = {0, 0, 0};
+      R G[3] = {0.0, 0.0, 0.0};
       for (int i = 1; i < L.Q; ++i) {
-        double ph = phi[neighbour(n, L.e[i], true)];
+        R ph = phi[neighbour(n, L.e[i], true)];
         for (int a = 0; a < 3; ++a) G[a] += 3.0 * L.w[i] * L.e[i][a] * ph;
       }
-      double m = std::sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
+      R m = sqrt(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
       for (int a = 0; a < 3; ++a) {
-        C[a * N + n] = (m > EPS_C) ? G[a] : 0.0;
-        nc[a * N + n] = (m > EPS_C) ? G[a] / m : 0.0;
+        C[a * N + n] = (m > EPS_C) ? G[a] : R(0.0);
+        nc[a * N + n] = (m > EPS_C) ? G[a] / m : R(0.0);
       }
     }
   }
 
   // Eq. (28): f(v) = v . n_w - |v| cos(theta)
-  static double secant_residual(const double v[3], const double w[3],
-                                double cth) {
-    double vn = v[0] * w[0] + v[1] * w[1] + v[2] * w[2];
-    double vv = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  template <class T>
+  static T secant_residual(const T v[3], const double w[3], const T &cth) {
+    T vn = v[0] * w[0] + v[1] * w[1] + v[2] * w[2];
+    T vv = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
     return vn - vv * cth;
   }
 
@@ -438,28 +523,29 @@ struct Oracle {
   // EPS_SECANT the iteration stops and keeps v_{n-1}; if the final vector
   // has zero length n_c is left unchanged (the degenerate cases of Sec.
   // II.B.1, last paragraph).
-  static void scheme1(const double n_c[3], const double n_w[3], double theta,
-                      double out[3]) {
+  template <class T>
+  static void scheme1(const T n_c[3], const double n_w[3], const T &theta,
+                      T out[3]) {
     const double lambda = 0.5;
-    const double cth = std::cos(theta);
-    double vm2[3], vm1[3];
+    const T cth = cos(theta);
+    T vm2[3], vm1[3];
     for (int a = 0; a < 3; ++a) {
       vm2[a] = n_c[a];
       vm1[a] = n_c[a] - lambda * (n_c[a] + n_w[a]);
     }
     for (int it = 2; it <= 4; ++it) {
-      double f1 = secant_residual(vm1, n_w, cth);
-      double f2 = secant_residual(vm2, n_w, cth);
-      double den = f1 - f2;
-      if (std::fabs(den) < EPS_SECANT) break;
-      double vn[3];
+      T f1 = secant_residual(vm1, n_w, cth);
+      T f2 = secant_residual(vm2, n_w, cth);
+      T den = f1 - f2;
+      if (fabs(den) < EPS_SECANT) break;
+      T vn[3];
       for (int a = 0; a < 3; ++a) vn[a] = (vm2[a] * f1 - vm1[a] * f2) / den;
       for (int a = 0; a < 3; ++a) {
         vm2[a] = vm1[a];
         vm1[a] = vn[a];
       }
     }
-    double m = std::sqrt(vm1[0] * vm1[0] + vm1[1] * vm1[1] + vm1[2] * vm1[2]);
+    T m = sqrt(vm1[0] * vm1[0] + vm1[1] * vm1[1] + vm1[2] * vm1[2]);
     for (int a = 0; a < 3; ++a) out[a] = (m > 0.0) ? vm1[a] / m : n_c[a];
   }
 
@@ -468,23 +554,24 @@ struct Oracle {
   //        + sin(+-theta)/sin(theta') n_c;
   // n_c is replaced by whichever of n_+ and n_- lies nearer to n_c (n_+ on a
   // tie). Left unchanged when sin(theta') < EPS_SIN.
-  static void scheme2(const double n_c[3], const double n_w[3], double theta,
-                      double out[3]) {
-    double c = n_w[0] * n_c[0] + n_w[1] * n_c[1] + n_w[2] * n_c[2];
-    c = std::min(1.0, std::max(-1.0, c));
-    double thp = std::acos(c);
-    double sp = std::sin(thp);
+  template <class T>
+  static void scheme2(const T n_c[3], const double n_w[3], const T &theta,
+                      T out[3]) {
+    T c = n_c[0] * n_w[0] + n_c[1] * n_w[1] + n_c[2] * n_w[2];
+    c = clamp1(c);
+    T thp = acos(c);
+    T sp = sin(thp);
     if (sp < EPS_SIN) {
       for (int a = 0; a < 3; ++a) out[a] = n_c[a];
       return;
     }
-    double cp = std::cos(thp);
-    double np[3], nm[3];
-    double dp = 0.0, dm = 0.0;
+    T cp = cos(thp);
+    T np[3], nm[3];
+    T dp = 0.0, dm = 0.0;
     for (int a = 0; a < 3; ++a) {
-      double sgn_p = std::sin(theta), sgn_m = std::sin(-theta);
-      np[a] = (std::cos(theta) - sgn_p * cp / sp) * n_w[a] + sgn_p / sp * n_c[a];
-      nm[a] = (std::cos(-theta) - sgn_m * cp / sp) * n_w[a] + sgn_m / sp * n_c[a];
+      T sgn_p = sin(theta), sgn_m = sin(-theta);
+      np[a] = (cos(theta) - sgn_p * cp / sp) * n_w[a] + sgn_p / sp * n_c[a];
+      nm[a] = (cos(-theta) - sgn_m * cp / sp) * n_w[a] + sgn_m / sp * n_c[a];
       dp += (np[a] - n_c[a]) * (np[a] - n_c[a]);
       dm += (nm[a] - n_c[a]) * (nm[a] - n_c[a]);
     }
@@ -496,12 +583,13 @@ struct Oracle {
   // angle with Scheme-I or Scheme-II; the magnitude |C| is kept, so the
   // colour gradient becomes |C| n_c (Sec. II.B.1).
   void wetting() {
-    const double theta = p.theta_deg * PI / 180.0;
 #pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
       if (cls[n] != CLS_FLUID_BND) continue;
-      double ncv[3], nwv[3], out[3];
-      double m2 = 0.0, w2 = 0.0;
+      R ncv[3], out[3];
+      double nwv[3];
+      R m2 = 0.0;
+      double w2 = 0.0;
       for (int a = 0; a < 3; ++a) {
         ncv[a] = nc[a * N + n];
         nwv[a] = nw[a * N + n];
@@ -513,9 +601,9 @@ struct Oracle {
         scheme1(ncv, nwv, theta, out);
       else
         scheme2(ncv, nwv, theta, out);
-      double mag = 0.0;
+      R mag = 0.0;
       for (int a = 0; a < 3; ++a) mag += C[a * N + n] * C[a * N + n];
-      mag = std::sqrt(mag);
+      mag = sqrt(mag);
       for (int a = 0; a < 3; ++a) {
         nc[a * N + n] = out[a];
         C[a * N + n] = mag * out[a];
@@ -529,7 +617,8 @@ struct Oracle {
 #pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
       if (cls[n] != CLS_SOLID_BND) continue;
-      double num[3] = {0, 0, 0}, den = 0.0;
+      R num[3] = {0.0, 0.0, 0.0};
+      double den = 0.0;
       for (int i = 1; i < L.Q; ++i) {
         long m = neighbour(n, L.e[i], false);
         if (!is_fluid(m)) continue;
@@ -547,23 +636,23 @@ struct Oracle {
 #pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
       if (solid[n]) continue;
-      double dn[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};  // dn[a][b] = d_b n_a
+      R dn[3][3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};  // d_b n_a
       for (int i = 1; i < L.Q; ++i) {
         long m = neighbour(n, L.e[i], true);
         for (int a = 0; a < 3; ++a)
           for (int b = 0; b < 3; ++b)
             dn[a][b] += 3.0 * L.w[i] * L.e[i][b] * nc[a * N + m];
       }
-      double nx_ = nc[0 * N + n], ny_ = nc[1 * N + n], nz_ = nc[2 * N + n];
-      double k = (nx_ * nx_ - 1.0) * dn[0][0] + (ny_ * ny_ - 1.0) * dn[1][1] +
+      R nx_ = nc[0 * N + n], ny_ = nc[1 * N + n], nz_ = nc[2 * N + n];
+      R k = (nx_ * nx_ - 1.0) * dn[0][0] + (ny_ * ny_ - 1.0) * dn[1][1] +
                  (nz_ * nz_ - 1.0) * dn[2][2] +
                  (dn[0][1] + dn[1][0]) * nx_ * ny_ +
                  (dn[0][2] + dn[2][0]) * nx_ * nz_ +
                  (dn[2][1] + dn[1][2]) * nz_ * ny_;
       kappa[n] = k;
-      double rho = rho_r[n] + rho_b[n];
+      R rho = rho_r[n] + rho_b[n];
       for (int a = 0; a < 3; ++a)
-        F[a * N + n] = 0.5 * p.gamma * k * C[a * N + n] + rho * p.g[a];
+        F[a * N + n] = 0.5 * p.gamma * k * C[a * N + n] + rho * g[a];
     }
   }
 
@@ -581,24 +670,25 @@ struct Oracle {
   // first two that would relax the conserved momentum: the post-collision
   // momentum is exactly j + F and the mass is unchanged. u is Eq. (22):
   // u = (sum_i e_i f_i + F/2) / rho.
-  static void collide(const Lattice &L, const double *ft, const double Fv[3],
-                      double S, double rho0, double *out, double u_out[3]) {
-    double rho = 0.0, j[3] = {0, 0, 0};
+  template <class T>
+  static void collide(const Lattice &L, const T *ft, const T Fv[3], const T &S,
+                      double rho0, T *out, T u_out[3]) {
+    T rho = 0.0, j[3] = {0.0, 0.0, 0.0};
     for (int i = 0; i < L.Q; ++i) {
       rho += ft[i];
       for (int a = 0; a < 3; ++a) j[a] += L.e[i][a] * ft[i];
     }
     double E2 = 0.0;
     for (int i = 0; i < L.Q; ++i) E2 += L.e[i][0] * L.e[i][0];
-    double u[3], back[3];
+    T u[3], back[3];
     for (int a = 0; a < 3; ++a) u[a] = (j[a] + 0.5 * Fv[a]) / rho;
     for (int a = 0; a < 3; ++a)
       back[a] = S * (j[a] - rho0 * u[a] + 0.5 * Fv[a]) / E2;
-    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    T uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     for (int i = 0; i < L.Q; ++i) {
-      double eu = L.e[i][0] * u[0] + L.e[i][1] * u[1] + L.e[i][2] * u[2];
-      double feq = L.w[i] * (rho + rho0 * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
-      double guo = 0.0, cons = 0.0;
+      T eu = L.e[i][0] * u[0] + L.e[i][1] * u[1] + L.e[i][2] * u[2];
+      T feq = L.w[i] * (rho + rho0 * (3.0 * eu + 4.5 * eu * eu - 1.5 * uu));
+      T guo = 0.0, cons = 0.0;
       for (int a = 0; a < 3; ++a) {
         guo += (3.0 * (L.e[i][a] - u[a]) + 9.0 * eu * L.e[i][a]) * Fv[a];
         cons += L.e[i][a] * back[a];
@@ -613,11 +703,11 @@ struct Oracle {
  private:
   // Eqs. (13)-(14): harmonic-mean viscosity, S_nu = 1 / (3 nu + 1/2);
   // phi is clamped to [-1, 1] here only.
-  double relaxation_rate(double ph) const {
+  R relaxation_rate(const R &ph) const {
     double nur = (p.tau_r - 0.5) / 3.0, nub = (p.tau_b - 0.5) / 3.0;
-    double pc = std::min(1.0, std::max(-1.0, ph));
-    double inv_nu = (1.0 + pc) / (2.0 * nur) + (1.0 - pc) / (2.0 * nub);
-    double nu = 1.0 / inv_nu;
+    R pc = clamp1(ph);
+    R inv_nu = (1.0 + pc) / (2.0 * nur) + (1.0 - pc) / (2.0 * nub);
+    R nu = 1.0 / inv_nu;
     return 1.0 / (3.0 * nu + 0.5);
   }
 
@@ -630,18 +720,18 @@ struct Oracle {
 #pragma omp parallel for schedule(static)
     for (long n = 0; n < N; ++n) {
       if (solid[n]) continue;
-      double ft[19], fpp[19], Fv[3], uu[3];
+      R ft[19], fpp[19], Fv[3], uu[3];
       for (int i = 0; i < L.Q; ++i)
         ft[i] = ftmp[(0L * L.Q + i) * N + n] + ftmp[(1L * L.Q + i) * N + n];
       for (int a = 0; a < 3; ++a) Fv[a] = F[a * N + n];
-      double S = relaxation_rate(phi[n]);
+      R S = relaxation_rate(phi[n]);
       collide(L, ft, Fv, S, p.rho0, fpp, uu);
       for (int a = 0; a < 3; ++a) u[a * N + n] = uu[a];
-      double r = rho_r[n], b = rho_b[n], rho = r + b;
-      double nv[3] = {nc[0 * N + n], nc[1 * N + n], nc[2 * N + n]};
+      R r = rho_r[n], b = rho_b[n], rho = r + b;
+      R nv[3] = {nc[0 * N + n], nc[1 * N + n], nc[2 * N + n]};
       for (int i = 0; i < L.Q; ++i) {
-        double en = L.e[i][0] * nv[0] + L.e[i][1] * nv[1] + L.e[i][2] * nv[2];
-        double fr = r / rho * fpp[i] + p.beta * L.w[i] * r * b / rho * en;
+        R en = L.e[i][0] * nv[0] + L.e[i][1] * nv[1] + L.e[i][2] * nv[2];
+        R fr = r / rho * fpp[i] + p.beta * L.w[i] * r * b / rho * en;
         f[(0L * L.Q + i) * N + n] = fr;
         f[(1L * L.Q + i) * N + n] = fpp[i] - fr;
       }
@@ -672,16 +762,18 @@ struct Oracle {
     F.assign(3 * N, 0.0);
     u.assign(3 * N, 0.0);
     std::memset(&p, 0, sizeof(p));
+    theta = 0.0;
+    for (int a = 0; a < 3; ++a) g[a] = 0.0;
   }
 
   // Initial state: f^s_i = w_i rho^s with rho^r = rho0 (1 + phi0)/2 and
   // rho^b = rho0 (1 - phi0)/2 (a fluid at rest).
   void init_state(const double *phi0) {
-    std::fill(f.begin(), f.end(), 0.0);
+    std::fill(f.begin(), f.end(), R(0.0));
     for (long n = 0; n < N; ++n) {
       if (solid[n]) continue;
-      double r = p.rho0 * 0.5 * (1.0 + phi0[n]);
-      double b = p.rho0 * 0.5 * (1.0 - phi0[n]);
+      R r = p.rho0 * 0.5 * (1.0 + phi0[n]);
+      R b = p.rho0 * 0.5 * (1.0 - phi0[n]);
       for (int i = 0; i < L.Q; ++i) {
         f[(0L * L.Q + i) * N + n] = L.w[i] * r;
         f[(1L * L.Q + i) * N + n] = L.w[i] * b;
@@ -690,7 +782,7 @@ struct Oracle {
       rho_b[n] = b;
       phi[n] = (r - b) / (r + b);
     }
-    std::fill(u.begin(), u.end(), 0.0);
+    std::fill(u.begin(), u.end(), R(0.0));
   }
 
   // One time step in the order of Eq. (1) and Sec. II.B.3: stream (with
@@ -714,6 +806,8 @@ struct Oracle {
   }
 };
 
+using Oracle = OracleT<double>;
+
 }  // namespace
 
 extern "C" {
@@ -730,7 +824,7 @@ void *orc_create(int lattice, int nx, int ny, int nz, const uint8_t *solid,
 void orc_destroy(void *h) { delete static_cast<Oracle *>(h); }
 
 void orc_set_params(void *h, const orc_params *p) {
-  static_cast<Oracle *>(h)->p = *p;
+  static_cast<Oracle *>(h)->set_params(*p, p->theta_deg * PI / 180.0, p->g);
 }
 
 void orc_init_state(void *h, const double *phi0) {
@@ -885,6 +979,52 @@ void orc_collide(int lattice, const double *ft, const double *F, double S,
                  double rho0, double *out, double *u) {
   Lattice L = make_lattice(lattice);
   Oracle::collide(L, ft, F, S, rho0, out, u);
+}
+
+// ---- tangent-linear run ----------------------------------------------------
+// The same step on Dual numbers: every field carries its derivatives with
+// respect to the contact angle theta (radians; direction 0) and the body
+// acceleration g_x (direction 1), seeded in orc_tlm_set_params.
+
+void *orc_tlm_create(int lattice, int nx, int ny, int nz, const uint8_t *solid,
+                     unsigned periodic_mask) {
+  if (lattice != 9 && lattice != 19) return nullptr;
+  if (lattice == 9 && nz != 1) return nullptr;
+  OracleT<Dual> *o = new OracleT<Dual>();
+  o->init(lattice, nx, ny, nz, solid, periodic_mask);
+  return o;
+}
+
+void orc_tlm_destroy(void *h) { delete static_cast<OracleT<Dual> *>(h); }
+
+void orc_tlm_set_params(void *h, const orc_params *p) {
+  const Dual th(p->theta_deg * PI / 180.0, 1.0, 0.0);
+  const Dual gg[3] = {Dual(p->g[0], 0.0, 1.0), Dual(p->g[1]), Dual(p->g[2])};
+  static_cast<OracleT<Dual> *>(h)->set_params(*p, th, gg);
+}
+
+void orc_tlm_init_state(void *h, const double *phi0) {
+  static_cast<OracleT<Dual> *>(h)->init_state(phi0);
+}
+
+void orc_tlm_step(void *h, int nsteps) {
+  OracleT<Dual> *o = static_cast<OracleT<Dual> *>(h);
+  for (int s = 0; s < nsteps; ++s) o->step();
+}
+
+// Smooth S_w of the most recent step (orc_reduce kind 3) and its
+// derivatives: out = {S_w, dS_w/dtheta (per radian), dS_w/dg_x}.
+void orc_tlm_sw(void *h, double *out) {
+  OracleT<Dual> *o = static_cast<OracleT<Dual> *>(h);
+  Dual s = 0.0;
+  for (long n = 0; n < o->N; ++n) {
+    if (o->solid[n]) continue;
+    s += 0.5 * (1.0 - o->phi[n]);
+  }
+  s = s / (double)o->n_fluid;
+  out[0] = s.v;
+  out[1] = s.d[0];
+  out[2] = s.d[1];
 }
 
 int orc_max_threads(void) {

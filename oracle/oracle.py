@@ -73,6 +73,14 @@ def lib():
         L.orc_collide.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_double,
                                   C.c_double, C.c_void_p, C.c_void_p]
         L.orc_max_threads.restype = C.c_int
+        L.orc_tlm_create.restype = C.c_void_p
+        L.orc_tlm_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int,
+                                     C.c_void_p, C.c_uint]
+        L.orc_tlm_destroy.argtypes = [C.c_void_p]
+        L.orc_tlm_set_params.argtypes = [C.c_void_p, C.POINTER(_Params)]
+        L.orc_tlm_init_state.argtypes = [C.c_void_p, C.c_void_p]
+        L.orc_tlm_step.argtypes = [C.c_void_p, C.c_int]
+        L.orc_tlm_sw.argtypes = [C.c_void_p, C.c_void_p]
         _lib = L
     return _lib
 
@@ -203,6 +211,57 @@ class Oracle:
 
     def reduce(self, kind: int) -> float:
         return lib().orc_reduce(self._h, int(kind))
+
+
+class TangentLinear:
+    """The oracle's step on forward-mode dual numbers (FP64): the smooth
+    saturation after n steps and its derivatives with respect to the
+    contact angle (per radian) and the body acceleration g_x."""
+
+    def __init__(self, lattice_q: int, solid: np.ndarray,
+                 periodic=(True, True, True)):
+        solid = np.ascontiguousarray(solid, dtype=np.uint8)
+        if solid.ndim == 2:
+            solid = solid[None]
+        self.shape = solid.shape
+        nz, ny, nx = self.shape
+        mask = sum((1 << a) for a in range(3) if periodic[a])
+        self._h = lib().orc_tlm_create(lattice_q, nx, ny, nz, _ptr(solid),
+                                       mask)
+        if not self._h:
+            raise ValueError("oracle: bad lattice/shape")
+        self.params = dict(PARAM_DEFAULTS)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h and _lib is not None:
+            _lib.orc_tlm_destroy(h)
+            self._h = None
+
+    def set_params(self, **kw):
+        for k in kw:
+            if k not in PARAM_DEFAULTS:
+                raise KeyError(k)
+        self.params.update(kw)
+        p = self.params
+        st = _Params(p["tau_r"], p["tau_b"], p["gamma"], p["beta"], p["rho0"],
+                     p["theta_deg"], int(p["wetting"]), int(p["zou_he"]),
+                     int(p["flow_axis"]), p["rho_in"], p["rho_out"],
+                     p["zeta_r"], (C.c_double * 3)(*p["g"]))
+        lib().orc_tlm_set_params(self._h, C.byref(st))
+
+    def init_state(self, phi0: np.ndarray):
+        a = np.ascontiguousarray(np.broadcast_to(phi0, self.shape), np.float64)
+        lib().orc_tlm_init_state(self._h, _ptr(a))
+
+    def step(self, n: int = 1):
+        lib().orc_tlm_step(self._h, int(n))
+
+    def sw(self):
+        """(S_w smooth, dS_w/dtheta per radian, dS_w/dg_x)."""
+        out = np.zeros(3)
+        lib().orc_tlm_sw(self._h, _ptr(out))
+        return float(out[0]), float(out[1]), float(out[2])
 
 
 def max_threads() -> int:

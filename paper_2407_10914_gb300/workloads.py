@@ -303,3 +303,28 @@ def batched_droplets(count=96, smin=48, smax=128, seed=7, steps=5000,
         c.name = f"drop{j}_s{side}_th{theta:.0f}_w{wetting}"
         cases.append(c)
     return cases
+
+
+# ------------------------------------------------------------ adjoint pack
+def adjoint_pack(n=(128, 128, 128), porosity=0.25, seed=2025, theta_deg=40.0,
+                 g_x=5e-6, slab: Optional[int] = None, steps=2000,
+                 tau_r=1.0, tau_b=1.0, gamma=0.01, beta=0.95) -> Case:
+    """The gradient workload: a D3Q19 sphere pack (Boolean model as in
+    sphere_pack, no reservoirs or side walls) periodic on every axis, filled
+    with red (non-wetting) fluid except a blue (wetting, theta < 90 deg
+    through fluid b) slab x < slab; Scheme-II; the body acceleration g_x
+    drives the flow (Type-II, Eq. 36). Periodic ends stand in for the
+    paper's reservoirs so that no Zou-He plane enters the adjoint."""
+    nx, ny, nz = n
+    pack = sphere_pack((nx, ny, nz), porosity, seed=seed, reservoir=0,
+                       side_walls=False)
+    solid = pack["solid"]
+    s = slab if slab is not None else max(2, nx // 8)
+    phi0 = np.ones((nz, ny, nx))
+    phi0[:, :, :s] = -1.0
+    phi0[solid == 1] = 0.0
+    p = base_params(tau_r=tau_r, tau_b=tau_b, gamma=gamma, beta=beta,
+                    theta_deg=theta_deg, wetting=2, g=(g_x, 0.0, 0.0))
+    return Case(f"adjoint_pack{nx}x{ny}x{nz}", 19, solid, (True, True, True),
+                phi0, p, steps,
+                dict(rock_porosity=pack["rock_porosity"], slab=s))
