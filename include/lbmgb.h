@@ -197,6 +197,16 @@ lbm_status lbm_colour_mass_noalloc(int lattice, int64_t n_nodes,
                                    const float *pops_dev, double *mass_host,
                                    void *stream);
 
+/* Bytes of one exact copy of the stored state (the f''_i planes in the
+ * storage type and the per-node colour split (q, v)): for checkpoints. */
+size_t lbm_state_bytes(lbm_handle h);
+
+/* Copy the current state to / from caller device memory of
+ * lbm_state_bytes() bytes (device to device, asynchronous on `stream`).
+ * A loaded state continues exactly as the saved one would have. */
+lbm_status lbm_save_state(lbm_handle h, void *dst_dev, void *stream);
+lbm_status lbm_load_state(lbm_handle h, const void *src_dev, void *stream);
+
 /* Message of the last failed call on this handle ("" if none). */
 const char *lbm_last_error(lbm_handle h);
 
@@ -272,6 +282,64 @@ const char *lbm_batch_last_error(lbm_batch b);
 
 /* Release the batch (host side; the workspace stays the caller's). */
 void lbm_batch_destroy(lbm_batch b);
+
+/* ------------------------------------------------------------------------
+ * Adjoint: the hand-written reverse of one time step, for the gradient of
+ * J = LBM_SW_SMOOTH after T steps (the mean over fluid nodes of (1 - phi)/2,
+ * phi from the last step's streamed populations) with respect to the
+ * contact angle theta (radians) and the body acceleration g (Eq. 36).
+ * The state of a fluid node is (f''_i, r = rho^r/rho, v) with the red part
+ * of population i equal to r f''_i + w_i e_i.v (Eqs. 20-21); the adjoint
+ * state has the same shape. Scope: float32 storage, no wetting or Scheme-II
+ * (Eqs. 32-33), no Zou-He ends (periodic axes or bounce-back walls);
+ * lbm_adj_create() rejects anything else with LBM_ERR_ARG. All arithmetic
+ * is float32; the parameter gradients accumulate in float64.
+ *
+ * Use (T steps, states x_0 .. x_T, with x_{t+1} = step(x_t)):
+ *   load x_{T-1} into the handle (lbm_load_state), lbm_adj_seed_sw();
+ *   for t = T-2 down to 0: load x_t, lbm_adj_step();
+ *   lbm_adj_gradients().
+ * The states can come from checkpoints and recomputation (the binding's
+ * SwGradient keeps every K-th state and recomputes the rest, K ~ sqrt(T)).
+ * Each call recomputes the forward fields of its step on the handle, which
+ * changes the handle's per-step fields (macros) but not its state.
+ * ------------------------------------------------------------------------ */
+typedef struct lbm_adj_s *lbm_adj;
+
+/* Device workspace (bytes) of the adjoint of handle h: about
+ * (3Q + 15) x 4 bytes per fluid node. */
+size_t lbm_adj_workspace_bytes(lbm_handle h);
+
+/* Adjoint of handle h (which must have its parameters set), in caller
+ * device memory of ws_bytes >= lbm_adj_workspace_bytes(h), 256-byte
+ * aligned. The handle must outlive it. */
+lbm_status lbm_adj_create(lbm_adj *out, lbm_handle h, void *dev_workspace,
+                          size_t ws_bytes);
+
+/* Start the reverse sweep: the handle holds x_{T-1}. Sets the adjoint state
+ * to dJ/dx_{T-1} and zeroes the parameter gradients. Asynchronous. */
+lbm_status lbm_adj_seed_sw(lbm_adj a, void *stream);
+
+/* Reverse one step: the handle holds x_t, the adjoint dJ/dx_{t+1}; on
+ * return (asynchronously) the adjoint is dJ/dx_t and the step's parts of
+ * dJ/dtheta and dJ/dg are added. */
+lbm_status lbm_adj_step(lbm_adj a, void *stream);
+
+/* dJ/dtheta (per radian) and dJ/dg_x, dJ/dg_y, dJ/dg_z into out4 (host);
+ * synchronises `stream`. */
+lbm_status lbm_adj_gradients(lbm_adj a, double *out4, void *stream);
+
+/* The current adjoint state: lt_dev float32 [Q][NFp] (fluid nodes in the
+ * library's internal order) and ls_dev float32 [NF][4] (lambda r,
+ * lambda v). For tests. */
+lbm_status lbm_adj_get_lambda(lbm_adj a, float *lt_dev, float *ls_dev,
+                              void *stream);
+
+/* Message of the last failed call on this adjoint ("" if none). */
+const char *lbm_adj_last_error(lbm_adj a);
+
+/* Release the adjoint (host side). */
+void lbm_adj_destroy(lbm_adj a);
 
 #ifdef __cplusplus
 }

@@ -983,8 +983,9 @@ void orc_collide(int lattice, const double *ft, const double *F, double S,
 
 // ---- tangent-linear run ----------------------------------------------------
 // The same step on Dual numbers: every field carries its derivatives with
-// respect to the contact angle theta (radians; direction 0) and the body
-// acceleration g_x (direction 1), seeded in orc_tlm_set_params.
+// respect to the contact angle theta (radians; direction 0) and one
+// component of the body acceleration (direction 1), seeded in
+// orc_tlm_set_params.
 
 void *orc_tlm_create(int lattice, int nx, int ny, int nz, const uint8_t *solid,
                      unsigned periodic_mask) {
@@ -997,9 +998,11 @@ void *orc_tlm_create(int lattice, int nx, int ny, int nz, const uint8_t *solid,
 
 void orc_tlm_destroy(void *h) { delete static_cast<OracleT<Dual> *>(h); }
 
-void orc_tlm_set_params(void *h, const orc_params *p) {
+// Direction 1 is the component g_axis of the body acceleration.
+void orc_tlm_set_params(void *h, const orc_params *p, int g_axis) {
   const Dual th(p->theta_deg * PI / 180.0, 1.0, 0.0);
-  const Dual gg[3] = {Dual(p->g[0], 0.0, 1.0), Dual(p->g[1]), Dual(p->g[2])};
+  Dual gg[3] = {Dual(p->g[0]), Dual(p->g[1]), Dual(p->g[2])};
+  gg[g_axis] = Dual(p->g[g_axis], 0.0, 1.0);
   static_cast<OracleT<Dual> *>(h)->set_params(*p, th, gg);
 }
 
@@ -1013,7 +1016,7 @@ void orc_tlm_step(void *h, int nsteps) {
 }
 
 // Smooth S_w of the most recent step (orc_reduce kind 3) and its
-// derivatives: out = {S_w, dS_w/dtheta (per radian), dS_w/dg_x}.
+// derivatives: out = {S_w, dS_w/dtheta (per radian), dS_w/dg_axis}.
 void orc_tlm_sw(void *h, double *out) {
   OracleT<Dual> *o = static_cast<OracleT<Dual> *>(h);
   Dual s = 0.0;

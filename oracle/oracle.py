@@ -77,7 +77,8 @@ def lib():
         L.orc_tlm_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int,
                                      C.c_void_p, C.c_uint]
         L.orc_tlm_destroy.argtypes = [C.c_void_p]
-        L.orc_tlm_set_params.argtypes = [C.c_void_p, C.POINTER(_Params)]
+        L.orc_tlm_set_params.argtypes = [C.c_void_p, C.POINTER(_Params),
+                                         C.c_int]
         L.orc_tlm_init_state.argtypes = [C.c_void_p, C.c_void_p]
         L.orc_tlm_step.argtypes = [C.c_void_p, C.c_int]
         L.orc_tlm_sw.argtypes = [C.c_void_p, C.c_void_p]
@@ -216,10 +217,12 @@ class Oracle:
 class TangentLinear:
     """The oracle's step on forward-mode dual numbers (FP64): the smooth
     saturation after n steps and its derivatives with respect to the
-    contact angle (per radian) and the body acceleration g_x."""
+    contact angle (per radian) and the component g_axis of the body
+    acceleration."""
 
     def __init__(self, lattice_q: int, solid: np.ndarray,
-                 periodic=(True, True, True)):
+                 periodic=(True, True, True), g_axis: int = 0):
+        self.g_axis = int(g_axis)
         solid = np.ascontiguousarray(solid, dtype=np.uint8)
         if solid.ndim == 2:
             solid = solid[None]
@@ -248,7 +251,7 @@ class TangentLinear:
                      p["theta_deg"], int(p["wetting"]), int(p["zou_he"]),
                      int(p["flow_axis"]), p["rho_in"], p["rho_out"],
                      p["zeta_r"], (C.c_double * 3)(*p["g"]))
-        lib().orc_tlm_set_params(self._h, C.byref(st))
+        lib().orc_tlm_set_params(self._h, C.byref(st), self.g_axis)
 
     def init_state(self, phi0: np.ndarray):
         a = np.ascontiguousarray(np.broadcast_to(phi0, self.shape), np.float64)
@@ -258,7 +261,7 @@ class TangentLinear:
         lib().orc_tlm_step(self._h, int(n))
 
     def sw(self):
-        """(S_w smooth, dS_w/dtheta per radian, dS_w/dg_x)."""
+        """(S_w smooth, dS_w/dtheta per radian, dS_w/dg[g_axis])."""
         out = np.zeros(3)
         lib().orc_tlm_sw(self._h, _ptr(out))
         return float(out[0]), float(out[1]), float(out[2])

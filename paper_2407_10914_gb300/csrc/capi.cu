@@ -435,6 +435,43 @@ lbm_status lbm_counts(lbm_handle c, int64_t *n_nodes, int64_t *n_fluid,
   return LBM_OK;
 }
 
+size_t lbm_state_bytes(lbm_handle c) {
+  if (!c) return 0;
+  const size_t bp = c->storage == LBM_STORAGE_FP32 ? 4 : 2;
+  return (size_t)c->Q * (size_t)c->d.NFp * bp + (size_t)c->d.NFp * 16;
+}
+
+lbm_status lbm_save_state(lbm_handle c, void *dst_dev, void *stream) {
+  if (!c || !dst_dev) return LBM_ERR_ARG;
+  if (!c->state_set) return fail(c, LBM_ERR_STATE, "no state to save");
+  const size_t tb = lbm_state_bytes(c) - (size_t)c->d.NFp * 16;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(dst_dev, c->d.T_src, tb,
+                                  cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((char *)dst_dev + tb, c->d.S_src,
+                        (size_t)c->d.NFp * 16, cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "save_state");
+  return LBM_OK;
+}
+
+lbm_status lbm_load_state(lbm_handle c, const void *src_dev, void *stream) {
+  if (!c || !src_dev) return LBM_ERR_ARG;
+  if (!c->params_set) return fail(c, LBM_ERR_STATE, "set params first");
+  const size_t tb = lbm_state_bytes(c) - (size_t)c->d.NFp * 16;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(const_cast<void *>(c->d.T_src), src_dev, tb,
+                                  cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(const_cast<float4 *>(c->d.S_src),
+                        (const char *)src_dev + tb, (size_t)c->d.NFp * 16,
+                        cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "load_state");
+  c->state_set = true;
+  ++c->gen;
+  return LBM_OK;
+}
+
 const char *lbm_last_error(lbm_handle c) { return c ? c->err : "null handle"; }
 
 void lbm_destroy(lbm_handle c) { delete c; }

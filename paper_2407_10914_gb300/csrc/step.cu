@@ -80,6 +80,30 @@ static void launch_step_t(const Dom &d, cudaStream_t s, bool macros,
   if (ev) cudaEventRecord(ev[6], s);
 }
 
+template <int Q, int ST>
+static void launch_fields_t(const Dom &d, cudaStream_t s) {
+  const unsigned g = (unsigned)((d.NF + BLOCK - 1) / BLOCK);
+  const unsigned gs = (unsigned)((d.NS + BLOCK - 1) / BLOCK);
+  const unsigned gz = (unsigned)((d.n_zh + BLOCK - 1) / BLOCK);
+  k_stream<Q, ST><<<g, BLOCK, 0, s>>>(d);
+  if (d.n_zh > 0) k_zh_fix<Q, ST><<<gz, BLOCK, 0, s>>>(d);
+  if (d.NS > 0) k_phi_solid<Q><<<gs, BLOCK, 0, s>>>(d);
+  k_gradient<Q><<<g, BLOCK, 0, s>>>(d);
+  if (d.NS > 0) k_nc_solid<Q><<<gs, BLOCK, 0, s>>>(d);
+}
+
+void launch_fields(int Q, int storage, const Dom &d, cudaStream_t s) {
+  if (Q == 19) {
+    if (storage == LBM_STORAGE_FP32) launch_fields_t<19, LBM_STORAGE_FP32>(d, s);
+    if (storage == LBM_STORAGE_FP16) launch_fields_t<19, LBM_STORAGE_FP16>(d, s);
+    if (storage == LBM_STORAGE_BF16) launch_fields_t<19, LBM_STORAGE_BF16>(d, s);
+  } else {
+    if (storage == LBM_STORAGE_FP32) launch_fields_t<9, LBM_STORAGE_FP32>(d, s);
+    if (storage == LBM_STORAGE_FP16) launch_fields_t<9, LBM_STORAGE_FP16>(d, s);
+    if (storage == LBM_STORAGE_BF16) launch_fields_t<9, LBM_STORAGE_BF16>(d, s);
+  }
+}
+
 static void dispatch(int Q, int storage, const Dom &d, cudaStream_t s,
                      bool macros, cudaEvent_t *ev) {
   if (Q == 19) {

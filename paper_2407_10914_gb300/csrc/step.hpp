@@ -18,6 +18,11 @@ void launch_step(int Q, int storage, const Dom &d, cudaStream_t s,
 void launch_step_events(int Q, int storage, const Dom &d, cudaStream_t s,
                         bool macros, cudaEvent_t *ev);
 
+// The passes of a step before the collision (stream, Zou-He fix-up, Eq. 34,
+// gradient and wetting, Eq. 35) on the current state: fills U, R, the
+// phase fields and the normals without changing the state.
+void launch_fields(int Q, int storage, const Dom &d, cudaStream_t s);
+
 // Geometry set-up (geometry.cu): classes, the compact lists and the map,
 // Eq. (25) smoothing, Eq. (26) normals and the counts.
 cudaError_t build_geometry(lbm_ctx *c, cudaStream_t s);

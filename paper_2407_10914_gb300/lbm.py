@@ -36,7 +36,11 @@ EXPORTS = ("lbm_workspace_bytes", "lbm_init_geometry", "lbm_set_params",
            "lbm_batch_workspace_bytes", "lbm_batch_create",
            "lbm_batch_set_config", "lbm_batch_step", "lbm_batch_status",
            "lbm_batch_check_wait", "lbm_batch_last_error",
-           "lbm_batch_destroy")
+           "lbm_batch_destroy",
+           "lbm_state_bytes", "lbm_save_state", "lbm_load_state",
+           "lbm_adj_workspace_bytes", "lbm_adj_create", "lbm_adj_seed_sw",
+           "lbm_adj_step", "lbm_adj_gradients", "lbm_adj_get_lambda",
+           "lbm_adj_last_error", "lbm_adj_destroy")
 
 
 class LbmError(RuntimeError):
@@ -118,6 +122,26 @@ def load_library(path: str = LIB_PATH):
     L.lbm_batch_last_error.argtypes = [vp]
     L.lbm_batch_destroy.restype = None
     L.lbm_batch_destroy.argtypes = [vp]
+    L.lbm_state_bytes.restype = sz
+    L.lbm_state_bytes.argtypes = [vp]
+    for f in (L.lbm_save_state, L.lbm_load_state):
+        f.restype = C.c_int
+        f.argtypes = [vp, vp, vp]
+    L.lbm_adj_workspace_bytes.restype = sz
+    L.lbm_adj_workspace_bytes.argtypes = [vp]
+    L.lbm_adj_create.restype = C.c_int
+    L.lbm_adj_create.argtypes = [C.POINTER(vp), vp, vp, sz]
+    for f in (L.lbm_adj_seed_sw, L.lbm_adj_step):
+        f.restype = C.c_int
+        f.argtypes = [vp, vp]
+    L.lbm_adj_gradients.restype = C.c_int
+    L.lbm_adj_gradients.argtypes = [vp, C.POINTER(C.c_double), vp]
+    L.lbm_adj_get_lambda.restype = C.c_int
+    L.lbm_adj_get_lambda.argtypes = [vp, vp, vp, vp]
+    L.lbm_adj_last_error.restype = C.c_char_p
+    L.lbm_adj_last_error.argtypes = [vp]
+    L.lbm_adj_destroy.restype = None
+    L.lbm_adj_destroy.argtypes = [vp]
     _lib = L
     return L
 
@@ -459,3 +483,65 @@ class Batch:
 
     def check_wait(self, limit_ms: float) -> float:
         return lbm_batch_check_wait(self.b, limit_ms, self.stream())
+
+
+# ------------------------------------------------------ checkpoints, adjoint
+def lbm_state_bytes(h) -> int:
+    return int(load_library().lbm_state_bytes(h))
+
+
+def lbm_save_state(h, dst, stream):
+    _check(load_library().lbm_save_state(h, C.c_void_p(dst.data_ptr()), stream),
+           h, "lbm_save_state")
+
+
+def lbm_load_state(h, src, stream):
+    _check(load_library().lbm_load_state(h, C.c_void_p(src.data_ptr()), stream),
+           h, "lbm_load_state")
+
+
+def _acheck(st: int, a=None, what: str = ""):
+    if st != LBM_OK:
+        msg = load_library().lbm_adj_last_error(a).decode() if a else ""
+        raise LbmError(f"{what}: {STATUS.get(st, st)} {msg}")
+
+
+def lbm_adj_workspace_bytes(h) -> int:
+    return int(load_library().lbm_adj_workspace_bytes(h))
+
+
+def lbm_adj_create(h, workspace):
+    out = C.c_void_p()
+    _acheck(load_library().lbm_adj_create(
+        C.byref(out), h, C.c_void_p(workspace.data_ptr()),
+        workspace.numel() * workspace.element_size()), None, "lbm_adj_create")
+    return out
+
+
+def lbm_adj_seed_sw(a, stream):
+    _acheck(load_library().lbm_adj_seed_sw(a, stream), a, "lbm_adj_seed_sw")
+
+
+def lbm_adj_step(a, stream):
+    _acheck(load_library().lbm_adj_step(a, stream), a, "lbm_adj_step")
+
+
+def lbm_adj_gradients(a, stream):
+    out = (C.c_double * 4)()
+    _acheck(load_library().lbm_adj_gradients(a, out, stream), a,
+            "lbm_adj_gradients")
+    return list(out)
+
+
+def lbm_adj_get_lambda(a, lt, ls, stream):
+    _acheck(load_library().lbm_adj_get_lambda(
+        a, C.c_void_p(lt.data_ptr()), C.c_void_p(ls.data_ptr()), stream), a,
+        "lbm_adj_get_lambda")
+
+
+def lbm_adj_last_error(a) -> str:
+    return load_library().lbm_adj_last_error(a).decode()
+
+
+def lbm_adj_destroy(a):
+    load_library().lbm_adj_destroy(a)
