@@ -335,6 +335,22 @@ lbm_status lbm_adj_gradients(lbm_adj a, double *out4, void *stream);
 lbm_status lbm_adj_get_lambda(lbm_adj a, float *lt_dev, float *ls_dev,
                               void *stream);
 
+/* Regularised linearisation of Scheme-II: where sin(theta') (theta' the
+ * angle between n_c and n_w) is below freeze_sin, the derivative of the
+ * result's direction around n_w, which grows as 1/sin(theta'), is dropped
+ * and only its theta dependence kept. Over long runs the exact derivative
+ * of the discrete step grows without bound through such nodes; the default
+ * 0.05 keeps the gradient finite and close to finite differences of the
+ * forward run. 0 gives the exact derivative. Range [0, 1]. */
+lbm_status lbm_adj_set_freeze(lbm_adj a, double freeze_sin);
+
+/* Regularised linearisation of the interface normal n_c = C/|C| (Eq. 11):
+ * where |C| < c_min the direction of n_c is held constant (its derivative
+ * grows as 1/|C| in the tails of the interface). The default 1e-3 keeps
+ * long-run gradients finite (with freeze_sin 0.05); 0 gives the exact
+ * derivative. Range [0, 10]. */
+lbm_status lbm_adj_set_cmin(lbm_adj a, double c_min);
+
 /* Message of the last failed call on this adjoint ("" if none). */
 const char *lbm_adj_last_error(lbm_adj a);
 

@@ -130,6 +130,8 @@ inline double acos(double a) { return std::acos(a); }
 inline double sin(double a) { return std::sin(a); }
 inline double cos(double a) { return std::cos(a); }
 inline double fabs(double a) { return std::fabs(a); }
+inline double value_of(double x) { return x; }
+inline Dual value_of(const Dual &x) { return Dual(x.v); }  // derivatives dropped
 template <class R>
 R clamp1(const R &x) {  // x limited to [-1, 1]
   return x < R(-1.0) ? R(-1.0) : (x > R(1.0) ? R(1.0) : x);
@@ -205,6 +207,8 @@ struct OracleT {
   std::vector<R> kappa, F;  // curvature and force (3N)
   std::vector<R> u;         // velocity of Eq. (22), 3N
   R theta;                  // contact angle (radians) of p.theta_deg
+  double freeze_sin = 0.0;   // regularised Scheme-II linearisation (TLM)
+  double c_min = 0.0;        // regularised normalisation linearisation
   R g[3];                   // body acceleration p.g
   long n_fluid = 0;
 
@@ -503,6 +507,9 @@ struct OracleT {
       for (int a = 0; a < 3; ++a) {
         C[a * N + n] = (m > EPS_C) ? G[a] : R(0.0);
         nc[a * N + n] = (m > EPS_C) ? G[a] / m : R(0.0);
+        // regularised linearisation (tangent-linear runs only): below c_min
+        // the direction of n_c is held constant
+        if (m > EPS_C && m < c_min) nc[a * N + n] = value_of(G[a] / m);
       }
     }
   }
@@ -556,7 +563,7 @@ struct OracleT {
   // tie). Left unchanged when sin(theta') < EPS_SIN.
   template <class T>
   static void scheme2(const T n_c[3], const double n_w[3], const T &theta,
-                      T out[3]) {
+                      T out[3], double freeze_sin = 0.0) {
     T c = n_c[0] * n_w[0] + n_c[1] * n_w[1] + n_c[2] * n_w[2];
     c = clamp1(c);
     T thp = acos(c);
@@ -576,6 +583,18 @@ struct OracleT {
       dm += (nm[a] - n_c[a]) * (nm[a] - n_c[a]);
     }
     for (int a = 0; a < 3; ++a) out[a] = (dp <= dm) ? np[a] : nm[a];
+    // Regularised linearisation (tangent-linear runs only): with n_c almost
+    // along n_w the direction t = (n_c - cos(theta') n_w) / sin(theta') of
+    // the result around n_w is undefined at sin(theta') = 0 and its
+    // derivative grows as 1/sin(theta'). Below freeze_sin that direction is
+    // held constant: out = cos(theta) n_w +- sin(theta) t with t's value.
+    if (freeze_sin > 0.0 && sp < freeze_sin) {
+      const T st = (dp <= dm) ? sin(theta) : sin(-theta);
+      for (int a = 0; a < 3; ++a) {
+        const T t = (n_c[a] - cp * n_w[a]) / sp;
+        out[a] = cos(theta) * n_w[a] + st * value_of(t);
+      }
+    }
   }
 
  private:
@@ -600,7 +619,7 @@ struct OracleT {
       if (p.wetting == 1)
         scheme1(ncv, nwv, theta, out);
       else
-        scheme2(ncv, nwv, theta, out);
+        scheme2(ncv, nwv, theta, out, freeze_sin);
       R mag = 0.0;
       for (int a = 0; a < 3; ++a) mag += C[a * N + n] * C[a * N + n];
       mag = sqrt(mag);
@@ -997,6 +1016,19 @@ void *orc_tlm_create(int lattice, int nx, int ny, int nz, const uint8_t *solid,
 }
 
 void orc_tlm_destroy(void *h) { delete static_cast<OracleT<Dual> *>(h); }
+
+// Regularised linearisation of Scheme-II in the tangent-linear run: where
+// sin(theta') < freeze_sin the direction of the result around n_w is held
+// constant (0: exact derivatives).
+void orc_tlm_set_freeze(void *h, double freeze_sin) {
+  static_cast<OracleT<Dual> *>(h)->freeze_sin = freeze_sin;
+}
+
+// Regularised linearisation of n_c = C/|C|: where |C| < c_min its direction
+// is held constant (0: exact derivatives).
+void orc_tlm_set_cmin(void *h, double c_min) {
+  static_cast<OracleT<Dual> *>(h)->c_min = c_min;
+}
 
 // Direction 1 is the component g_axis of the body acceleration.
 void orc_tlm_set_params(void *h, const orc_params *p, int g_axis) {

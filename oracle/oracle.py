@@ -82,6 +82,8 @@ def lib():
         L.orc_tlm_init_state.argtypes = [C.c_void_p, C.c_void_p]
         L.orc_tlm_step.argtypes = [C.c_void_p, C.c_int]
         L.orc_tlm_sw.argtypes = [C.c_void_p, C.c_void_p]
+        L.orc_tlm_set_freeze.argtypes = [C.c_void_p, C.c_double]
+        L.orc_tlm_set_cmin.argtypes = [C.c_void_p, C.c_double]
         _lib = L
     return _lib
 
@@ -256,6 +258,16 @@ class TangentLinear:
     def init_state(self, phi0: np.ndarray):
         a = np.ascontiguousarray(np.broadcast_to(phi0, self.shape), np.float64)
         lib().orc_tlm_init_state(self._h, _ptr(a))
+
+    def set_freeze(self, freeze_sin: float):
+        """Hold Scheme-II's direction around n_w constant in the
+        linearisation where sin(theta') < freeze_sin (0: exact)."""
+        lib().orc_tlm_set_freeze(self._h, float(freeze_sin))
+
+    def set_cmin(self, c_min: float):
+        """Hold the direction of n_c constant in the linearisation where
+        |C| < c_min (0: exact)."""
+        lib().orc_tlm_set_cmin(self._h, float(c_min))
 
     def step(self, n: int = 1):
         lib().orc_tlm_step(self._h, int(n))

@@ -11,6 +11,13 @@ checkpoint and reverses the steps one by one, so memory holds about 2
 sqrt(T) states and the work is about 3T steps. Every step runs in the CUDA
 library; this module only schedules the calls.
 
+freeze_sin (default 0.05) and c_min (default 1e-3) regularise the
+linearisation (lbm_adj_set_freeze, lbm_adj_set_cmin): over long runs the
+exact derivative of the discrete step grows without bound through wetting
+nodes where n_c is almost along n_w (Jacobian ~ 1/sin(theta')) and through
+the interface tails (Jacobian of n_c = C/|C| ~ 1/|C|). Zeros give the exact
+derivative, right for short runs.
+
 ``SwGradient`` wraps it as a torch.autograd.Function of (theta in degrees,
 g as a 3-vector): J.backward() fills their .grad.
 """
@@ -27,7 +34,8 @@ from . import lbm
 class Run:
     """One checkpointed forward run of a Session and its reverse sweep."""
 
-    def __init__(self, session, phi0, steps: int, every: Optional[int] = None):
+    def __init__(self, session, phi0, steps: int, every: Optional[int] = None,
+                 freeze_sin: float = 0.05, c_min: float = 1e-3):
         if steps < 1:
             raise ValueError("steps must be >= 1")
         self.s = session
@@ -38,6 +46,8 @@ class Run:
         self.nb = lbm.lbm_state_bytes(session.h)
         self._new = lambda: torch.empty(self.nb, dtype=torch.uint8,
                                         device=session.device)
+        self.freeze_sin = float(freeze_sin)
+        self.c_min = float(c_min)
         self.checkpoints = {}
         self.last = None  # x_{T-1}
         self.J = None
@@ -65,6 +75,8 @@ class Run:
                          device=s.device)
         a = lbm.lbm_adj_create(s.h, ws)
         try:
+            lbm.lbm_adj_set_freeze(a, self.freeze_sin)
+            lbm.lbm_adj_set_cmin(a, self.c_min)
             lbm.lbm_load_state(s.h, self.last, st)
             lbm.lbm_adj_seed_sw(a, st)
             n_states = self.T - 1  # x_0 .. x_{T-2} are reversed

@@ -26,6 +26,18 @@
 // The adjoint covers float32 storage, no wetting or Scheme-II, and ends
 // without Zou-He planes (periodic axes or bounce-back walls); Scheme-I's
 // secant iterations and App. B are not differentiated here.
+//
+// Regularised linearisation. Where n_c is almost along n_w, Scheme-II's
+// result direction around n_w is undefined and its derivative grows as
+// 1/sin(theta'); over a few hundred steps such nodes make the exact
+// derivative of the discrete step grow without bound (the FP64 tangent-
+// linear run of the oracle shows it), while the response to a finite
+// change of theta or g stays smooth. The interface normal n_c = C/|C| has
+// the same kind of Jacobian (1/|C|) in the interface tails. By default the
+// adjoint drops the derivative of Scheme-II's direction around n_w where
+// sin(theta') < 0.05 and of n_c's direction where |C| < 1e-3, and keeps
+// everything else exact; lbm_adj_set_freeze(a, 0) and lbm_adj_set_cmin(a,
+// 0) restore the exact derivative.
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -50,6 +62,8 @@ struct Adj {
   float4 *lns;              // [NS] lambda of the Eq. 35 n
   float2 *ab;               // [NF] coefficients of the stream transpose
   double *acc;              // [4] dJ/dtheta, dJ/dg
+  float freeze_sin;         // Scheme-II linearisation: see scheme2_adj
+  float c_min;              // normalisation linearisation: see k_adj_gradient
 };
 
 __device__ __forceinline__ void atomic_add3(float4 *p, float x, float y,
@@ -265,9 +279,14 @@ __global__ void __launch_bounds__(ABLOCK) k_adj_nc_solid(Dom d, Adj a) {
 // Scheme-II (Eqs. 32-33) reversed: given lambda of its output n, adds
 // lambda of its input n_c to lnc and of theta (radians) to *lth. The
 // forward choice between n+ and n- is kept (a discrete, locally constant
-// decision); below EPS_SIN the scheme is the identity.
+// decision); below EPS_SIN the scheme is the identity. The output is
+// cos(theta) n_w +- sin(theta) t^ with t^ the direction of n_c's part
+// across n_w; where sin(theta') = |n_c - cos(theta') n_w| < freeze_sin the
+// derivative of t^ (which grows as 1/sin(theta')) is dropped and only the
+// theta dependence is kept: the regularised linearisation (see Adj).
 __device__ __forceinline__ void scheme2_adj(const float *nc, const float *nw,
                                             float cth, float sth,
+                                            float freeze_sin,
                                             const float *lout, float *lnc,
                                             float *lth) {
   const float c0 = dot3(nw, nc);
@@ -289,6 +308,7 @@ __device__ __forceinline__ void scheme2_adj(const float *nc, const float *nw,
   const float th[3] = {t[0] / sp, t[1] / sp, t[2] / sp};
   // out = cos(theta) n_w + s sin(theta) t^, t^ = t / |t|, t = n_c - c n_w
   *lth += dot3(lout, nw) * (-sth) + s * cth * dot3(lout, th);
+  if (sp < freeze_sin) return;
   float lt[3];
   const float lth_dot = s * sth * dot3(lout, th);
   for (int q = 0; q < 3; ++q) lt[q] = (s * sth * lout[q] - th[q] * lth_dot) / sp;
@@ -327,15 +347,19 @@ __global__ void __launch_bounds__(ABLOCK) k_adj_gradient(Dom d, Adj a) {
         const float4 w4 = d.nw[k];
         const float nw[3] = {w4.x, w4.y, w4.z};
         if (nw[0] != 0.f || nw[1] != 0.f || nw[2] != 0.f) {
-          scheme2_adj(nc, nw, d.c.cos_t, d.c.sin_t, lout, lnc, &lth);
+          scheme2_adj(nc, nw, d.c.cos_t, d.c.sin_t, a.freeze_sin, lout, lnc,
+                      &lth);
           wet = true;
         }
       }
       if (!wet)
         for (int q = 0; q < 3; ++q) lnc[q] = lout[q];
+      // n_c = C / |C|: its derivative grows as 1 / |C|; below c_min the
+      // direction is held constant (regularised linearisation)
       const float nl = dot3(nc, lnc);
+      const float kn = Cm < a.c_min ? 0.f : 1.f / Cm;
       float lC[3];
-      for (int q = 0; q < 3; ++q) lC[q] = (lnc[q] - nc[q] * nl) / Cm + nc[q] * l4.w;
+      for (int q = 0; q < 3; ++q) lC[q] = (lnc[q] - nc[q] * nl) * kn + nc[q] * l4.w;
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
         const float v = 3.f * Lattice<Q>::w(i) *
@@ -543,6 +567,8 @@ lbm_status lbm_adj_create(lbm_adj *out, lbm_handle h, void *dev_workspace,
   a->a.lns = (float4 *)(b + L.lns);
   a->a.ab = (float2 *)(b + L.ab);
   a->a.acc = (double *)(b + L.acc);
+  a->a.freeze_sin = 0.05f;
+  a->a.c_min = 1e-3f;
   a->ln_bytes = L.lns - L.ln;
   a->lns_bytes = L.ab - L.lns;
   a->lphis_bytes = L.ln - L.lphis;
@@ -610,6 +636,18 @@ lbm_status lbm_adj_get_lambda(lbm_adj a, float *lt_dev, float *ls_dev,
     e = cudaMemcpyAsync(ls_dev, a->a.ls_out, sizeof(float4) * (size_t)d.NF,
                         cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return afail(a, LBM_ERR_CUDA, cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+lbm_status lbm_adj_set_freeze(lbm_adj a, double freeze_sin) {
+  if (!a || !(freeze_sin >= 0.0) || freeze_sin > 1.0) return LBM_ERR_ARG;
+  a->a.freeze_sin = (float)freeze_sin;
+  return LBM_OK;
+}
+
+lbm_status lbm_adj_set_cmin(lbm_adj a, double c_min) {
+  if (!a || !(c_min >= 0.0) || c_min > 10.0) return LBM_ERR_ARG;
+  a->a.c_min = (float)c_min;
   return LBM_OK;
 }
 

@@ -40,7 +40,8 @@ EXPORTS = ("lbm_workspace_bytes", "lbm_init_geometry", "lbm_set_params",
            "lbm_state_bytes", "lbm_save_state", "lbm_load_state",
            "lbm_adj_workspace_bytes", "lbm_adj_create", "lbm_adj_seed_sw",
            "lbm_adj_step", "lbm_adj_gradients", "lbm_adj_get_lambda",
-           "lbm_adj_last_error", "lbm_adj_destroy")
+           "lbm_adj_set_freeze", "lbm_adj_set_cmin", "lbm_adj_last_error",
+           "lbm_adj_destroy")
 
 
 class LbmError(RuntimeError):
@@ -138,6 +139,10 @@ def load_library(path: str = LIB_PATH):
     L.lbm_adj_gradients.argtypes = [vp, C.POINTER(C.c_double), vp]
     L.lbm_adj_get_lambda.restype = C.c_int
     L.lbm_adj_get_lambda.argtypes = [vp, vp, vp, vp]
+    L.lbm_adj_set_freeze.restype = C.c_int
+    L.lbm_adj_set_freeze.argtypes = [vp, C.c_double]
+    L.lbm_adj_set_cmin.restype = C.c_int
+    L.lbm_adj_set_cmin.argtypes = [vp, C.c_double]
     L.lbm_adj_last_error.restype = C.c_char_p
     L.lbm_adj_last_error.argtypes = [vp]
     L.lbm_adj_destroy.restype = None
@@ -537,6 +542,16 @@ def lbm_adj_get_lambda(a, lt, ls, stream):
     _acheck(load_library().lbm_adj_get_lambda(
         a, C.c_void_p(lt.data_ptr()), C.c_void_p(ls.data_ptr()), stream), a,
         "lbm_adj_get_lambda")
+
+
+def lbm_adj_set_freeze(a, freeze_sin: float):
+    _acheck(load_library().lbm_adj_set_freeze(a, float(freeze_sin)), a,
+            "lbm_adj_set_freeze")
+
+
+def lbm_adj_set_cmin(a, c_min: float):
+    _acheck(load_library().lbm_adj_set_cmin(a, float(c_min)), a,
+            "lbm_adj_set_cmin")
 
 
 def lbm_adj_last_error(a) -> str:

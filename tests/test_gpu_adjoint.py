@@ -44,25 +44,29 @@ def session(torch, case):
     return s
 
 
-def tlm(case, steps, g_axis=0):
+def tlm(case, steps, g_axis=0, freeze=0.0, cmin=0.0):
     t = O.TangentLinear(case.lattice, case.solid, case.periodic, g_axis)
     t.set_params(**case.params)
+    t.set_freeze(freeze)
+    t.set_cmin(cmin)
     t.init_state(case.phi0)
     t.step(steps)
     return t.sw()
 
 
-@pytest.mark.parametrize("name,case,steps", CASES, ids=[c[0] for c in CASES])
-def test_adjoint_matches_tangent_linear(torch, name, case, steps):
+def compare(torch, case, steps, freeze, cmin):
     """Every gradient component within 1e-3 of the FP64 tangent-linear
     value, relative to the size of the gradient it belongs to: theta on its
     own, g as a vector (a component that nearly cancels, like g_x on a
-    drop symmetric in x, is judged against |dJ/dg|)."""
+    drop symmetric in x, is judged against |dJ/dg|). Both sides take the
+    same linearisation (freeze: Scheme-II, cmin: the normal n_c)."""
     from paper_2407_10914_gb300.adjoint import Run
-    refs = [tlm(case, steps, a) for a in range(2 if case.lattice == 9 else 3)]
+    refs = [tlm(case, steps, a, freeze, cmin)
+            for a in range(2 if case.lattice == 9 else 3)]
     J_ref, dth_ref = refs[0][0], refs[0][1]
     dg_ref = np.array([r[2] for r in refs] + [0.0] * (3 - len(refs)))
-    run = Run(session(torch, case), case.phi0, steps)
+    run = Run(session(torch, case), case.phi0, steps, freeze_sin=freeze,
+              c_min=cmin)
     J = run.forward()
     dth, dg = run.backward()
     assert J == pytest.approx(J_ref, rel=2e-5)
@@ -76,12 +80,26 @@ def test_adjoint_matches_tangent_linear(torch, name, case, steps):
         assert dth == 0.0 and dth_ref == 0.0
 
 
+@pytest.mark.parametrize("name,case,steps", CASES, ids=[c[0] for c in CASES])
+def test_adjoint_matches_tangent_linear(torch, name, case, steps):
+    """The exact derivative (no regularisation) on short runs."""
+    compare(torch, case, steps, 0.0, 0.0)
+
+
+def test_regularised_adjoint_matches_regularised_tangent_linear(torch):
+    """The default regularised linearisation, on both sides, over a run long
+    enough for wetting nodes with n_c almost along n_w."""
+    case = W.adjoint_pack(n=(40, 36, 32), slab=6, steps=150)
+    compare(torch, case, 150, 0.05, 1e-3)
+
+
 def test_checkpoint_interval_does_not_change_the_gradient(torch):
     from paper_2407_10914_gb300.adjoint import Run
     case, steps = CASES[2][1], CASES[2][2]
     out = []
     for every in (1, 3, steps):
-        run = Run(session(torch, case), case.phi0, steps, every=every)
+        run = Run(session(torch, case), case.phi0, steps, every=every,
+                  freeze_sin=0.0, c_min=0.0)
         run.forward()
         dth, dg = run.backward()
         out.append((dth, dg[0]))
@@ -102,7 +120,7 @@ def test_autograd_function(torch):
     run = Run(session(torch, case), case.phi0, steps)
     J2 = run.forward()
     dth, dg = run.backward()
-    assert float(J) == pytest.approx(J2, rel=1e-7)
+    assert float(J.detach()) == pytest.approx(J2, rel=1e-7)
     # atomics sum in any order: two sweeps agree to float32 rounding of
     # the gradient's largest component
     assert float(th.grad) == pytest.approx(dth * math.pi / 180.0, rel=1e-5)

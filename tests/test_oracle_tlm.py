@@ -73,3 +73,26 @@ def test_tangent_linear_matches_central_differences(name, case, steps):
     assert abs(dth) > 1e-6 and abs(dg) > 1e-6, (dth, dg)  # both act
     assert dth == pytest.approx(fd_th, rel=1e-6), (dth, fd_th)
     assert dg == pytest.approx(fd_g, rel=1e-5), (dg, fd_g)
+
+
+def test_regularised_linearisation_changes_derivatives_only():
+    """freeze_sin / c_min hold directions constant in the linearisation:
+    the values (S_w) are those of the plain oracle, and thresholds below
+    every node's sin(theta') and |C| leave the derivatives exact."""
+    name, case, steps = CASES[0]
+    exact = tlm_after(case, steps)
+
+    def run(freeze, cmin):
+        t = O.TangentLinear(case.lattice, case.solid, case.periodic)
+        t.set_params(**case.params)
+        t.set_freeze(freeze)
+        t.set_cmin(cmin)
+        t.init_state(case.phi0)
+        t.step(steps)
+        return t.sw()
+
+    tiny = run(1e-12, 1e-12)
+    assert tiny == exact
+    big = run(1.0, 10.0)
+    assert big[0] == pytest.approx(exact[0], rel=1e-13)
+    assert big[1] != exact[1]  # the held directions change the derivative
