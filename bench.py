@@ -15,7 +15,14 @@ One JSON line on rank 0:
              nodes it processes; every pass's figures are under "passes";
   step_bandwidth  the step-level accounting of 308 B per fluid-node update
              (2 x 2Q populations of 4 B plus a 4 B link mask);
-  cpu_baseline  the FP64 oracle on a bounded slab of the same rock.
+  cpu_baseline  the FP64 oracle on a bounded slab of the same rock;
+  storage_16bit the same rock with FP16 / BF16 population storage, each
+             with its error against the FP64 oracle on a slab;
+  batched    the 96-drop contact-angle sweep stepped as one batch
+             (autotuned schedule);
+  adjoint    the gradient of the smooth saturation after 2000 steps of the
+             128^3 imbibition pack w.r.t. theta and g_x, beside central
+             finite differences.
 
 `--impl reference` times the oracle (the reference arm of this build) on the
 host cores instead. Several GPUs (torchrun) run independent replicas.
@@ -86,6 +93,8 @@ def parse():
                     help="skip the 96-drop batched sweep object")
     ap.add_argument("--batched-cases", type=int, default=96)
     ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--no-16bit", action="store_true",
+                    help="skip the FP16/BF16-storage objects")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the gradient (adjoint) object")
     ap.add_argument("--adjoint-size", type=int, default=128)
@@ -340,6 +349,10 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = end_to_end(args, case, torch, lbm)
 
+    sixteen = None
+    if not args.no_16bit and rank == 0:
+        sixteen = run_16bit(args, torch, lbm, case, min(args.steps, 500))
+
     batched = None
     if not args.no_batched:
         batched = run_batched(args, torch, lbm)
@@ -392,6 +405,8 @@ def run_ours(args):
         }
         if e2e:
             line["e2e"] = e2e
+        if sixteen:
+            line["storage_16bit"] = sixteen
         if batched:
             line["batched"] = batched
         if adjoint:
@@ -451,6 +466,61 @@ def end_to_end(args, case, torch, lbm):
             "final_sw": sw, "seconds": round(dt, 3),
             "note": "geometry set-up, phi0 upload, per-step S_w read-back "
                     "and the final phi download inside the timed region"}
+
+
+def run_16bit(args, torch, lbm, case, steps: int):
+    """The same rock with the f''_i planes stored as 16-bit offsets (FP16,
+    BF16): throughput over `steps` steps, per-pass times, and the error
+    against the FP64 oracle after 10 steps from the initial state on the
+    32-plane slab (max |f_gpu - f_oracle| / max |f_oracle| per colour), with
+    the FP32 storage's error on the same slab beside it."""
+    from oracle import oracle as O
+    out = {}
+    slab = oracle_sample(case, 32)
+    o = O.Oracle(slab.lattice, slab.solid, slab.periodic)
+    o.set_params(**slab.params)
+    o.init_state(slab.phi0)
+    o.step(10)
+    ref = o.pops
+    fl = slab.solid == 0
+
+    def slab_err(storage):
+        t = lbm.Session(slab.lattice, slab.solid, slab.periodic, storage)
+        t.set_params(**slab.params)
+        t.init_state(slab.phi0.astype(np.float32))
+        t.step(10)
+        got = t.get_populations().cpu().numpy().astype(np.float64)
+        return max(float(np.abs(got[c][:, fl] - ref[c][:, fl]).max()
+                         / np.abs(ref[c][:, fl]).max()) for c in range(2))
+
+    out["fp32_slab_error"] = slab_err("fp32")
+    stream = torch.cuda.current_stream()
+    for storage in ("fp16", "bf16"):
+        s = lbm.Session(case.lattice, case.solid, case.periodic, storage)
+        s.set_params(**case.params)
+        s.init_state(case.phi0.astype(np.float32))
+        s.step(args.warmup)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        k2 = min(steps, 100)
+        pm = s.step_timed(k2)
+        out[storage] = {
+            "value": round(s.n_fluid / (ms * 1e-3) / 1e6, 2), "unit": "MLUPS",
+            "ms_per_step": round(ms, 4),
+            "pass_ms_per_step": {k: round(v / k2, 5) for k, v in pm.items()},
+            "bytes_per_update_survey": 2 * 2 * case.lattice * 2 + 4,
+            "error_vs_fp64_oracle": slab_err(storage),
+            "error_sample": "32-plane slab of the rock, 10 steps from the "
+                            "initial state, max relative population error",
+        }
+        del s
+    return out
 
 
 def run_batched(args, torch, lbm):
