@@ -97,6 +97,12 @@ typedef struct {
                           1 - zeta^r; the inlet phase field is zeta^r -
                           zeta^b (Sec. II.D.1)                              */
   double g[3];         /* body acceleration; force density rho*g (Eq. 36)  */
+  int collision;       /* 0: Eq. 2 with one rate S_nu for every
+                          non-conserved moment (single-rate reading);
+                          1: MRT, Eq. 2 with the rates of Eq. 4: S_e =
+                          S_eps = S_pi = S_nu (Eq. 15), S_q = S_m =
+                          8 (2 - S_nu) / (8 - S_nu) (Eq. 16). MRT is D3Q19
+                          only (Appendix A); D2Q9 gives LBM_ERR_ARG       */
 } lbm_params;
 
 /* Device bytes one domain needs (populations A/B, phase field, normals,

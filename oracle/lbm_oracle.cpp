@@ -25,6 +25,10 @@
 //   * collision: the single-rate (BGK) form of Eq. (2): rate S_nu (Eq. 13)
 //     for every non-conserved moment, rate 0 for rho and j, equilibrium of
 //     Eq. (A.4) and forcing of Eq. (A.5), written in velocity space;
+//     or (collision = 1, D3Q19) the MRT form in moment space with the
+//     rates of Eq. (4) read with 19 entries and Eqs. (15)-(16), m_10 and
+//     m_12 of Eq. (A.4) read as -1/2 of m_9 and m_11; in both, Eq. (2) is
+//     read with S^F outside the product with S;
 //   * D2Q9 = the z-free subset of the D3Q19 set of Eq. (A.1), in the same
 //     order, with weights 4/9, 1/9, 1/36;
 //   * out-of-domain neighbours on a non-periodic axis: halfway bounce-back
@@ -68,6 +72,72 @@ const int E_D3Q19[19][3] = {
     {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, 1, 0}, {1, -1, 0},
     {-1, -1, 0}, {1, 0, 1},  {-1, 0, 1}, {1, 0, -1}, {-1, 0, -1},
     {0, 1, 1},  {0, -1, 1},  {0, 1, -1}, {0, -1, -1}};
+
+// Eq. (3): the 19 moments of D3Q19 in the paper's order, (rho, e, eps, j_x,
+// q_x, j_y, q_y, j_z, q_z, 3p_xx, 3pi_xx, p_ww, pi_ww, p_xy, p_yz, p_xz, m_x,
+// m_y, m_z), each written as the polynomial of the velocity e = (x, y, z)
+// (s = |e|^2) whose values at the 19 velocities are one row of the
+// transformation matrix of Eq. (A.3).
+double moment_poly(int k, const int v[3]) {
+  const double x = v[0], y = v[1], z = v[2], s = x * x + y * y + z * z;
+  switch (k) {
+    case 0: return 1.0;
+    case 1: return 19.0 * s - 30.0;
+    case 2: return (21.0 * s * s - 53.0 * s + 24.0) / 2.0;
+    case 3: return x;
+    case 4: return (5.0 * s - 9.0) * x;
+    case 5: return y;
+    case 6: return (5.0 * s - 9.0) * y;
+    case 7: return z;
+    case 8: return (5.0 * s - 9.0) * z;
+    case 9: return 3.0 * x * x - s;
+    case 10: return (3.0 * s - 5.0) * (3.0 * x * x - s);
+    case 11: return y * y - z * z;
+    case 12: return (3.0 * s - 5.0) * (y * y - z * z);
+    case 13: return x * y;
+    case 14: return y * z;
+    case 15: return x * z;
+    case 16: return x * (y * y - z * z);
+    case 17: return y * (z * z - x * x);
+    case 18: return z * (x * x - y * y);
+  }
+  return 0.0;
+}
+
+// M of Eq. (A.3), M[k][i] = moment k of velocity i (Eq. A.1 order), and its
+// inverse by Gauss-Jordan elimination with partial pivoting.
+struct MomentBasis {
+  double M[19][19], Minv[19][19];
+  MomentBasis() {
+    double A[19][38];
+    for (int k = 0; k < 19; ++k)
+      for (int i = 0; i < 19; ++i) {
+        M[k][i] = moment_poly(k, E_D3Q19[i]);
+        A[k][i] = M[k][i];
+        A[k][19 + i] = (k == i) ? 1.0 : 0.0;
+      }
+    for (int c = 0; c < 19; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < 19; ++r)
+        if (std::fabs(A[r][c]) > std::fabs(A[piv][c])) piv = r;
+      for (int j = 0; j < 38; ++j) std::swap(A[c][j], A[piv][j]);
+      const double d = A[c][c];
+      for (int j = 0; j < 38; ++j) A[c][j] /= d;
+      for (int r = 0; r < 19; ++r) {
+        if (r == c || A[r][c] == 0.0) continue;
+        const double f = A[r][c];
+        for (int j = 0; j < 38; ++j) A[r][j] -= f * A[c][j];
+      }
+    }
+    for (int k = 0; k < 19; ++k)
+      for (int i = 0; i < 19; ++i) Minv[k][i] = A[k][19 + i];
+  }
+};
+
+const MomentBasis &moment_basis() {
+  static const MomentBasis b;
+  return b;
+}
 
 // Forward-mode derivatives for the tangent-linear run: a value and its
 // derivatives along two directions (the contact angle in radians and the
@@ -183,6 +253,7 @@ typedef struct {
   double rho_in, rho_out;  // Zou-He densities (B.1, B.9)
   double zeta_r;        // injected red fraction zeta^r; zeta^b = 1 - zeta^r
   double g[3];          // body acceleration (Type-II), Eq. (36)
+  int collision;        // 0 single-rate Eq. (2); 1 MRT (Eqs. 2, 4, 15-16)
 } orc_params;
 
 }  // extern "C"
@@ -719,6 +790,99 @@ struct OracleT {
       for (int a = 0; a < 3; ++a) u_out[a] = u[a];
   }
 
+  // Single-node MRT collision of D3Q19, Eq. (2) in moment space:
+  //   m = M f,  f'' = f - M^-1 S (m - m^eq) + M^-1 S^F,
+  // read with S^F outside the product with S (as in the single-rate form
+  // above). S is the diagonal of Eq. (4) taken with 19 entries (the print's
+  // 20 carry a spurious 0 before the first S_nu):
+  //   (0, S_e, S_eps, 0, S_q, 0, S_q, 0, S_q, S_nu, S_pi, S_nu, S_pi,
+  //    S_nu, S_nu, S_nu, S_m, S_m, S_m)
+  // with S_e = S_eps = S_pi = S_nu (Eq. 15); S_q and S_m are passed in (the
+  // step uses Eq. 16). m^eq is Eq. (A.4), m_10 read as -(1/2) m_9 and m_12
+  // as -(1/2) m_11 (the print's -3/2 p_xx drops the 1/3 of p_xx = m_9 / 3);
+  // S^F is Eq. (A.5), each entry with the (1 - S_k/2) of its own rate.
+  // u is Eq. (22): u = (j + F/2) / rho with j = (m_3, m_5, m_7).
+  template <class T>
+  static void collide_mrt(const T *ft, const T Fv[3], const T &Snu,
+                          const T &Sq, const T &Sm, double rho0, T *out,
+                          T u_out[3]) {
+    const MomentBasis &B = moment_basis();
+    T m[19];
+    for (int k = 0; k < 19; ++k) {
+      m[k] = 0.0;
+      for (int i = 0; i < 19; ++i) m[k] += B.M[k][i] * ft[i];
+    }
+    const T rho = m[0];
+    T u[3];
+    u[0] = (m[3] + 0.5 * Fv[0]) / rho;
+    u[1] = (m[5] + 0.5 * Fv[1]) / rho;
+    u[2] = (m[7] + 0.5 * Fv[2]) / rho;
+    const T ux = u[0], uy = u[1], uz = u[2];
+    const T Fx = Fv[0], Fy = Fv[1], Fz = Fv[2];
+    const T u2 = ux * ux + uy * uy + uz * uz;
+    const T uF = ux * Fx + uy * Fy + uz * Fz;
+    const T Se = Snu, Seps = Snu, Spi = Snu;  // Eq. (15)
+    const T zero = 0.0;
+    const T S[19] = {zero, Se,  Seps, zero, Sq,  zero, Sq,  zero, Sq, Snu,
+                     Spi,  Snu, Spi,  Snu,  Snu, Snu,  Sm,  Sm,   Sm};
+    const T pxx3 = rho0 * (2.0 * ux * ux - uy * uy - uz * uz);
+    const T pww = rho0 * (uy * uy - uz * uz);
+    const T meq[19] = {rho,
+                       -11.0 * rho + 19.0 * rho0 * u2,
+                       3.0 * rho - 5.5 * rho0 * u2,
+                       rho0 * ux,
+                       -(2.0 / 3.0) * rho0 * ux,
+                       rho0 * uy,
+                       -(2.0 / 3.0) * rho0 * uy,
+                       rho0 * uz,
+                       -(2.0 / 3.0) * rho0 * uz,
+                       pxx3,
+                       -0.5 * pxx3,
+                       pww,
+                       -0.5 * pww,
+                       rho0 * ux * uy,
+                       rho0 * uy * uz,
+                       rho0 * ux * uz,
+                       zero,
+                       zero,
+                       zero};
+    const T h[19] = {zero,
+                     38.0 * uF,
+                     -11.0 * uF,
+                     Fx,
+                     -(2.0 / 3.0) * Fx,
+                     Fy,
+                     -(2.0 / 3.0) * Fy,
+                     Fz,
+                     -(2.0 / 3.0) * Fz,
+                     2.0 * (2.0 * ux * Fx - uy * Fy - uz * Fz),
+                     -2.0 * ux * Fx + uy * Fy + uz * Fz,
+                     2.0 * (uy * Fy - uz * Fz),
+                     -uy * Fy + uz * Fz,
+                     uy * Fx + ux * Fy,
+                     uz * Fy + uy * Fz,
+                     ux * Fz + uz * Fx,
+                     zero,
+                     zero,
+                     zero};
+    T dm[19];
+    for (int k = 0; k < 19; ++k)
+      dm[k] = -S[k] * (m[k] - meq[k]) + (1.0 - 0.5 * S[k]) * h[k];
+    for (int i = 0; i < 19; ++i) {
+      T acc = ft[i];
+      for (int k = 0; k < 19; ++k) acc += B.Minv[i][k] * dm[k];
+      out[i] = acc;
+    }
+    if (u_out)
+      for (int a = 0; a < 3; ++a) u_out[a] = u[a];
+  }
+
+  // Eq. (16): the rate of the q and m moments from S_nu.
+  template <class T>
+  static T mrt_rate(const T &Snu) {
+    return 8.0 * (2.0 - Snu) / (8.0 - Snu);
+  }
+
  private:
   // Eqs. (13)-(14): harmonic-mean viscosity, S_nu = 1 / (3 nu + 1/2);
   // phi is clamped to [-1, 1] here only.
@@ -730,7 +894,8 @@ struct OracleT {
     return 1.0 / (3.0 * nu + 0.5);
   }
 
-  // Collision (Eq. 2, BGK reading) followed by recolouring, Eqs. (20)-(21):
+  // Collision (Eq. 2: single-rate reading, or MRT with the rates of Eqs.
+  // 15-16 when collision = 1) followed by recolouring, Eqs. (20)-(21):
   //   f^r'_i = rho^r/rho f^t''_i + beta w_i rho^r rho^b / rho (e_i . n)
   //   f^b'_i = f^t''_i - f^r'_i
   // with n the post-wetting interface normal n_c (the i = 0 term vanishes
@@ -744,7 +909,12 @@ struct OracleT {
         ft[i] = ftmp[(0L * L.Q + i) * N + n] + ftmp[(1L * L.Q + i) * N + n];
       for (int a = 0; a < 3; ++a) Fv[a] = F[a * N + n];
       R S = relaxation_rate(phi[n]);
-      collide(L, ft, Fv, S, p.rho0, fpp, uu);
+      if (p.collision == 1) {
+        const R Sq = mrt_rate(S);
+        collide_mrt(ft, Fv, S, Sq, Sq, p.rho0, fpp, uu);
+      } else {
+        collide(L, ft, Fv, S, p.rho0, fpp, uu);
+      }
       for (int a = 0; a < 3; ++a) u[a * N + n] = uu[a];
       R r = rho_r[n], b = rho_b[n], rho = r + b;
       R nv[3] = {nc[0 * N + n], nc[1 * N + n], nc[2 * N + n]};
@@ -842,8 +1012,14 @@ void *orc_create(int lattice, int nx, int ny, int nz, const uint8_t *solid,
 
 void orc_destroy(void *h) { delete static_cast<Oracle *>(h); }
 
-void orc_set_params(void *h, const orc_params *p) {
-  static_cast<Oracle *>(h)->set_params(*p, p->theta_deg * PI / 180.0, p->g);
+// Returns 0, or -1 (parameters unchanged) for a collision other than 0/1 or
+// MRT (collision = 1) on D2Q9: Appendix A defines it for D3Q19 only.
+int orc_set_params(void *h, const orc_params *p) {
+  Oracle *o = static_cast<Oracle *>(h);
+  if (p->collision != 0 && p->collision != 1) return -1;
+  if (p->collision == 1 && o->L.Q != 19) return -1;
+  o->set_params(*p, p->theta_deg * PI / 180.0, p->g);
+  return 0;
 }
 
 void orc_init_state(void *h, const double *phi0) {
@@ -1000,6 +1176,20 @@ void orc_collide(int lattice, const double *ft, const double *F, double S,
   Oracle::collide(L, ft, F, S, rho0, out, u);
 }
 
+// One node's MRT collision (D3Q19, Eq. 2 in moment space) with the rates
+// S_nu, S_q, S_m given; Eq. (15) fixes the others to S_nu.
+void orc_collide_mrt(const double *ft, const double *F, double Snu, double Sq,
+                     double Sm, double rho0, double *out, double *u) {
+  Oracle::collide_mrt(ft, F, Snu, Sq, Sm, rho0, out, u);
+}
+
+// M of Eq. (A.3) as the oracle builds it (19 x 19, row = moment).
+void orc_moment_matrix(double *M) {
+  const MomentBasis &B = moment_basis();
+  for (int k = 0; k < 19; ++k)
+    for (int i = 0; i < 19; ++i) M[19 * k + i] = B.M[k][i];
+}
+
 // ---- tangent-linear run ----------------------------------------------------
 // The same step on Dual numbers: every field carries its derivatives with
 // respect to the contact angle theta (radians; direction 0) and one
@@ -1031,11 +1221,15 @@ void orc_tlm_set_cmin(void *h, double c_min) {
 }
 
 // Direction 1 is the component g_axis of the body acceleration.
-void orc_tlm_set_params(void *h, const orc_params *p, int g_axis) {
+int orc_tlm_set_params(void *h, const orc_params *p, int g_axis) {
+  if (p->collision != 0 && p->collision != 1) return -1;
+  if (p->collision == 1 && static_cast<OracleT<Dual> *>(h)->L.Q != 19)
+    return -1;
   const Dual th(p->theta_deg * PI / 180.0, 1.0, 0.0);
   Dual gg[3] = {Dual(p->g[0]), Dual(p->g[1]), Dual(p->g[2])};
   gg[g_axis] = Dual(p->g[g_axis], 0.0, 1.0);
   static_cast<OracleT<Dual> *>(h)->set_params(*p, th, gg);
+  return 0;
 }
 
 void orc_tlm_init_state(void *h, const double *phi0) {

@@ -41,7 +41,8 @@ class _Params(C.Structure):
                 ("wetting", C.c_int), ("zou_he", C.c_int),
                 ("flow_axis", C.c_int),
                 ("rho_in", C.c_double), ("rho_out", C.c_double),
-                ("zeta_r", C.c_double), ("g", C.c_double * 3)]
+                ("zeta_r", C.c_double), ("g", C.c_double * 3),
+                ("collision", C.c_int)]
 
 
 _lib = None
@@ -56,7 +57,12 @@ def lib():
         L.orc_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int,
                                  C.c_void_p, C.c_uint]
         L.orc_destroy.argtypes = [C.c_void_p]
+        L.orc_set_params.restype = C.c_int
         L.orc_set_params.argtypes = [C.c_void_p, C.POINTER(_Params)]
+        L.orc_collide_mrt.argtypes = [C.c_void_p, C.c_void_p, C.c_double,
+                                      C.c_double, C.c_double, C.c_double,
+                                      C.c_void_p, C.c_void_p]
+        L.orc_moment_matrix.argtypes = [C.c_void_p]
         L.orc_init_state.argtypes = [C.c_void_p, C.c_void_p]
         L.orc_set_pops.argtypes = [C.c_void_p, C.c_void_p]
         L.orc_get_pops.argtypes = [C.c_void_p, C.c_void_p]
@@ -77,6 +83,7 @@ def lib():
         L.orc_tlm_create.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int,
                                      C.c_void_p, C.c_uint]
         L.orc_tlm_destroy.argtypes = [C.c_void_p]
+        L.orc_tlm_set_params.restype = C.c_int
         L.orc_tlm_set_params.argtypes = [C.c_void_p, C.POINTER(_Params),
                                          C.c_int]
         L.orc_tlm_init_state.argtypes = [C.c_void_p, C.c_void_p]
@@ -127,9 +134,38 @@ def collide(q, ft, F, S, rho0=1.0):
     return out, u
 
 
+def collide_mrt(ft, F, S, rho0=1.0, Sq=None, Sm=None):
+    """MRT collision of one D3Q19 node (Eq. 2 in moment space); S_q and S_m
+    default to Eq. (16)."""
+    ft = np.ascontiguousarray(ft, np.float64)
+    Fv = np.ascontiguousarray(F, np.float64)
+    if Sq is None:
+        Sq = mrt_rate(S)
+    if Sm is None:
+        Sm = mrt_rate(S)
+    out = np.zeros(19)
+    u = np.zeros(3)
+    lib().orc_collide_mrt(_ptr(ft), _ptr(Fv), float(S), float(Sq), float(Sm),
+                          float(rho0), _ptr(out), _ptr(u))
+    return out, u
+
+
+def mrt_rate(S):
+    """Eq. (16): S_q = S_m = 8 (2 - S_nu) / (8 - S_nu)."""
+    return 8.0 * (2.0 - S) / (8.0 - S)
+
+
+def moment_matrix():
+    """The oracle's M (Eq. A.3), built from the moment polynomials."""
+    M = np.zeros(19 * 19)
+    lib().orc_moment_matrix(_ptr(M))
+    return M.reshape(19, 19)
+
+
 PARAM_DEFAULTS = dict(tau_r=1.0, tau_b=1.0, gamma=0.01, beta=0.7, rho0=1.0,
                       theta_deg=90.0, wetting=0, zou_he=0, flow_axis=0,
-                      rho_in=1.0, rho_out=1.0, zeta_r=1.0, g=(0.0, 0.0, 0.0))
+                      rho_in=1.0, rho_out=1.0, zeta_r=1.0, g=(0.0, 0.0, 0.0),
+                      collision=0)
 
 
 class Oracle:
@@ -166,8 +202,10 @@ class Oracle:
         st = _Params(p["tau_r"], p["tau_b"], p["gamma"], p["beta"], p["rho0"],
                      p["theta_deg"], int(p["wetting"]), int(p["zou_he"]),
                      int(p["flow_axis"]), p["rho_in"], p["rho_out"],
-                     p["zeta_r"], (C.c_double * 3)(*p["g"]))
-        lib().orc_set_params(self._h, C.byref(st))
+                     p["zeta_r"], (C.c_double * 3)(*p["g"]),
+                     int(p["collision"]))
+        if lib().orc_set_params(self._h, C.byref(st)) != 0:
+            raise ValueError("collision must be 0 or 1 (MRT: D3Q19 only)")
 
     def init_state(self, phi0: np.ndarray):
         a = np.ascontiguousarray(np.broadcast_to(phi0, self.shape), np.float64)
@@ -252,8 +290,10 @@ class TangentLinear:
         st = _Params(p["tau_r"], p["tau_b"], p["gamma"], p["beta"], p["rho0"],
                      p["theta_deg"], int(p["wetting"]), int(p["zou_he"]),
                      int(p["flow_axis"]), p["rho_in"], p["rho_out"],
-                     p["zeta_r"], (C.c_double * 3)(*p["g"]))
-        lib().orc_tlm_set_params(self._h, C.byref(st), self.g_axis)
+                     p["zeta_r"], (C.c_double * 3)(*p["g"]),
+                     int(p["collision"]))
+        if lib().orc_tlm_set_params(self._h, C.byref(st), self.g_axis) != 0:
+            raise ValueError("collision must be 0 or 1 (MRT: D3Q19 only)")
 
     def init_state(self, phi0: np.ndarray):
         a = np.ascontiguousarray(np.broadcast_to(phi0, self.shape), np.float64)

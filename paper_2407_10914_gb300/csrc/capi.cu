@@ -242,6 +242,10 @@ lbm_status lbm_set_params(lbm_handle c, const lbm_params *p) {
     return fail(c, LBM_ERR_ARG, "flow_axis must be 0, 1 or 2");
   if (p->zou_he != 0 && p->zou_he != 1)
     return fail(c, LBM_ERR_ARG, "zou_he must be 0 or 1");
+  if (p->collision != 0 && p->collision != 1)
+    return fail(c, LBM_ERR_ARG, "collision must be 0 or 1");
+  if (p->collision == 1 && c->Q != 19)
+    return fail(c, LBM_ERR_ARG, "MRT collision is defined for D3Q19 only");
   for (int a = 0; a < 3; ++a)
     if (!std::isfinite(p->g[a])) return fail(c, LBM_ERR_ARG, "g not finite");
   if (p->zou_he) {
@@ -283,6 +287,7 @@ lbm_status lbm_set_params(lbm_handle c, const lbm_params *p) {
     std::memcpy(&k.m_in, &bits, 4);
   }
   for (int a = 0; a < 3; ++a) k.g[a] = (float)p->g[a];
+  k.mrt = p->collision;
   c->params_set = true;
   ++c->gen;
   return LBM_OK;

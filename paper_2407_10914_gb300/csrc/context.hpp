@@ -42,6 +42,7 @@ struct StepConst {
   float rho_in_r, rho_in_b, rho_out;  // rho_in zeta^s, rho_out
   float m_in;                          // encoded inlet phase field
   float g[3];
+  int mrt;  // 1: Eq. 2 with the rates of Eqs. 4, 15-16 (D3Q19)
 };
 
 // Everything a kernel needs, passed by value.

@@ -56,7 +56,8 @@ class lbm_params(C.Structure):
                 ("wetting", C.c_int), ("zou_he", C.c_int),
                 ("flow_axis", C.c_int),
                 ("rho_in", C.c_double), ("rho_out", C.c_double),
-                ("zeta_r", C.c_double), ("g", C.c_double * 3)]
+                ("zeta_r", C.c_double), ("g", C.c_double * 3),
+                ("collision", C.c_int)]
 
 
 _lib = None
@@ -177,7 +178,7 @@ def _dptr(t) -> C.c_void_p:
 def make_params(**kw) -> lbm_params:
     d = dict(tau_r=1.0, tau_b=1.0, gamma=0.01, beta=0.95, rho0=1.0,
              theta_deg=90.0, wetting=0, zou_he=0, flow_axis=0, rho_in=1.0,
-             rho_out=1.0, zeta_r=1.0, g=(0.0, 0.0, 0.0))
+             rho_out=1.0, zeta_r=1.0, g=(0.0, 0.0, 0.0), collision=0)
     for k in kw:
         if k not in d:
             raise KeyError(k)
@@ -185,7 +186,8 @@ def make_params(**kw) -> lbm_params:
     return lbm_params(d["tau_r"], d["tau_b"], d["gamma"], d["beta"],
                       d["rho0"], d["theta_deg"], int(d["wetting"]),
                       int(d["zou_he"]), int(d["flow_axis"]), d["rho_in"],
-                      d["rho_out"], d["zeta_r"], (C.c_double * 3)(*d["g"]))
+                      d["rho_out"], d["zeta_r"], (C.c_double * 3)(*d["g"]),
+                      int(d["collision"]))
 
 
 # ------------------------------------------------ one-to-one C wrappers

@@ -59,7 +59,8 @@ class Case:
 def base_params(**kw) -> dict:
     p = dict(tau_r=1.0, tau_b=1.0, gamma=0.01, beta=0.95, rho0=1.0,
              theta_deg=90.0, wetting=0, zou_he=0, flow_axis=0,
-             rho_in=1.0, rho_out=1.0, zeta_r=1.0, g=(0.0, 0.0, 0.0))
+             rho_in=1.0, rho_out=1.0, zeta_r=1.0, g=(0.0, 0.0, 0.0),
+             collision=0)
     p.update(kw)
     return p
 
@@ -134,6 +135,20 @@ def channel_2d(nx=4, ny=33, g=1e-6, tau=1.0, steps=4000) -> Case:
     phi0[solid == 1] = 0.0
     p = base_params(tau_r=tau, tau_b=tau, g=(g, 0.0, 0.0))
     return Case("channel2d", 9, solid, (True, False, True), phi0, p, steps)
+
+
+def channel_3d(nx=4, ny=19, nz=4, g=1e-6, tau=1.0, collision=0,
+               steps=4000) -> Case:
+    """Single-phase (all red) D3Q19 channel between solid planes y = 0 and
+    y = ny - 1, periodic in x and z, driven by a body acceleration along x."""
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    solid[:, 0, :] = 1
+    solid[:, ny - 1, :] = 1
+    phi0 = np.ones((nz, ny, nx))
+    phi0[solid == 1] = 0.0
+    p = base_params(tau_r=tau, tau_b=tau, g=(g, 0.0, 0.0),
+                    collision=collision)
+    return Case("channel3d", 19, solid, (True, False, True), phi0, p, steps)
 
 
 def tube_3d(nx=256, ny=20, nz=20, radius=8.0, red_len=32, theta_deg=90.0,
