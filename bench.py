@@ -16,6 +16,8 @@ One JSON line on rank 0:
   step_bandwidth  the step-level accounting of 308 B per fluid-node update
              (2 x 2Q populations of 4 B plus a 4 B link mask);
   cpu_baseline  the FP64 oracle on a bounded slab of the same rock;
+  mrt        the same rock with the MRT collision (Eq. 2 with the rates of
+             Eqs. 4, 15-16), with its error against the FP64 oracle's MRT;
   storage_16bit the same rock with FP16 / BF16 population storage, each
              with its error against the FP64 oracle on a slab;
   batched    the 96-drop contact-angle sweep stepped as one batch
@@ -93,6 +95,8 @@ def parse():
                     help="skip the 96-drop batched sweep object")
     ap.add_argument("--batched-cases", type=int, default=96)
     ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--no-mrt", action="store_true",
+                    help="skip the MRT-collision object")
     ap.add_argument("--no-16bit", action="store_true",
                     help="skip the FP16/BF16-storage objects")
     ap.add_argument("--no-adjoint", action="store_true",
@@ -349,6 +353,10 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = end_to_end(args, case, torch, lbm)
 
+    mrt = None
+    if not args.no_mrt and rank == 0 and args.storage == "fp32":
+        mrt = run_mrt(args, torch, lbm, case, min(args.steps, 500))
+
     sixteen = None
     if not args.no_16bit and rank == 0:
         sixteen = run_16bit(args, torch, lbm, case, min(args.steps, 500))
@@ -405,6 +413,8 @@ def run_ours(args):
         }
         if e2e:
             line["e2e"] = e2e
+        if mrt:
+            line["mrt"] = mrt
         if sixteen:
             line["storage_16bit"] = sixteen
         if batched:
@@ -466,6 +476,54 @@ def end_to_end(args, case, torch, lbm):
             "final_sw": sw, "seconds": round(dt, 3),
             "note": "geometry set-up, phi0 upload, per-step S_w read-back "
                     "and the final phi download inside the timed region"}
+
+
+def run_mrt(args, torch, lbm, case, steps: int):
+    """The same rock and storage with the MRT collision (collision = 1):
+    throughput over `steps` steps, per-pass times, and the error against the
+    FP64 oracle's MRT after 10 steps from the initial state on the 32-plane
+    slab (max |f_gpu - f_oracle| / max |f_oracle| per colour)."""
+    from oracle import oracle as O
+    params = dict(case.params, collision=1)
+    slab = oracle_sample(case, 32)
+    o = O.Oracle(slab.lattice, slab.solid, slab.periodic)
+    o.set_params(**dict(slab.params, collision=1))
+    o.init_state(slab.phi0)
+    o.step(10)
+    ref = o.pops
+    fl = slab.solid == 0
+    t = lbm.Session(slab.lattice, slab.solid, slab.periodic, args.storage)
+    t.set_params(**dict(slab.params, collision=1))
+    t.init_state(slab.phi0.astype(np.float32))
+    t.step(10)
+    got = t.get_populations().cpu().numpy().astype(np.float64)
+    err = max(float(np.abs(got[c][:, fl] - ref[c][:, fl]).max()
+                    / np.abs(ref[c][:, fl]).max()) for c in range(2))
+    del t
+    s = lbm.Session(case.lattice, case.solid, case.periodic, args.storage)
+    s.set_params(**params)
+    s.init_state(case.phi0.astype(np.float32))
+    stream = torch.cuda.current_stream()
+    s.step(args.warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    k2 = min(steps, 100)
+    pm = s.step_timed(k2)
+    out = {"collision": "MRT, rates of Eqs. 4, 15-16",
+           "value": round(s.n_fluid / (ms * 1e-3) / 1e6, 2), "unit": "MLUPS",
+           "ms_per_step": round(ms, 4),
+           "pass_ms_per_step": {k: round(v / k2, 5) for k, v in pm.items()},
+           "error_vs_fp64_oracle": err,
+           "error_sample": "32-plane slab of the rock, 10 steps from the "
+                           "initial state, max relative population error"}
+    del s
+    return out
 
 
 def run_16bit(args, torch, lbm, case, steps: int):

@@ -9,8 +9,9 @@
  * or a uniform body force (Type-II, Eq. 36); phase field (Eq. 7), colour
  * gradient (Eq. 6), wetting by Scheme-I (Eqs. 28-31) or Scheme-II (Eqs.
  * 32-33) with the extrapolations of Eqs. 34-35, curvature (Eq. 12), CSF force
- * (Eq. 5), the single-rate (BGK) form of the collision of Eq. 2 with the
- * viscosity of Eqs. 13-14, and recolouring (Eqs. 20-21).
+ * (Eq. 5), the collision of Eq. 2 in its single-rate (BGK) form or with the
+ * MRT rates of Eqs. 4, 15-16, the viscosity of Eqs. 13-14, and recolouring
+ * (Eqs. 20-21).
  *
  * Conventions shared by every call:
  *  - Layout. A field over the box has N = nx*ny*nz entries, node
@@ -296,8 +297,9 @@ void lbm_batch_destroy(lbm_batch b);
  * contact angle theta (radians) and the body acceleration g (Eq. 36).
  * The state of a fluid node is (f''_i, r = rho^r/rho, v) with the red part
  * of population i equal to r f''_i + w_i e_i.v (Eqs. 20-21); the adjoint
- * state has the same shape. Scope: float32 storage, no wetting or Scheme-II
- * (Eqs. 32-33), no Zou-He ends (periodic axes or bounce-back walls);
+ * state has the same shape. Scope: float32 storage, the single-rate
+ * collision (collision = 0), no wetting or Scheme-II (Eqs. 32-33), no
+ * Zou-He ends (periodic axes or bounce-back walls);
  * lbm_adj_create() rejects anything else with LBM_ERR_ARG. All arithmetic
  * is float32; the parameter gradients accumulate in float64.
  *

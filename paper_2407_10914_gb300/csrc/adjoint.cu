@@ -23,9 +23,10 @@
 //   A5 the phase field (Eq. 7) and the colour densities per node;
 //   A6 streaming (Eq. 1) transposed: every (node, direction) of x_t sends
 //      its population to exactly one place, so this is a gather.
-// The adjoint covers float32 storage, no wetting or Scheme-II, and ends
-// without Zou-He planes (periodic axes or bounce-back walls); Scheme-I's
-// secant iterations and App. B are not differentiated here.
+// The adjoint covers float32 storage, the single-rate collision, no wetting
+// or Scheme-II, and ends without Zou-He planes (periodic axes or bounce-back
+// walls); Scheme-I's secant iterations, App. B and the MRT rates are not
+// differentiated here.
 //
 // Regularised linearisation. Where n_c is almost along n_w, Scheme-II's
 // result direction around n_w is undefined and its derivative grows as
@@ -548,7 +549,7 @@ lbm_status lbm_adj_create(lbm_adj *out, lbm_handle h, void *dev_workspace,
   if (((uintptr_t)dev_workspace) % 256) return LBM_ERR_ARG;
   if (h->storage != LBM_STORAGE_FP32) return LBM_ERR_ARG;
   if (!h->params_set) return LBM_ERR_STATE;
-  if (h->p.zou_he || h->p.wetting == 1) return LBM_ERR_ARG;
+  if (h->p.zou_he || h->p.wetting == 1 || h->p.collision) return LBM_ERR_ARG;
   const AdjLayout L = adj_layout(h->Q, h->d.NFp, h->d.NS);
   if (ws_bytes < L.total) return LBM_ERR_NOMEM;
   lbm_adj a = new (std::nothrow) lbm_adj_s();
@@ -580,7 +581,8 @@ lbm_status lbm_adj_seed_sw(lbm_adj a, void *stream) {
   if (!a) return LBM_ERR_ARG;
   lbm_ctx *c = a->c;
   if (!c->state_set) return afail(a, LBM_ERR_STATE, "the handle has no state");
-  if (c->p.zou_he || c->p.wetting == 1 || c->storage != LBM_STORAGE_FP32)
+  if (c->p.zou_he || c->p.wetting == 1 || c->p.collision ||
+      c->storage != LBM_STORAGE_FP32)
     return afail(a, LBM_ERR_ARG, "parameters outside the adjoint's scope");
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaMemsetAsync(a->a.acc, 0, 8 * sizeof(double), s);
@@ -599,7 +601,8 @@ lbm_status lbm_adj_step(lbm_adj a, void *stream) {
   if (!a) return LBM_ERR_ARG;
   if (!a->seeded) return afail(a, LBM_ERR_STATE, "seed the adjoint first");
   lbm_ctx *c = a->c;
-  if (c->p.zou_he || c->p.wetting == 1 || c->storage != LBM_STORAGE_FP32)
+  if (c->p.zou_he || c->p.wetting == 1 || c->p.collision ||
+      c->storage != LBM_STORAGE_FP32)
     return afail(a, LBM_ERR_ARG, "parameters outside the adjoint's scope");
   cudaStream_t s = (cudaStream_t)stream;
   lbm::launch_fields(c->Q, c->storage, c->d, s);

@@ -386,6 +386,41 @@ __device__ __forceinline__ void collide(const StepConst &c, float *ft,
     b[a] = S * (j[a] - c.rho0 * u[a] + 0.5f * F[a]) * (1.f / Lattice<Q>::E2);
   const float kf = 1.f - 0.5f * S;
   const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+  // MRT (D3Q19): Eq. (2) with the rates of Eq. (4), S_e = S_eps = S_pi =
+  // S_nu (Eq. 15) and S_q = S_m from Eq. (16). It differs from the
+  // single-rate form only in the rows of q (4, 6, 8) and m (16-18) of M
+  // (Eq. A.3), which relax at S_q instead of S_nu. The rows of M are
+  // orthogonal, so M^-1 = M^T diag(1/|row_k|^2), and the difference is
+  //   f''_i += sum_k M_ki dm_k / |row_k|^2,
+  //   dm_k = -(S_q - S_nu) (m_k - m_k^eq + h_k / 2)
+  // with m^eq_q = -2/3 rho0 u, h_q = -2/3 F (A.4, A.5), m^eq_m = h_m = 0,
+  // |row_q|^2 = 40 and |row_m|^2 = 8.
+  float aq[3] = {0.f, 0.f, 0.f}, am[3] = {0.f, 0.f, 0.f};
+  if constexpr (Q == 19) {
+    if (c.mrt) {
+      float q[3] = {0.f, 0.f, 0.f}, m[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
+        const int ex = Lattice<Q>::ex(i), ey = Lattice<Q>::ey(i),
+                  ez = Lattice<Q>::ez(i);
+        const float c5 = (float)(5 * (ex * ex + ey * ey + ez * ez) - 9);
+        q[0] += c5 * (float)ex * ft[i];
+        q[1] += c5 * (float)ey * ft[i];
+        q[2] += c5 * (float)ez * ft[i];
+        m[0] += (float)(ex * (ey * ey - ez * ez)) * ft[i];
+        m[1] += (float)(ey * (ez * ez - ex * ex)) * ft[i];
+        m[2] += (float)(ez * (ex * ex - ey * ey)) * ft[i];
+      }
+      const float Sq = 8.f * (2.f - S) / (8.f - S);  // Eq. (16)
+      const float dS = Sq - S;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        aq[a] = -dS * (q[a] + (2.f / 3.f) * c.rho0 * u[a] - (1.f / 3.f) * F[a]) *
+                (1.f / 40.f);
+        am[a] = -dS * m[a] * (1.f / 8.f);
+      }
+    }
+  }
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const float ex = (float)Lattice<Q>::ex(i), ey = (float)Lattice<Q>::ey(i),
@@ -397,6 +432,17 @@ __device__ __forceinline__ void collide(const StepConst &c, float *ft,
     const float guo = w * (3.f * (eF - uF) + 9.f * eu * eF);
     ft[i] = ft[i] - S * (ft[i] - feq) + kf * guo +
             (ex * b[0] + ey * b[1] + ez * b[2]);
+    if constexpr (Q == 19) {
+      if (c.mrt && i > 0) {
+        const int ix = Lattice<Q>::ex(i), iy = Lattice<Q>::ey(i),
+                  iz = Lattice<Q>::ez(i);
+        const float c5 = (float)(5 * (ix * ix + iy * iy + iz * iz) - 9);
+        ft[i] += c5 * (ex * aq[0] + ey * aq[1] + ez * aq[2]) +
+                 (float)(ix * (iy * iy - iz * iz)) * am[0] +
+                 (float)(iy * (iz * iz - ix * ix)) * am[1] +
+                 (float)(iz * (ix * ix - iy * iy)) * am[2];
+      }
+    }
   }
 }
 
