@@ -165,8 +165,13 @@ static void scan_exclusive(const int *in, int *out, long long n, int *bsum,
 }
 
 // One block per tile: rank of each node among the nodes of its kind in the
-// tile, in the tile's (z, y, x) order; map = (class << 14) | rank; the F and
-// S lists hold box indices.
+// tile; map = (class << 14) | rank; the F and S lists hold box indices.
+// Fluid nodes on the two x faces of the box (x = 0, x = nx - 1) come first
+// in their tile, then the tile's other fluid nodes in (z, y, x) order;
+// solid-boundary nodes in (z, y, x) order. With the x faces leading, the
+// Zou-He planes of an x-axis flow are runs of consecutive F indices (the
+// fix-up pass reads and writes them coalesced) instead of nodes a tile row
+// apart; for every other node the order is the plain tile order.
 template <int Q>
 __global__ void k_tile_map(Dom d, uint16_t *__restrict__ map,
                            int *__restrict__ fg, int *__restrict__ sg) {
@@ -184,45 +189,54 @@ __global__ void k_tile_map(Dom d, uint16_t *__restrict__ map,
     carry_s = 0;
   }
   __syncthreads();
-  for (int c0 = 0; c0 < G::TN; c0 += GBLOCK) {
-    const int lp = c0 + threadIdx.x;
-    int x, y, z, p0;
-    local_node<Q>(lp, X0, Y0, Z0, x, y, z, p0);
-    const bool valid = x < d.nx && y < d.ny && z < d.nz;
-    const int g = valid ? x + d.nx * (y + d.ny * z) : 0;
-    const int c = valid ? d.cls[g] : CLS_SOLID;
-    const bool isf = valid && (c & 2), iss = valid && c == CLS_SOLID_BND;
-    const unsigned bf = __ballot_sync(0xffffffffu, isf);
-    const unsigned bs = __ballot_sync(0xffffffffu, iss);
-    if (lane == 0) {
-      wf[warp] = __popc(bf);
-      ws[warp] = __popc(bs);
-    }
-    __syncthreads();
-    int of = carry_f, os = carry_s;
-    for (int w = 0; w < warp; ++w) {
-      of += wf[w];
-      os += ws[w];
-    }
-    if (valid) {
-      int rank = 0;
-      if (isf) {
-        rank = of + __popc(bf & lt);
-        fg[d.fbase[t] + rank] = g;
-      } else if (iss) {
-        rank = os + __popc(bs & lt);
-        sg[d.sbase[t] + rank] = g;
+  // pass 0: the x-face fluid nodes (tiles on an x face only); pass 1: the rest
+  const bool face_tile = X0 == 0 || X0 + G::TX >= d.nx;
+  for (int pass = face_tile ? 0 : 1; pass < 2; ++pass) {
+    for (int c0 = 0; c0 < G::TN; c0 += GBLOCK) {
+      const int lp = c0 + threadIdx.x;
+      int x, y, z, p0;
+      local_node<Q>(lp, X0, Y0, Z0, x, y, z, p0);
+      const bool valid = x < d.nx && y < d.ny && z < d.nz;
+      const int g = valid ? x + d.nx * (y + d.ny * z) : 0;
+      const int c = valid ? d.cls[g] : CLS_SOLID;
+      const bool face = x == 0 || x == d.nx - 1;
+      const bool fluid = valid && (c & 2);
+      const bool isf = fluid && (pass == 0 ? face : !(face && face_tile));
+      const bool iss = pass == 1 && valid && c == CLS_SOLID_BND;
+      const unsigned bf = __ballot_sync(0xffffffffu, isf);
+      const unsigned bs = __ballot_sync(0xffffffffu, iss);
+      if (lane == 0) {
+        wf[warp] = __popc(bf);
+        ws[warp] = __popc(bs);
       }
-      map[g] = (uint16_t)((c << 14) | rank);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int w = 0; w < GBLOCK / 32; ++w) {
-        carry_f += wf[w];
-        carry_s += ws[w];
+      __syncthreads();
+      int of = carry_f, os = carry_s;
+      for (int w = 0; w < warp; ++w) {
+        of += wf[w];
+        os += ws[w];
       }
+      // the node's map entry is written in the pass that ranks it (every
+      // node that is not fluid in pass 1)
+      if (valid && (isf || (pass == 1 && !fluid))) {
+        int rank = 0;
+        if (isf) {
+          rank = of + __popc(bf & lt);
+          fg[d.fbase[t] + rank] = g;
+        } else if (iss) {
+          rank = os + __popc(bs & lt);
+          sg[d.sbase[t] + rank] = g;
+        }
+        map[g] = (uint16_t)((c << 14) | rank);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int w = 0; w < GBLOCK / 32; ++w) {
+          carry_f += wf[w];
+          carry_s += ws[w];
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
 }
 

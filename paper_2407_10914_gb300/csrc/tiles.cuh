@@ -2,7 +2,8 @@
 //
 // The box is cut into tiles of TX x TY x TZ nodes (32 x 8 x 8 for D3Q19,
 // 64 x 32 x 1 for D2Q9). Fluid nodes are numbered tile by tile (F-space),
-// and within a tile in (z, y, x) order; solid-boundary nodes likewise
+// and within a tile the fluid nodes on the box's x faces first, then the
+// others in (z, y, x) order; solid-boundary nodes in (z, y, x) order
 // (S-space). The uint16 map over the box holds a node's class (bits 14-15)
 // and its rank among the nodes of its kind in its tile (bits 0-13); with the
 // per-tile bases fbase/sbase this gives its F- or S-index.
