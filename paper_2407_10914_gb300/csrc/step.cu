@@ -20,8 +20,13 @@ namespace lbm {
 
 constexpr int BLOCK = 256;
 
+// Blocks per SM, measured on the 256^3 rock: the gather passes are bound by
+// load latency, so the stream and gradient passes run with 32 registers
+// (7-8 resident blocks of 256 threads; the gradient pass gains 14 % over its
+// unbounded 34 registers, the stream pass 4 % over 40), the collision with
+// 64 (4 blocks; 3 or 5 blocks are 7 % and 20 % slower).
 template <int Q, int ST>
-__global__ void __launch_bounds__(BLOCK) k_stream(Dom d) {
+__global__ void __launch_bounds__(BLOCK, 7) k_stream(Dom d) {
   const int k = blockIdx.x * BLOCK + threadIdx.x;
   if (k < d.NF) stream_node<Q, ST, false>(d, k);
 }
@@ -39,7 +44,7 @@ __global__ void __launch_bounds__(BLOCK) k_phi_solid(Dom d) {
 }
 
 template <int Q>
-__global__ void __launch_bounds__(BLOCK) k_gradient(Dom d) {
+__global__ void __launch_bounds__(BLOCK, 8) k_gradient(Dom d) {
   const int k = blockIdx.x * BLOCK + threadIdx.x;
   if (k < d.NF) gradient_node<Q, false>(d, k);
 }
