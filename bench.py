@@ -205,7 +205,7 @@ def measured_peaks():
 def kernel_source_hash():
     h = hashlib.sha1()
     for f in ("step.cu", "passes.cuh", "tiles.cuh", "stencil.cuh",
-              "lattice.cuh", "context.hpp"):
+              "lattice.cuh", "context.hpp", "geometry.cu"):
         h.update(open(os.path.join(ROOT, "paper_2407_10914_gb300", "csrc", f),
                       "rb").read())
     return h.hexdigest()[:12]
