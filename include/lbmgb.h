@@ -171,6 +171,16 @@ lbm_status lbm_get_populations(lbm_handle h, float *dst_dev, void *stream);
 lbm_status lbm_set_populations(lbm_handle h, const float *src_dev,
                                void *stream);
 
+/* Replace the injected fluid (Sec. II.D.1, Eqs. 37-38): at every fluid node
+ * of the inlet plane (coordinate 0 of flow_axis) the stored populations of
+ * the other colour are added to colour `colour` (0 = r, 1 = b) and set to
+ * zero, f^s_i += f^sbar_i, f^sbar_i = 0, so those nodes hold pure fluid s.
+ * For sequential injection of different fluids (e.g. forced imbibition
+ * after drainage); set the matching zeta_r with lbm_set_params() as well.
+ * Needs a state and zou_he = 1 (LBM_ERR_STATE), colour 0 or 1
+ * (LBM_ERR_ARG). Asynchronous. */
+lbm_status lbm_swap_inlet(lbm_handle h, int colour, void *stream);
+
 /* Node classes (uint8 [N], LBM_CLS_*) and wall normals (float32 [3][N],
  * zero away from fluid-boundary nodes) into caller device buffers. */
 lbm_status lbm_get_geometry(lbm_handle h, uint8_t *cls_dev, float *nw_dev,

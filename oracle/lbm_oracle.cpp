@@ -1041,6 +1041,34 @@ void orc_step(void *h, int nsteps) {
   for (int s = 0; s < nsteps; ++s) o->step();
 }
 
+// Sec. II.D.1, Eqs. (37)-(38): the injected fluid is replaced by colour
+// `colour` (0 = r, 1 = b) at every fluid node of the inlet plane (coordinate
+// 0 of the flow axis): f^s_i += f^sbar_i, f^sbar_i = 0 for every i. The
+// stored populations change; the caller sets the new zeta^s of Eq. (B.1).
+// Returns the number of nodes changed, or -1 for a colour other than 0/1.
+long orc_swap_inlet(void *h, int colour) {
+  Oracle *o = static_cast<Oracle *>(h);
+  if (colour != 0 && colour != 1) return -1;
+  const int a = o->p.flow_axis;
+  const long N = o->N;
+  const int Q = o->L.Q;
+  long changed = 0;
+  for (long n = 0; n < N; ++n) {
+    if (o->solid[n]) continue;
+    int c[3];
+    o->coords(n, c);
+    if (c[a] != 0) continue;
+    for (int i = 0; i < Q; ++i) {
+      double &fs = o->f[((long)colour * Q + i) * N + n];
+      double &fo = o->f[((long)(1 - colour) * Q + i) * N + n];
+      fs = fs + fo;  // Eq. (37)
+      fo = 0.0;      // Eq. (38)
+    }
+    ++changed;
+  }
+  return changed;
+}
+
 // The first half of a step only: streaming with bounce-back, the macros
 // and, when enabled, Zou-He; the streamed (and rebuilt) populations go to
 // dst (2QN). The stored state is not changed.

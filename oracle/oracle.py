@@ -67,6 +67,8 @@ def lib():
         L.orc_set_pops.argtypes = [C.c_void_p, C.c_void_p]
         L.orc_get_pops.argtypes = [C.c_void_p, C.c_void_p]
         L.orc_step.argtypes = [C.c_void_p, C.c_int]
+        L.orc_swap_inlet.argtypes = [C.c_void_p, C.c_int]
+        L.orc_swap_inlet.restype = C.c_long
         L.orc_stream_only.argtypes = [C.c_void_p, C.c_void_p]
         L.orc_geometry.argtypes = [C.c_void_p] + [C.c_void_p] * 3
         L.orc_fields.argtypes = [C.c_void_p] + [C.c_void_p] * 6
@@ -224,6 +226,15 @@ class Oracle:
 
     def step(self, n: int = 1):
         lib().orc_step(self._h, int(n))
+
+    def swap_inlet(self, colour: int) -> int:
+        """Eqs. (37)-(38) on the inlet plane of the flow axis: the nodes
+        become pure colour `colour` (0 = r, 1 = b). Returns the number of
+        nodes changed."""
+        n = lib().orc_swap_inlet(self._h, int(colour))
+        if n < 0:
+            raise ValueError("colour must be 0 (r) or 1 (b)")
+        return int(n)
 
     def stream_only(self) -> np.ndarray:
         """Streamed (and Zou-He rebuilt) populations of the next step,

@@ -415,6 +415,20 @@ lbm_status lbm_set_populations(lbm_handle c, const float *src, void *stream) {
   return LBM_OK;
 }
 
+lbm_status lbm_swap_inlet(lbm_handle c, int colour, void *stream) {
+  if (!c) return LBM_ERR_ARG;
+  if (colour != 0 && colour != 1)
+    return fail(c, LBM_ERR_ARG, "colour must be 0 (r) or 1 (b)");
+  if (!c->state_set) return fail(c, LBM_ERR_STATE, "init the state first");
+  if (!c->p.zou_he)
+    return fail(c, LBM_ERR_STATE, "the inlet plane is a Zou-He plane: zou_he = 1");
+  lbm::launch_swap_inlet(c->d, colour == 1, (cudaStream_t)stream);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(c, e, "swap_inlet");
+  ++c->gen;
+  return LBM_OK;
+}
+
 lbm_status lbm_get_geometry(lbm_handle c, uint8_t *cls, float *nw,
                             void *stream) {
   if (!c) return LBM_ERR_ARG;

@@ -507,6 +507,25 @@ cudaError_t build_geometry(lbm_ctx *c, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// ------------------------------------------------ injected-fluid swap
+// Sec. II.D.1, Eqs. (37)-(38) on the stored state: at every fluid node of
+// the inlet plane (coordinate 0 of the flow axis, first half of the Zou-He
+// list) the populations of the other colour join colour `blue ? b : r`:
+// f^s_i += f^sbar_i, f^sbar_i = 0. In the stored form (f''_i, q, v) that is
+// f''_i unchanged, the minority fraction q = 0 with colour s the majority,
+// and v = 0 (the minority part of every population is zero).
+__global__ void k_swap_inlet(Dom d, bool blue) {
+  const int j = blockIdx.x * GBLOCK + threadIdx.x;
+  if (j >= d.n_zh) return;
+  const int k = d.zh_list[j];
+  if (!(d.fflag[k] & (2u << (2 * d.c.axis)))) return;  // outlet node
+  const_cast<float4 *>(d.S_src)[k] = make_float4(m_pack(blue, 0.f), 0.f, 0.f, 0.f);
+}
+
+void launch_swap_inlet(const Dom &d, bool blue, cudaStream_t s) {
+  if (d.n_zh > 0) k_swap_inlet<<<gblocks(d.n_zh), GBLOCK, 0, s>>>(d, blue);
+}
+
 // ------------------------------------------------------------ state I/O
 // Fluid at rest: f^s_i = w_i rho^s, i.e. f''_i = w_i rho0, q from phi0, v = 0.
 template <int Q, int ST>

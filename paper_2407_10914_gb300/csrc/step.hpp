@@ -32,6 +32,10 @@ cudaError_t build_geometry(lbm_ctx *c, cudaStream_t s);
 void launch_init_state(int Q, int storage, const Dom &d, const float *phi0,
                        cudaStream_t s);
 
+// Eqs. (37)-(38) at the inlet plane's fluid nodes: the stored state becomes
+// pure colour b (blue) or r (geometry.cu).
+void launch_swap_inlet(const Dom &d, bool blue, cudaStream_t s);
+
 // Dense float32 export/import of the stored populations (geometry.cu).
 void launch_export_pops(int Q, int storage, const Dom &d, float *dst,
                         cudaStream_t s);

@@ -30,7 +30,8 @@ STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 EXPORTS = ("lbm_workspace_bytes", "lbm_init_geometry", "lbm_set_params",
            "lbm_init_state", "lbm_step", "lbm_step_timed", "lbm_macros",
            "lbm_reduce",
-           "lbm_get_populations", "lbm_set_populations", "lbm_get_geometry",
+           "lbm_get_populations", "lbm_set_populations", "lbm_swap_inlet",
+           "lbm_get_geometry",
            "lbm_counts", "lbm_colour_mass_noalloc", "lbm_last_error",
            "lbm_destroy",
            "lbm_batch_workspace_bytes", "lbm_batch_create",
@@ -95,6 +96,8 @@ def load_library(path: str = LIB_PATH):
     L.lbm_get_populations.argtypes = [vp, vp, vp]
     L.lbm_set_populations.restype = C.c_int
     L.lbm_set_populations.argtypes = [vp, vp, vp]
+    L.lbm_swap_inlet.restype = C.c_int
+    L.lbm_swap_inlet.argtypes = [vp, C.c_int, vp]
     L.lbm_get_geometry.restype = C.c_int
     L.lbm_get_geometry.argtypes = [vp, vp, vp, vp]
     L.lbm_counts.restype = C.c_int
@@ -256,6 +259,11 @@ def lbm_set_populations(h, src, stream):
            "lbm_set_populations")
 
 
+def lbm_swap_inlet(h, colour: int, stream):
+    _check(load_library().lbm_swap_inlet(h, int(colour), stream), h,
+           "lbm_swap_inlet")
+
+
 def lbm_get_geometry(h, cls, nw, stream):
     p = [None if t is None else _dptr(t) for t in (cls, nw)]
     _check(load_library().lbm_get_geometry(h, *p, stream), h,
@@ -376,6 +384,11 @@ class Session:
         src = t.as_tensor(f).to(self.device, t.float32).contiguous()
         assert src.numel() == 2 * self.q * self.N
         lbm_set_populations(self.h, src, self.stream())
+
+    def swap_inlet(self, colour: int):
+        """Eqs. (37)-(38): the inlet plane's nodes become pure colour
+        `colour` (0 = r, 1 = b)."""
+        lbm_swap_inlet(self.h, colour, self.stream())
 
     def geometry(self):
         t = self.torch
