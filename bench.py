@@ -16,6 +16,9 @@ One JSON line on rank 0:
   step_bandwidth  the step-level accounting of 308 B per fluid-node update
              (2 x 2Q populations of 4 B plus a 4 B link mask);
   cpu_baseline  the FP64 oracle on a bounded slab of the same rock;
+  washburn   Washburn Case-I (Sec. IV.A.1): spontaneous imbibition in the
+             12x12x101 tube at 30-75 deg with both wetting schemes, the
+             paper's area error against Eq. (49) for each;
   mrt        the same rock with the MRT collision (Eq. 2 with the rates of
              Eqs. 4, 15-16), with its error against the FP64 oracle's MRT;
   storage_16bit the same rock with FP16 / BF16 population storage, each
@@ -95,6 +98,8 @@ def parse():
                     help="skip the 96-drop batched sweep object")
     ap.add_argument("--batched-cases", type=int, default=96)
     ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--no-washburn", action="store_true",
+                    help="skip the Washburn Case-I object")
     ap.add_argument("--no-mrt", action="store_true",
                     help="skip the MRT-collision object")
     ap.add_argument("--no-16bit", action="store_true",
@@ -353,6 +358,10 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = end_to_end(args, case, torch, lbm)
 
+    washburn = None
+    if not args.no_washburn and rank == 0:
+        washburn = run_washburn(lbm)
+
     mrt = None
     if not args.no_mrt and rank == 0 and args.storage == "fp32":
         mrt = run_mrt(args, torch, lbm, case, min(args.steps, 500))
@@ -413,6 +422,8 @@ def run_ours(args):
         }
         if e2e:
             line["e2e"] = e2e
+        if washburn:
+            line["washburn"] = washburn
         if mrt:
             line["mrt"] = mrt
         if sixteen:
@@ -476,6 +487,39 @@ def end_to_end(args, case, torch, lbm):
             "final_sw": sw, "seconds": round(dt, 3),
             "note": "geometry set-up, phi0 upload, per-step S_w read-back "
                     "and the final phi download inside the timed region"}
+
+
+def run_washburn(lbm):
+    """Washburn Case-I on the paper's tube: for each contact angle and
+    wetting scheme the area error (%) of the interface path against Eq.
+    (49) from t*_init (Eq. 49 at the settled initial interface) to t* = 60,
+    and the interface position at the end beside Eq. (49)'s."""
+    from paper_2407_10914_gb300 import washburn as Wb
+    from paper_2407_10914_gb300 import workloads as W
+    t0 = time.time()
+    out = {"workload": "washburn_tube_12x12x101_r5", "viscosity_ratio": 0.2,
+           "gamma_lbm": 1.0 / 45.0, "tstar_end": 60.0, "runs": []}
+    for wetting in (1, 2):
+        for theta in (30.0, 45.0, 60.0, 75.0):
+            case = W.washburn_tube(theta, wetting)
+
+            def make(params, case=case):
+                s = lbm.Session(19, case.solid, case.periodic)
+                s.set_params(**params)
+                s.init_state(case.phi0.astype(np.float32))
+                return s
+
+            r = Wb.run_case1(make, case, theta, wetting, tstar_end=60.0)
+            out["runs"].append({
+                "scheme": "I" if wetting == 1 else "II", "theta_deg": theta,
+                "area_error_pct": round(100 * r["area_error"], 3),
+                "zstar_init": round(r["z_init"], 4),
+                "tstar_init": round(r["tstar_init"], 3),
+                "zstar_end": round(float(r["zstar"][-1]), 4),
+                "zstar_end_eq49": round(float(r["zstar_eq49"][-1]), 4),
+                "tstar_end": round(float(r["tstar"][-1]), 2)})
+    out["seconds"] = round(time.time() - t0, 1)
+    return out
 
 
 def run_mrt(args, torch, lbm, case, steps: int):

@@ -176,6 +176,28 @@ def tube_3d(nx=256, ny=20, nz=20, radius=8.0, red_len=32, theta_deg=90.0,
                 phi0, p, steps, dict(radius=radius, red_len=red_len))
 
 
+def washburn_tube(theta_deg=60.0, wetting=1, nx=101, ny=12, nz=12,
+                  radius=5.0, tau_w=1.0, tau_nw=0.6, gamma=1.0 / 45.0,
+                  beta=0.95, rho=1.0, b_layers=1) -> Case:
+    """Spontaneous imbibition in a capillary tube (Sec. IV.A, Case-I): the
+    paper's 12 x 12 x 101 tube of radius 5 along x, the wetting fluid b
+    (tau^b = 1.0) in the first ``b_layers`` layers, the non-wetting fluid r
+    (tau^r = 0.6, viscosity ratio 1/5) in the rest, equal Zou-He densities
+    at both ends (Delta P = 0) with b injected (zeta^r = 0), and the lattice
+    tension 1/45 of the paper's unit system (0.02 N/m at a_o = 1e-6 m)."""
+    c = tube_3d(nx=nx, ny=ny, nz=nz, radius=radius, red_len=0,
+                theta_deg=theta_deg, wetting=wetting, rho_in=rho, rho_out=rho,
+                tau=1.0, gamma=gamma, beta=beta)
+    x = np.arange(nx)[None, None, :]
+    phi0 = np.where(np.broadcast_to(x < b_layers, c.solid.shape), -1.0, 1.0)
+    phi0 = np.ascontiguousarray(phi0)
+    phi0[c.solid == 1] = 0.0
+    p = dict(c.params, tau_r=tau_nw, tau_b=tau_w, zeta_r=0.0)
+    return Case(f"washburn_{nx}x{ny}x{nz}_r{radius:g}_th{theta_deg:g}", 19,
+                c.solid, c.periodic, phi0, p, 0,
+                dict(radius=radius, length=nx - 1))
+
+
 # ------------------------------------------------------------ porous rock
 def sphere_pack(n=(256, 256, 256), porosity=0.22, rmin=4.0, rmax=10.0,
                 seed=240710914, reservoir=10, side_walls=True,

@@ -1,25 +1,29 @@
 """Physical-unit conversion (Sec. II.E, Eqs. 40-44) against the worked
-example the paper prints in Sec. IV.B (tests/golden/units_sec4b.txt)."""
+examples the paper prints in Sec. IV.B and IV.A
+(tests/golden/units_sec4b.txt, units_sec4a.txt)."""
 import os
 
 import pytest
 
 from paper_2407_10914_gb300 import units as U
 
-GOLD = os.path.join(os.path.dirname(__file__), "golden", "units_sec4b.txt")
+HERE = os.path.join(os.path.dirname(__file__), "golden")
 
 
-def golden():
+def golden(name="units_sec4b.txt"):
     out = {}
-    for line in open(GOLD):
+    for line in open(os.path.join(HERE, name)):
         if line.strip() and not line.startswith("#"):
             k, v = line.split()
             out[k] = float(v)
     return out
 
 
-def test_paper_worked_example():
-    g = golden()
+@pytest.mark.parametrize("name", ["units_sec4b.txt", "units_sec4a.txt"])
+def test_paper_worked_example(name):
+    """Both worked examples of the paper: the SCAL drainage set-up of Sec.
+    IV.B and the capillary tube of Sec. IV.A."""
+    g = golden(name)
     r = U.Units.from_tau(g["a0"], g["rho_phys"], g["nu_phys_r"], g["tau_r"],
                          g["rho_lbm"])
     b = U.Units.from_tau(g["a0"], g["rho_phys"], g["nu_phys_b"], g["tau_b"],
