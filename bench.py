@@ -16,6 +16,9 @@ One JSON line on rank 0:
   step_bandwidth  the step-level accounting of 308 B per fluid-node update
              (2 x 2Q populations of 4 B plus a 4 B link mask);
   cpu_baseline  the FP64 oracle on a bounded slab of the same rock;
+  laplace    the Laplace test of Sec. III.A at the paper's 128^3 scale: the
+             interfacial tension from five drops in N/m beside the 0.02 N/m
+             input and the paper's 0.02009;
   washburn   Washburn Case-I (Sec. IV.A.1): spontaneous imbibition in the
              12x12x101 tube at 30-75 deg with both wetting schemes, the
              paper's area error against Eq. (49) for each;
@@ -98,6 +101,8 @@ def parse():
                     help="skip the 96-drop batched sweep object")
     ap.add_argument("--batched-cases", type=int, default=96)
     ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--no-laplace", action="store_true",
+                    help="skip the Laplace-law object")
     ap.add_argument("--no-washburn", action="store_true",
                     help="skip the Washburn Case-I object")
     ap.add_argument("--no-mrt", action="store_true",
@@ -358,6 +363,10 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = end_to_end(args, case, torch, lbm)
 
+    laplace = None
+    if not args.no_laplace and rank == 0:
+        laplace = run_laplace(lbm)
+
     washburn = None
     if not args.no_washburn and rank == 0:
         washburn = run_washburn(lbm)
@@ -422,6 +431,8 @@ def run_ours(args):
         }
         if e2e:
             line["e2e"] = e2e
+        if laplace:
+            line["laplace"] = laplace
         if washburn:
             line["washburn"] = washburn
         if mrt:
@@ -487,6 +498,34 @@ def end_to_end(args, case, torch, lbm):
             "final_sw": sw, "seconds": round(dt, 3),
             "note": "geometry set-up, phi0 upload, per-step S_w read-back "
                     "and the final phi download inside the timed region"}
+
+
+def run_laplace(lbm):
+    """Sec. III.A at the paper's scale: five drops (R = 12-30) in a periodic
+    128^3 box, 12000 steps each, the jump averaged over the second half;
+    the slope of dP against 2/R in N/m (Eqs. 43-44, the paper's units)."""
+    from paper_2407_10914_gb300 import laplace as Lp
+    t0 = time.time()
+
+    def make(case):
+        s = lbm.Session(19, case.solid, case.periodic)
+        s.set_params(**case.params)
+        s.init_state(case.phi0.astype(np.float32))
+        return s
+
+    out = {"workload": "laplace_128cubed_5drops", "steps_per_drop": 12000,
+           "gamma_input_n_per_m": 0.02, "paper_gamma_sim_n_per_m": 0.02009,
+           "paper_error_pct": 0.45,
+           "paper_context": "MRT, RTX 3090, FP32 (Sec. III.A)"}
+    for coll, key in ((0, "single_rate"), (1, "mrt")):
+        r = Lp.sweep(make, 128, (12.0, 16.0, 20.0, 24.0, 30.0), steps=12000,
+                     collision=coll)
+        out[key] = {"radii": [round(x, 3) for x in r["radii"]],
+                    "dp_pa": [round(x, 2) for x in r["dp_phys"]],
+                    "gamma_sim_n_per_m": round(r["gamma_phys_sim"], 6),
+                    "error_pct": round(100 * r["error"], 3)}
+    out["seconds"] = round(time.time() - t0, 1)
+    return out
 
 
 def run_washburn(lbm):

@@ -100,3 +100,31 @@ def area_error(z_sim, z_ref, t) -> float:
     a_sim = np.trapezoid(z_sim, t)
     a_ref = np.trapezoid(z_ref, t)
     return abs(a_sim - a_ref) / a_ref
+
+
+def laplace_measure(rho: np.ndarray, phi: np.ndarray, inner: float = 0.5,
+                    gap: float = 5.0):
+    """Pressure jump and radius of a red drop centred in a periodic box
+    (Sec. III.A). R is the radius of the sphere (disc in 2-D, shape
+    (1, ny, nx)) with the drop's red volume sum (1 + phi)/2; the pressures
+    p = rho/3 are averaged inside r < inner R and outside r > R + gap, r
+    measured from the box centre. Returns (dP, R)."""
+    two_d = phi.shape[0] == 1
+    red = ((1.0 + phi) / 2.0).sum()
+    R = math.sqrt(red / math.pi) if two_d else (3 * red / (4 * math.pi)) ** (1 / 3)
+    nz, ny, nx = phi.shape
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx].astype(np.float64)
+    r2 = (x - (nx - 1) / 2.0) ** 2 + (y - (ny - 1) / 2.0) ** 2
+    if not two_d:
+        r2 = r2 + (z - (nz - 1) / 2.0) ** 2
+    r = np.sqrt(r2)
+    dp = (rho[r < inner * R].mean() - rho[r > R + gap].mean()) / 3.0
+    return float(dp), float(R)
+
+
+def laplace_slope(dps, radii, dims: int = 3) -> float:
+    """Least-squares slope through the origin of dP against (dims - 1)/R:
+    the interfacial tension of Laplace's law dP = (dims - 1) gamma / R."""
+    xs = (dims - 1) / np.asarray(radii, np.float64)
+    ys = np.asarray(dps, np.float64)
+    return float((xs * ys).sum() / (xs * xs).sum())
