@@ -248,7 +248,7 @@ __device__ __forceinline__ float curvature(const Dom &d, int k, float4 &c4) {
 // state of fluid node k: f''_i and (q, v) with q the encoded rho^r/rho and
 // v = beta rho^r rho^b / rho n (Eqs. 20-21). The relaxation rate follows
 // the node's phase field (Eq. 39's value on the outlet plane).
-template <int Q, int ST, bool MACROS, bool COH>
+template <int Q, int ST, bool MACROS, bool COH, int MRT = -1>
 __device__ __forceinline__ void collide_node(const Dom &d, int k) {
   using IO = TIO<Q, ST, COH>;
   float4 c4;
@@ -263,7 +263,7 @@ __device__ __forceinline__ void collide_node(const Dom &d, int k) {
   const float F[3] = {hk * c4.x + rho * d.c.g[0], hk * c4.y + rho * d.c.g[1],
                       hk * c4.z + rho * d.c.g[2]};
   float u[3];
-  collide<Q>(d.c, ft, rho, F, m_phi(ldv<COH>(d.mf + k)), u);
+  collide<Q, MRT>(d.c, ft, rho, F, m_phi(ldv<COH>(d.mf + k)), u);
 #pragma unroll
   for (int i = 0; i < Q; ++i) IO::store(d, d.T_dst, i, k, ft[i]);
   const float seg = d.c.beta * rr * rb / rho;

@@ -363,11 +363,13 @@ __device__ __forceinline__ float relaxation_rate(const StepConst &c,
 //   f''_i = f_i - S (f_i - feq_i) + (1 - S/2) G_i + e_i . b,
 //   b = S (j - rho0 u + F/2) / E2,
 // feq of Eq. (A.4), G_i = w_i [3 (e_i - u) + 9 (e_i.u) e_i].F (A.5), u of
-// Eq. (22). ft holds f^t on entry and f''^t on exit.
-template <int Q>
+// Eq. (22). ft holds f^t on entry and f''^t on exit. MRT: 1 the MRT rates
+// below, 0 the single rate, -1 as c.mrt says at run time.
+template <int Q, int MRT = -1>
 __device__ __forceinline__ void collide(const StepConst &c, float *ft,
                                         float rho, const float *F, float phi,
                                         float *u) {
+  const bool mrt = MRT < 0 ? c.mrt != 0 : MRT == 1;
   float j[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
@@ -396,8 +398,8 @@ __device__ __forceinline__ void collide(const StepConst &c, float *ft,
   // with m^eq_q = -2/3 rho0 u, h_q = -2/3 F (A.4, A.5), m^eq_m = h_m = 0,
   // |row_q|^2 = 40 and |row_m|^2 = 8.
   float aq[3] = {0.f, 0.f, 0.f}, am[3] = {0.f, 0.f, 0.f};
-  if constexpr (Q == 19) {
-    if (c.mrt) {
+  if constexpr (Q == 19 && MRT != 0) {
+    if (mrt) {
       float q[3] = {0.f, 0.f, 0.f}, m[3] = {0.f, 0.f, 0.f};
 #pragma unroll
       for (int i = 1; i < Q; ++i) {
@@ -432,8 +434,8 @@ __device__ __forceinline__ void collide(const StepConst &c, float *ft,
     const float guo = w * (3.f * (eF - uF) + 9.f * eu * eF);
     ft[i] = ft[i] - S * (ft[i] - feq) + kf * guo +
             (ex * b[0] + ey * b[1] + ez * b[2]);
-    if constexpr (Q == 19) {
-      if (c.mrt && i > 0) {
+    if constexpr (Q == 19 && MRT != 0) {
+      if (mrt && i > 0) {
         const int ix = Lattice<Q>::ex(i), iy = Lattice<Q>::ey(i),
                   iz = Lattice<Q>::ez(i);
         const float c5 = (float)(5 * (ix * ix + iy * iy + iz * iz) - 9);

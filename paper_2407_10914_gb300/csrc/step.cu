@@ -55,10 +55,11 @@ __global__ void __launch_bounds__(BLOCK) k_nc_solid(Dom d) {
   if (j < d.NS) nc_solid_node<Q, false>(d, j);
 }
 
-template <int Q, int ST, bool MACROS>
+// MRT: the collision compiled for the single rate (0) or the MRT rates (1)
+template <int Q, int ST, bool MACROS, int MRT>
 __global__ void __launch_bounds__(BLOCK, 4) k_collide(Dom d) {
   const int k = blockIdx.x * BLOCK + threadIdx.x;
-  if (k < d.NF) collide_node<Q, ST, MACROS, false>(d, k);
+  if (k < d.NF) collide_node<Q, ST, MACROS, false, MRT>(d, k);
 }
 
 template <int Q, int ST>
@@ -78,10 +79,14 @@ static void launch_step_t(const Dom &d, cudaStream_t s, bool macros,
   if (ev) cudaEventRecord(ev[4], s);
   if (d.NS > 0) k_nc_solid<Q><<<gs, BLOCK, 0, s>>>(d);
   if (ev) cudaEventRecord(ev[5], s);
-  if (macros)
-    k_collide<Q, ST, true><<<g, BLOCK, 0, s>>>(d);
-  else
-    k_collide<Q, ST, false><<<g, BLOCK, 0, s>>>(d);
+  const bool mrt = Q == 19 && d.c.mrt;
+  if (macros) {
+    if (mrt) k_collide<Q, ST, true, 1><<<g, BLOCK, 0, s>>>(d);
+    else k_collide<Q, ST, true, 0><<<g, BLOCK, 0, s>>>(d);
+  } else {
+    if (mrt) k_collide<Q, ST, false, 1><<<g, BLOCK, 0, s>>>(d);
+    else k_collide<Q, ST, false, 0><<<g, BLOCK, 0, s>>>(d);
+  }
   if (ev) cudaEventRecord(ev[6], s);
 }
 
