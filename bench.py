@@ -16,6 +16,9 @@ One JSON line on rank 0:
   step_bandwidth  the step-level accounting of 308 B per fluid-node update
              (2 x 2Q populations of 4 B plus a 4 B link mask);
   cpu_baseline  the FP64 oracle on a bounded slab of the same rock;
+  tube       the capillary-tube workload (256 x 20 x 20, r = 8, Type-I,
+             20000 steps): throughput, and the interface speed beside the
+             Washburn law for equal viscosities (Eq. 47);
   laplace    the Laplace test of Sec. III.A at the paper's 128^3 scale: the
              interfacial tension from five drops in N/m beside the 0.02 N/m
              input and the paper's 0.02009;
@@ -101,6 +104,8 @@ def parse():
                     help="skip the 96-drop batched sweep object")
     ap.add_argument("--batched-cases", type=int, default=96)
     ap.add_argument("--batched-steps", type=int, default=20)
+    ap.add_argument("--no-tube", action="store_true",
+                    help="skip the capillary-tube object")
     ap.add_argument("--no-laplace", action="store_true",
                     help="skip the Laplace-law object")
     ap.add_argument("--no-washburn", action="store_true",
@@ -363,6 +368,10 @@ def run_ours(args):
     if not args.no_e2e:
         e2e = end_to_end(args, case, torch, lbm)
 
+    tube = None
+    if not args.no_tube and rank == 0:
+        tube = run_tube(torch, lbm)
+
     laplace = None
     if not args.no_laplace and rank == 0:
         laplace = run_laplace(lbm)
@@ -431,6 +440,8 @@ def run_ours(args):
         }
         if e2e:
             line["e2e"] = e2e
+        if tube:
+            line["tube"] = tube
         if laplace:
             line["laplace"] = laplace
         if washburn:
@@ -498,6 +509,48 @@ def end_to_end(args, case, torch, lbm):
             "final_sw": sw, "seconds": round(dt, 3),
             "note": "geometry set-up, phi0 upload, per-step S_w read-back "
                     "and the final phi download inside the timed region"}
+
+
+def run_tube(torch, lbm):
+    """The capillary tube in full (20000 steps, 4000 per record): MLUPS over
+    its fluid nodes, and the interface speed (fit over the last four
+    records) beside Eq. (47) with equal viscosities and cos(theta) = 0,
+    with the effective radius that speed implies."""
+    from paper_2407_10914_gb300 import analysis as A
+    from paper_2407_10914_gb300 import workloads as W
+    case = W.tube_3d()
+    s = lbm.Session(19, case.solid, case.periodic)
+    s.set_params(**case.params)
+    s.init_state(case.phi0.astype(np.float32))
+    stream = torch.cuda.current_stream()
+    ts, zs, ms = [], [], 0.0
+    for k in range(5):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(4000)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms += e0.elapsed_time(e1)
+        ts.append(4000 * (k + 1))
+        zs.append(A.interface_position(s.macros()["phi"].cpu().numpy(), 0,
+                                       case.solid))
+    U = float(np.polyfit(ts[1:], zs[1:], 1)[0])
+    p = case.params
+    dP = (p["rho_in"] - p["rho_out"]) / 3
+    mu = p["rho0"] * (p["tau_r"] - 0.5) / 3
+    L = case.solid.shape[2] - 1
+    r = case.info["radius"]
+    U_ref = r * r * dP / (8 * mu * L)
+    return {"workload": "tube_256x20x20_r8_typeI", "steps": 20000,
+            "fluid_nodes": s.n_fluid,
+            "value": round(s.n_fluid * 20000 / (ms * 1e-3) / 1e6, 1),
+            "unit": "MLUPS", "ms_per_step": round(ms / 20000, 5),
+            "interface_z": [round(z, 3) for z in zs],
+            "speed": U, "speed_eq47": U_ref,
+            "speed_error_pct": round(100 * abs(U / U_ref - 1), 2),
+            "r_eff": round(float(np.sqrt(8 * mu * L * U / dP)), 3),
+            "note": "launch-bound at this size (six kernels per step)"}
 
 
 def run_laplace(lbm):

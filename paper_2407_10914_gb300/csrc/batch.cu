@@ -91,10 +91,16 @@ __device__ __forceinline__ void run_node(const Dom &d, int pass, bool macros,
     case P_GRAD: gradient_node<Q, COH>(d, n); break;
     case P_NC_S: nc_solid_node<Q, COH>(d, n); break;
     default:
-      if (macros)
-        collide_node<Q, ST, true, COH>(d, n);
-      else
-        collide_node<Q, ST, false, COH>(d, n);
+      // the same collision instantiations as the single-domain kernels
+      // (single rate or MRT fixed at compile time), so that a case stepped
+      // in a batch and alone agree bit for bit
+      if (d.c.mrt) {
+        if (macros) collide_node<Q, ST, true, COH, 1>(d, n);
+        else collide_node<Q, ST, false, COH, 1>(d, n);
+      } else {
+        if (macros) collide_node<Q, ST, true, COH, 0>(d, n);
+        else collide_node<Q, ST, false, COH, 0>(d, n);
+      }
   }
 }
 

@@ -71,27 +71,35 @@ __device__ __forceinline__ void zh_fix_node(const Dom &d, int jz) {
   float ft[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) ft[i] = IO::load_from(d, d.U, i, k);
-  float K0 = 0.f, Kin = 0.f, N[3] = {0.f, 0.f, 0.f};
+  // K0, Kin and N_t from the deviations f_i - w_i rho0 (exact in float32,
+  // and small): the weights of the known populations add up to
+  // sum_{e.a=0} w + 2 sum_{e.a=in} w = 1 and sum_{e.a=0} (e.t) w = 0, so
+  // j = (rho_in - rho0) - (K0d + 2 Kind) keeps the precision of the
+  // deviations instead of cancelling two numbers near one.
+  float K0 = 0.f, Kin = 0.f, K0d = 0.f, Kind = 0.f, N[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int ea = Lattice<Q>::e(i, a);
+    const float dv = ft[i] - __fmul_rn(Lattice<Q>::w(i), d.c.rho0);
     if (ea == 0) {
       K0 += ft[i];
+      K0d += dv;
 #pragma unroll
       for (int t = 0; t < 3; ++t)
-        if (t != a) N[t] += 0.5f * (float)Lattice<Q>::e(i, t) * ft[i];
+        if (t != a) N[t] += 0.5f * (float)Lattice<Q>::e(i, t) * dv;
     } else if (ea == in_dir) {
       Kin += ft[i];
+      Kind += dv;
     }
   }
   float rr, rb, m, jt;
   if (inlet) {
-    jt = d.c.rho_in_r + d.c.rho_in_b - (K0 + 2.f * Kin);
+    jt = (d.c.rho_in_r + d.c.rho_in_b - d.c.rho0) - (K0d + 2.f * Kind);
     rr = d.c.rho_in_r;
     rb = d.c.rho_in_b;
     m = d.c.m_in;
   } else {
-    jt = (K0 + 2.f * Kin) - d.c.rho_out;
+    jt = (K0d + 2.f * Kind) - (d.c.rho_out - d.c.rho0);
     const uint32_t e = nb_f(d, 2 * a + 2, k);  // the node at x - a
     const float2 Rk = ldv<true>(d.R + k);
     m = ((entry_cls(e) & 2) && !entry_out(e)) ? ldv<COH>(d.mf + entry_idx(e))

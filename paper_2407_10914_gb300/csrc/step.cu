@@ -56,8 +56,11 @@ __global__ void __launch_bounds__(BLOCK) k_nc_solid(Dom d) {
 }
 
 // MRT: the collision compiled for the single rate (0) or the MRT rates (1)
+#ifndef LBM_MINB_COLLIDE
+#define LBM_MINB_COLLIDE 3
+#endif
 template <int Q, int ST, bool MACROS, int MRT>
-__global__ void __launch_bounds__(BLOCK, 4) k_collide(Dom d) {
+__global__ void __launch_bounds__(BLOCK, LBM_MINB_COLLIDE) k_collide(Dom d) {
   const int k = blockIdx.x * BLOCK + threadIdx.x;
   if (k < d.NF) collide_node<Q, ST, MACROS, false, MRT>(d, k);
 }
