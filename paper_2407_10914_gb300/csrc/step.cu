@@ -23,8 +23,9 @@ constexpr int BLOCK = 256;
 // Blocks per SM, measured on the 256^3 rock: the gather passes are bound by
 // load latency, so the stream and gradient passes run with 32 registers
 // (7-8 resident blocks of 256 threads; the gradient pass gains 14 % over its
-// unbounded 34 registers, the stream pass 4 % over 40), the collision with
-// 64 (4 blocks; 3 or 5 blocks are 7 % and 20 % slower).
+// unbounded 34 registers, the stream pass 4 % over 40). The collision (with
+// its sums in deviation form) needs 80 registers: 3 blocks, 5 % faster than
+// 4 blocks with 64 registers and spills.
 template <int Q, int ST>
 __global__ void __launch_bounds__(BLOCK, 7) k_stream(Dom d) {
   const int k = blockIdx.x * BLOCK + threadIdx.x;
@@ -56,11 +57,8 @@ __global__ void __launch_bounds__(BLOCK) k_nc_solid(Dom d) {
 }
 
 // MRT: the collision compiled for the single rate (0) or the MRT rates (1)
-#ifndef LBM_MINB_COLLIDE
-#define LBM_MINB_COLLIDE 3
-#endif
 template <int Q, int ST, bool MACROS, int MRT>
-__global__ void __launch_bounds__(BLOCK, LBM_MINB_COLLIDE) k_collide(Dom d) {
+__global__ void __launch_bounds__(BLOCK, 3) k_collide(Dom d) {
   const int k = blockIdx.x * BLOCK + threadIdx.x;
   if (k < d.NF) collide_node<Q, ST, MACROS, false, MRT>(d, k);
 }
