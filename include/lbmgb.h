@@ -136,7 +136,13 @@ lbm_status lbm_set_params(lbm_handle h, const lbm_params *p);
  * ignored). Needs lbm_set_params() first. */
 lbm_status lbm_init_state(lbm_handle h, const float *phi0_dev, void *stream);
 
-/* Advance nsteps time steps (Eq. 1), asynchronously on `stream`. */
+/* Advance nsteps time steps (Eq. 1), asynchronously on `stream`. All
+ * steps but the last are replayed two at a time from a CUDA graph that the
+ * handle records on its own stream at first use (and again after
+ * lbm_set_params); the last step, which also stores the macros, and an odd
+ * one are plain launches. The results equal those of nsteps single steps
+ * bit for bit. If the graph cannot be recorded the steps are launched one
+ * by one. */
 lbm_status lbm_step(lbm_handle h, int nsteps, void *stream);
 
 /* Kernels of a step, in launch order, as lbm_step_timed() reports them. */

@@ -289,6 +289,7 @@ lbm_status lbm_set_params(lbm_handle c, const lbm_params *p) {
   for (int a = 0; a < 3; ++a) k.g[a] = (float)p->g[a];
   k.mrt = p->collision;
   c->params_set = true;
+  ++c->pgen;  // recorded step graphs hold the old parameters
   ++c->gen;
   return LBM_OK;
 }
@@ -304,11 +305,58 @@ lbm_status lbm_init_state(lbm_handle c, const float *phi0, void *stream) {
   return LBM_OK;
 }
 
+// The graph of two steps without macros for the current orientation of the
+// state buffers, recorded on first use (or after lbm_set_params); null if
+// the stream cannot be captured (lbm_step then launches step by step).
+static cudaGraphExec_t step_pair_graph(lbm_ctx *c) {
+  const int o = c->d.T_src == c->TA ? 0 : 1;
+  if (c->g2[o] && c->g2_pgen[o] == c->pgen) return c->g2[o];
+  if (c->g2[o]) {
+    cudaGraphExecDestroy(c->g2[o]);
+    c->g2[o] = nullptr;
+  }
+  cudaError_t e = cudaSuccess;
+  if (!c->cap) e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return nullptr;
+  cudaGraph_t g = nullptr;
+  e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int k = 0; k < 2; ++k) {  // two swaps: the orientation comes back
+      lbm::launch_step(c->Q, c->storage, c->d, c->cap, false);
+      swap_buffers(c);
+    }
+    e = cudaStreamEndCapture(c->cap, &g);
+  }
+  cudaGraphExec_t x = nullptr;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&x, g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // clear a capture error; step without a graph
+    return nullptr;
+  }
+  c->g2[o] = x;
+  c->g2_pgen[o] = c->pgen;
+  return x;
+}
+
 lbm_status lbm_step(lbm_handle c, int nsteps, void *stream) {
   if (!c || nsteps < 0) return LBM_ERR_ARG;
   if (!c->state_set) return fail(c, LBM_ERR_STATE, "init the state first");
   cudaStream_t s = (cudaStream_t)stream;
-  for (int k = 0; k < nsteps; ++k) {
+  // all steps but the last (which also stores the macros) in pairs from
+  // the recorded graph, then the odd one and the last by plain launches;
+  // the kernels and their arguments are the same either way
+  int k = 0;
+  const int pairs = (nsteps - 1) / 2;
+  cudaGraphExec_t g = pairs > 0 ? step_pair_graph(c) : nullptr;
+  if (g) {
+    for (int p = 0; p < pairs; ++p) {
+      const cudaError_t e = cudaGraphLaunch(g, s);
+      if (e != cudaSuccess) return cuda_fail(c, e, "step graph");
+    }
+    k = 2 * pairs;
+  }
+  for (; k < nsteps; ++k) {
     lbm::launch_step(c->Q, c->storage, c->d, s, k == nsteps - 1);
     swap_buffers(c);
   }

@@ -116,7 +116,19 @@ struct lbm_ctx {
   // batch (set_params, init_state, set_populations, step): a batch holding
   // this domain refreshes its copy of the kernel arguments when it changes
   unsigned long long gen = 0;
+  // lbm_step replays two steps at a time from a CUDA graph recorded on the
+  // handle's own stream: one graph per orientation of the state buffers
+  // (index 0: state in TA), valid while the parameters are those of pgen
+  unsigned long long pgen = 0;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t g2[2] = {nullptr, nullptr};
+  unsigned long long g2_pgen[2] = {0, 0};
   char err[256] = {0};
+  ~lbm_ctx() {
+    for (auto &x : g2)
+      if (x) cudaGraphExecDestroy(x);
+    if (cap) cudaStreamDestroy(cap);
+  }
 };
 
 namespace lbm {

@@ -246,3 +246,32 @@ def test_step_timed_equals_step(torch):
     fa = a.get_populations().cpu().numpy()
     fb = b.get_populations().cpu().numpy()
     assert np.array_equal(fa, fb)
+
+
+def test_step_graph_equals_single_steps(torch):
+    """lbm_step(n) replays pairs of steps from a recorded CUDA graph: the
+    state equals that of n single steps bit for bit, for odd and even n,
+    across both orientations of the state buffers, and after new
+    parameters (the graph is recorded again)."""
+    case = CASES[2][1]  # Zou-He planes and solids: all six kernels
+    a = gpu_session(torch, case)
+    b = gpu_session(torch, case)
+    for s in (a, b):
+        s.init_state(case.phi0.astype(np.float32))
+    for n in (7, 4, 5, 2, 9):
+        a.step(n)
+        for _ in range(n):
+            b.step(1)
+        assert np.array_equal(a.get_populations().cpu().numpy(),
+                              b.get_populations().cpu().numpy()), n
+    p = dict(case.params, theta_deg=60.0, rho_in=1.03)
+    for s in (a, b):
+        s.set_params(**p)
+    a.step(6)
+    for _ in range(6):
+        b.step(1)
+    assert np.array_equal(a.get_populations().cpu().numpy(),
+                          b.get_populations().cpu().numpy())
+    for k in ("rho", "phi", "u"):
+        assert np.array_equal(a.macros()[k].cpu().numpy(),
+                              b.macros()[k].cpu().numpy()), k
