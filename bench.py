@@ -149,6 +149,14 @@ def barrier(ws):
         dist.barrier()
 
 
+def whole_job_value(ws: int, units_per_rank: int, steps: int,
+                    ms_max: float) -> float:
+    """Whole-job throughput in millions of units per second: the units all
+    ranks processed (every rank steps its own replica) over the slowest
+    rank's time."""
+    return ws * units_per_rank * steps / (ms_max * 1e-3) / 1e6
+
+
 def max_over_ranks(v, ws):
     if ws == 1:
         return v
@@ -331,7 +339,7 @@ def run_ours(args):
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     ms_max = max_over_ranks(ms, ws)
-    value = ws * nf * args.steps / (ms_max * 1e-3) / 1e6
+    value = whole_job_value(ws, nf, args.steps, ms_max)
 
     # per-pass times (events inside the library, on the same stream)
     k2 = max(1, min(args.steps, 200))
