@@ -12,6 +12,7 @@
 // One thread per node of the compact fluid (F) or solid-boundary (S) list;
 // the work of a node is in passes.cuh.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "passes.cuh"
 #include "step.hpp"
@@ -63,24 +64,49 @@ __global__ void __launch_bounds__(BLOCK, 3) k_collide(Dom d) {
   if (k < d.NF) collide_node<Q, ST, MACROS, false, MRT>(d, k);
 }
 
+// NVTX range around the launch of one pass (header-only NVTX: a no-op
+// unless a profiler that records NVTX is attached), so that a timeline
+// names every kernel by its pass of the step.
+struct PassRange {
+  explicit PassRange(const char *name) { nvtxRangePushA(name); }
+  ~PassRange() { nvtxRangePop(); }
+};
+
 template <int Q, int ST>
 static void launch_step_t(const Dom &d, cudaStream_t s, bool macros,
                           cudaEvent_t *ev) {
+  PassRange step_range("lbm step");
   const unsigned g = (unsigned)((d.NF + BLOCK - 1) / BLOCK);
   const unsigned gs = (unsigned)((d.NS + BLOCK - 1) / BLOCK);
   const unsigned gz = (unsigned)((d.n_zh + BLOCK - 1) / BLOCK);
   if (ev) cudaEventRecord(ev[0], s);
-  k_stream<Q, ST><<<g, BLOCK, 0, s>>>(d);
+  {
+    PassRange r("stream (Eq. 1, 7-9)");
+    k_stream<Q, ST><<<g, BLOCK, 0, s>>>(d);
+  }
   if (ev) cudaEventRecord(ev[1], s);
-  if (d.n_zh > 0) k_zh_fix<Q, ST><<<gz, BLOCK, 0, s>>>(d);
+  if (d.n_zh > 0) {
+    PassRange r("Zou-He planes (App. B)");
+    k_zh_fix<Q, ST><<<gz, BLOCK, 0, s>>>(d);
+  }
   if (ev) cudaEventRecord(ev[2], s);
-  if (d.NS > 0) k_phi_solid<Q><<<gs, BLOCK, 0, s>>>(d);
+  if (d.NS > 0) {
+    PassRange r("phi at solid boundary (Eq. 34)");
+    k_phi_solid<Q><<<gs, BLOCK, 0, s>>>(d);
+  }
   if (ev) cudaEventRecord(ev[3], s);
-  k_gradient<Q><<<g, BLOCK, 0, s>>>(d);
+  {
+    PassRange r("gradient, wetting (Eq. 6, 27-33)");
+    k_gradient<Q><<<g, BLOCK, 0, s>>>(d);
+  }
   if (ev) cudaEventRecord(ev[4], s);
-  if (d.NS > 0) k_nc_solid<Q><<<gs, BLOCK, 0, s>>>(d);
+  if (d.NS > 0) {
+    PassRange r("n_c at solid boundary (Eq. 35)");
+    k_nc_solid<Q><<<gs, BLOCK, 0, s>>>(d);
+  }
   if (ev) cudaEventRecord(ev[5], s);
   const bool mrt = Q == 19 && d.c.mrt;
+  PassRange r("curvature, collision, recolouring (Eq. 12, 5, 2, 20-21)");
   if (macros) {
     if (mrt) k_collide<Q, ST, true, 1><<<g, BLOCK, 0, s>>>(d);
     else k_collide<Q, ST, true, 0><<<g, BLOCK, 0, s>>>(d);
