@@ -23,8 +23,9 @@ One JSON line on rank 0:
              interfacial tension from five drops in N/m beside the 0.02 N/m
              input and the paper's 0.02009;
   washburn   Washburn Case-I (Sec. IV.A.1): spontaneous imbibition in the
-             12x12x101 tube at 30-75 deg with both wetting schemes, the
-             paper's area error against Eq. (49) for each;
+             12x12x101 tube at 30-75 deg with both wetting schemes, and
+             Case-II (Sec. IV.A.2): theta = 90 deg, three pressure drops,
+             Type-I and Type-II; the paper's area error against Eq. (49);
   mrt        the same rock with the MRT collision (Eq. 2 with the rates of
              Eqs. 4, 15-16), with its error against the FP64 oracle's MRT;
   storage_16bit the same rock with FP16 / BF16 population storage, each
@@ -618,6 +619,26 @@ def run_washburn(lbm):
                 "zstar_end": round(float(r["zstar"][-1]), 4),
                 "zstar_end_eq49": round(float(r["zstar_eq49"][-1]), 4),
                 "tstar_end": round(float(r["tstar"][-1]), 2)})
+    # Case-II (Sec. IV.A.2): theta = 90 deg, pressure-driven, both drives
+    case = W.washburn_tube(90.0, 1)
+
+    def make2(params, case=case):
+        s = lbm.Session(19, case.solid, case.periodic)
+        s.set_params(**params)
+        s.init_state(case.phi0.astype(np.float32))
+        return s
+
+    out["case2"] = []
+    for drive in ("typeI", "typeII"):
+        for dp_term in (0.01, 0.02, 0.04):
+            dp = dp_term * 2 * case.info["length"] * case.params["gamma"] / 25.0
+            r = Wb.run_case2(make2, case, dp, drive, tstar_end=60.0)
+            out["case2"].append({
+                "drive": drive, "dp_lbm": round(dp, 6),
+                "dp_pa_paper_units": round(dp * 1e-15 / (1e-6 * (1e-6 / 30) ** 2), 1),
+                "area_error_pct": round(100 * r["area_error"], 3),
+                "zstar_end": round(float(r["zstar"][-1]), 4),
+                "zstar_end_eq49": round(float(r["zstar_eq49"][-1]), 4)})
     out["seconds"] = round(time.time() - t0, 1)
     return out
 

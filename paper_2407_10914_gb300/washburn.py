@@ -1,7 +1,9 @@
-"""Washburn Case-I of Sec. IV.A: spontaneous imbibition of the wetting
-fluid b into a capillary tube filled with the non-wetting fluid r, at equal
-end pressures, against the Washburn law with unequal viscosities (Eqs.
-47-51) and the paper's area error.
+"""Washburn tests of Sec. IV.A: the wetting fluid b entering a capillary
+tube filled with the non-wetting fluid r, against the Washburn law with
+unequal viscosities (Eqs. 47-51) and the paper's area error. Case-I:
+spontaneous imbibition (theta < 90 deg, equal end pressures). Case-II:
+neutral wetting (theta = 90 deg) and a pressure difference, imposed by the
+Zou-He densities (Type-I) or a body force (Type-II).
 
 In non-dimensional form (Eqs. 49-51), with m = mu_nw / (mu_w - mu_nw),
     z*(t*) = -m + sqrt(m^2 + (Delta P r^2 / (2 L gamma) + (r/L) cos(theta))
@@ -68,12 +70,35 @@ def run_case1(make_session: Callable[[dict], object], case,
               theta_deg: float, wetting: int, tstar_end: float = 60.0,
               sample_every: int = 500, init_tol: float = 0.01,
               init_max_steps: int = 40000) -> dict:
-    """Run Case-I at one contact angle and wetting scheme.
+    """Case-I (Sec. IV.A.1): spontaneous imbibition at contact angle
+    theta_deg, equal end pressures."""
+    return run(make_session, case, theta_deg, wetting, 0.0, "typeI",
+               tstar_end, sample_every, init_tol, init_max_steps)
+
+
+def run_case2(make_session: Callable[[dict], object], case, dp_lbm: float,
+              drive: str, wetting: int = 1, tstar_end: float = 60.0,
+              sample_every: int = 500, init_tol: float = 0.01,
+              init_max_steps: int = 40000) -> dict:
+    """Case-II (Sec. IV.A.2): neutral wetting (theta = 90 deg), the fluids
+    driven by a lattice pressure difference dp_lbm, imposed by the Zou-He
+    densities (Type-I, rho_in - rho_out = 3 dp) or by a body force with
+    equal end densities (Type-II, g = dp / (rho0 L))."""
+    return run(make_session, case, 90.0, wetting, dp_lbm, drive,
+               tstar_end, sample_every, init_tol, init_max_steps)
+
+
+def run(make_session, case, theta_deg: float, wetting: int, dp_lbm: float,
+        drive: str, tstar_end: float, sample_every: int, init_tol: float,
+        init_max_steps: int) -> dict:
+    """One run: the settled neutral start, then the contact angle and the
+    drive; the sampled curve beside Eq. (49) and the area error.
 
     make_session(params) returns an engine holding `case`'s geometry with
     those parameters and the initial phase field loaded (e.g. a GPU
-    Session). Returns the sampled curve, Eq. (49) on the same times, and
-    the area error."""
+    Session)."""
+    if drive not in ("typeI", "typeII"):
+        raise ValueError("drive must be typeI or typeII")
     p = dict(case.params)
     L = float(case.info["length"])
     r = float(case.info["radius"])
@@ -83,7 +108,8 @@ def run_case1(make_session: Callable[[dict], object], case,
     m = mu_nw / (mu_w - mu_nw)
     gamma = p["gamma"]
     steps_per_tstar = (mu_w - mu_nw) * L / gamma  # Eq. (51)
-    # 1) neutral initial run until the interface stops
+    dp_term = dp_lbm * r * r / (2.0 * L * gamma)
+    # 1) neutral initial run without drive until the interface stops
     s = make_session(dict(p, theta_deg=90.0, wetting=wetting))
     z_prev, steps = None, 0
     while steps < init_max_steps:
@@ -94,9 +120,16 @@ def run_case1(make_session: Callable[[dict], object], case,
             break
         z_prev = z
     z_init = z / L
-    # 2) the contact angle; t* starts at Eq. (49)'s time of z*_init
-    s.set_params(**dict(p, theta_deg=theta_deg, wetting=wetting))
-    t0 = tstar_of(z_init, theta_deg, m, r / L)
+    # 2) contact angle and drive; t* starts at Eq. (49)'s time of z*_init
+    q = dict(p, theta_deg=theta_deg, wetting=wetting)
+    if dp_lbm != 0.0:
+        rho = p["rho_out"]
+        if drive == "typeI":
+            q.update(rho_in=rho + 1.5 * dp_lbm, rho_out=rho - 1.5 * dp_lbm)
+        else:
+            q.update(g=(dp_lbm / (rho0 * L), 0.0, 0.0))
+    s.set_params(**q)
+    t0 = tstar_of(z_init, theta_deg, m, r / L, dp_term)
     n_steps = int(math.ceil((tstar_end - t0) * steps_per_tstar))
     ts, zs = [t0], [z_init]
     done = 0
@@ -111,8 +144,9 @@ def run_case1(make_session: Callable[[dict], object], case,
         zs.append(zz)
     ts = np.asarray(ts)
     zs = np.asarray(zs)
-    ref = zstar(ts, theta_deg, m, r / L)
-    return dict(theta_deg=theta_deg, wetting=wetting, z_init=z_init,
-                tstar_init=t0, init_steps=steps, tstar=ts, zstar=zs,
-                zstar_eq49=ref, area_error=area_error(zs, ref, ts),
+    ref = zstar(ts, theta_deg, m, r / L, dp_term)
+    return dict(theta_deg=theta_deg, wetting=wetting, dp_lbm=dp_lbm,
+                drive=drive, z_init=z_init, tstar_init=t0, init_steps=steps,
+                tstar=ts, zstar=zs, zstar_eq49=ref,
+                area_error=area_error(zs, ref, ts),
                 steps_per_tstar=steps_per_tstar)
