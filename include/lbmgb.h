@@ -177,6 +177,13 @@ lbm_status lbm_get_populations(lbm_handle h, float *dst_dev, void *stream);
 lbm_status lbm_set_populations(lbm_handle h, const float *src_dev,
                                void *stream);
 
+/* Error word of the bounds-checked build (the library compiled with
+ * LBM_BOUNDS_CHECK, liblbmgb_check.so; no counterpart in the paper): bit 0
+ * a pull source, bit 1 a stencil neighbour, bit 2 a Zou-He plane index,
+ * bit 3 a solid-boundary link was out of range (the access was redirected
+ * to index 0). Always 0 in the normal build. Synchronises the stream. */
+lbm_status lbm_debug_flags(lbm_handle h, unsigned *out_host, void *stream);
+
 /* Replace the injected fluid (Sec. II.D.1, Eqs. 37-38): at every fluid node
  * of the inlet plane (coordinate 0 of flow_axis) the stored populations of
  * the other colour are added to colour `colour` (0 = r, 1 = b) and set to

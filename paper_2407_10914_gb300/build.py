@@ -43,15 +43,24 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra=None) -> str:
-    os.makedirs(OBJDIR, exist_ok=True)
+CHECK_OBJDIR = os.path.join(HERE, "_build_check")
+CHECK_LIB = os.path.join(HERE, "liblbmgb_check.so")
+
+
+def build(force: bool = False, verbose: bool = False, extra=None,
+          check: bool = False) -> str:
+    """Build liblbmgb.so, or with check=True the bounds-checked debug
+    library liblbmgb_check.so (every gathered index guarded, violations
+    recorded in the error word that lbm_debug_flags reads)."""
+    objdir, lib = (CHECK_OBJDIR, CHECK_LIB) if check else (OBJDIR, LIB)
+    os.makedirs(objdir, exist_ok=True)
     srcs = _sources()
     hdrs = _headers()
-    extra = list(extra or [])
+    extra = list(extra or []) + (["-DLBM_BOUNDS_CHECK"] if check else [])
     objs = []
     jobs = []
     for s in srcs:
-        o = os.path.join(OBJDIR, os.path.basename(s)[:-3] + ".o")
+        o = os.path.join(objdir, os.path.basename(s)[:-3] + ".o")
         objs.append(o)
         if force or _stale(o, [s] + hdrs):
             cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", s, "-o", o]
@@ -67,15 +76,15 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> str:
                     print(r.stdout, r.stderr)
                 if r.returncode != 0:
                     raise RuntimeError(f"nvcc failed on {cmd[-3]}")
-    if force or jobs or _stale(LIB, objs):
-        tmp = LIB + f".{os.getpid()}.tmp"
+    if force or jobs or _stale(lib, objs):
+        tmp = lib + f".{os.getpid()}.tmp"
         cmd = [nvcc(), *ARCH, "-shared", "-cudart", "shared", *objs, "-o", tmp]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             print(r.stdout, r.stderr)
             raise RuntimeError("nvcc link failed")
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -215,6 +215,7 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
   d.ncf = (float4 *)(base + L.ncf);
   d.ncs = (float4 *)(base + L.ncs);
   d.macro = (float4 *)(base + L.macro);
+  d.err = (unsigned *)(c->counters + 3);  // zeroed with the counters at set-up
   cudaError_t e = cudaMemcpyAsync(c->mask, solid_host, (size_t)N,
                                   cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = lbm::build_geometry(c, s);
@@ -460,6 +461,16 @@ lbm_status lbm_set_populations(lbm_handle c, const float *src, void *stream) {
   if (e != cudaSuccess) return cuda_fail(c, e, "set_populations");
   c->state_set = true;
   ++c->gen;
+  return LBM_OK;
+}
+
+lbm_status lbm_debug_flags(lbm_handle c, unsigned *out_host, void *stream) {
+  if (!c || !out_host) return LBM_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(out_host, c->d.err, sizeof(unsigned),
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "debug_flags");
   return LBM_OK;
 }
 

@@ -84,6 +84,7 @@ struct Dom {
   float4 *ncf;          // [NF] (n_c, |C|)
   float4 *ncs;          // [NS] (n_c of Eq. 35, 0)
   float4 *macro;        // [NF] (u_x, u_y, u_z, rho) of the last macro step
+  unsigned *err;        // error word of the bounds-checked build (guard())
   StepConst c;
 };
 

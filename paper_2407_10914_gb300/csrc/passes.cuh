@@ -64,7 +64,7 @@ __device__ __forceinline__ void zh_fix_node(const Dom &d, int jz) {
   // U and R of the node are read and then rewritten by this thread: never
   // through the read-only path
   using IO = TIO<Q, ST, true>;
-  const int k = __ldg(d.zh_list + jz);
+  const int k = guard(d, __ldg(d.zh_list + jz), d.NF, GUARD_ZOU_HE);
   const int a = d.c.axis;
   const bool inlet = __ldg(d.fflag + k) & (2u << (2 * a));
   const int in_dir = inlet ? -1 : 1;  // e.a of the known, inward populations
@@ -102,7 +102,8 @@ __device__ __forceinline__ void zh_fix_node(const Dom &d, int jz) {
     jt = (K0d + 2.f * Kind) - (d.c.rho_out - d.c.rho0);
     const uint32_t e = nb_f(d, 2 * a + 2, k);  // the node at x - a
     const float2 Rk = ldv<true>(d.R + k);
-    m = ((entry_cls(e) & 2) && !entry_out(e)) ? ldv<COH>(d.mf + entry_idx(e))
+    m = ((entry_cls(e) & 2) && !entry_out(e))
+            ? ldv<COH>(d.mf + guard(d, entry_idx(e), d.NF, GUARD_ZOU_HE))
                                                : m_of(Rk.x, Rk.y);
     // red parts of the known populations (e.a >= 0), as the pull split them
     const float4 Sown = ldv<COH>(d.S_src + k);
@@ -117,7 +118,9 @@ __device__ __forceinline__ void zh_fix_node(const Dom &d, int jz) {
       } else {
         const uint32_t es = nb_f(d, Lattice<Q>::opp(i), k);
         const bool fl = (entry_cls(es) & 2) && !entry_out(es);
-        const float4 S = fl ? ldv<COH>(d.S_src + entry_idx(es)) : Sown;
+        const float4 S =
+            fl ? ldv<COH>(d.S_src + guard(d, entry_idx(es), d.NF, GUARD_ZOU_HE))
+               : Sown;
         const float ev = (float)Lattice<Q>::ex(i) * S.y +
                          (float)Lattice<Q>::ey(i) * S.z +
                          (float)Lattice<Q>::ez(i) * S.w;
@@ -153,9 +156,11 @@ __device__ __forceinline__ void phi_solid_node(const Dom &d, int j) {
   float den = 0.f, sphi = 0.f, ex_pos = 0.f, ex_neg = 0.f;
   const int e = __ldg(d.soff + j + 1);
   for (int p = __ldg(d.soff + j); p < e; ++p) {
-    const uint32_t l = __ldg(d.slink + p);
+    const uint32_t l =
+        __ldg(d.slink + guard(d, p, (Q - 1) * d.NS, GUARD_LINK));
     const float w = link_w<Q>(l);
-    const float m = ldv<COH>(d.mf + (l & 0x7FFFFFFFu));
+    const float m =
+        ldv<COH>(d.mf + guard(d, (int)(l & 0x7FFFFFFFu), d.NF, GUARD_LINK));
     den += w;
     sphi += w * m_phi(m);
     ex_pos += w * m_excess(m, false);
@@ -178,8 +183,9 @@ __device__ __forceinline__ void gradient_node(const Dom &d, int k) {
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     const uint32_t e = nb_f(d, i, k);
-    const int idx = entry_idx(e);
-    const float m = (entry_cls(e) & 2) ? ldv<COH>(d.mf + idx) : ldv<COH>(d.ms + idx);
+    const bool fl = entry_cls(e) & 2;
+    const int idx = guard(d, entry_idx(e), fl ? d.NF : d.NS, GUARD_STENCIL);
+    const float m = fl ? ldv<COH>(d.mf + idx) : ldv<COH>(d.ms + idx);
     const float p = 3.f * Lattice<Q>::w(i) * m_excess(m, own_blue);
     G[0] += (float)Lattice<Q>::ex(i) * p;
     G[1] += (float)Lattice<Q>::ey(i) * p;
@@ -212,9 +218,11 @@ __device__ __forceinline__ void nc_solid_node(const Dom &d, int j) {
   float num[3] = {0.f, 0.f, 0.f}, den = 0.f;
   const int e = __ldg(d.soff + j + 1);
   for (int p = __ldg(d.soff + j); p < e; ++p) {
-    const uint32_t l = __ldg(d.slink + p);
+    const uint32_t l =
+        __ldg(d.slink + guard(d, p, (Q - 1) * d.NS, GUARD_LINK));
     const float w = link_w<Q>(l);
-    const float4 v = ldv<COH>(d.ncf + (l & 0x7FFFFFFFu));
+    const float4 v =
+        ldv<COH>(d.ncf + guard(d, (int)(l & 0x7FFFFFFFu), d.NF, GUARD_LINK));
     num[0] += w * v.x;
     num[1] += w * v.y;
     num[2] += w * v.z;
@@ -232,8 +240,9 @@ __device__ __forceinline__ float curvature(const Dom &d, int k, float4 &c4) {
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     const uint32_t e = nb_f(d, i, k);
-    const int idx = entry_idx(e);
-    const float4 v = (entry_cls(e) & 2) ? ldv<COH>(d.ncf + idx) : ldv<COH>(d.ncs + idx);
+    const bool fl = entry_cls(e) & 2;
+    const int idx = guard(d, entry_idx(e), fl ? d.NF : d.NS, GUARD_STENCIL);
+    const float4 v = fl ? ldv<COH>(d.ncf + idx) : ldv<COH>(d.ncs + idx);
     const float w3 = 3.f * Lattice<Q>::w(i);
 #pragma unroll
     for (int b = 0; b < 3; ++b) {

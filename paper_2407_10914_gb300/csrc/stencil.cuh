@@ -46,6 +46,34 @@ __device__ __forceinline__ int axis_step(int v, int m, bool per, bool clamp,
 
 __device__ __forceinline__ bool is_fluid_cls(int c) { return c & 2; }
 
+// ------------------------------------------------------ index guards
+// Every gathered index goes through guard(). In a build with
+// LBM_BOUNDS_CHECK defined (build.build(check=True): liblbmgb_check.so) an
+// index outside [0, bound) sets `code` in the domain's error word
+// (lbm_debug_flags) and is replaced by 0, so that the access stays inside
+// its array; in the normal build guard() is the identity. This stands in
+// for a memory checker, which this GPU pool does not offer.
+enum : unsigned {
+  GUARD_PULL = 1u,      // a pull source (F-space)
+  GUARD_STENCIL = 2u,   // a stencil neighbour (F- or S-space)
+  GUARD_ZOU_HE = 4u,    // a Zou-He plane node or its x - a neighbour
+  GUARD_LINK = 8u,      // a solid-boundary link or its CSR offsets
+};
+__device__ __forceinline__ int guard(const Dom &d, int idx, int bound,
+                                     unsigned code) {
+#ifdef LBM_BOUNDS_CHECK
+  if ((unsigned)idx >= (unsigned)bound) {
+    atomicOr(d.err, code);
+    return 0;
+  }
+#else
+  (void)d;
+  (void)bound;
+  (void)code;
+#endif
+  return idx;
+}
+
 // ------------------------------------------------------ phase encoding
 // A node's colour split is kept as one float m: the minority fraction
 // mu = min(rho^r, rho^b)/rho with its own sign (it can be slightly negative,

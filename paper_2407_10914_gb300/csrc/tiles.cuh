@@ -175,7 +175,7 @@ __device__ __forceinline__ void pull_nb(const Dom &d, int k, float4 Sown,
     const uint32_t e =
         __ldg(d.nbf + (long long)(Lattice<Q>::opp(i) - 1) * d.NFp + k);
     const bool fl = (entry_cls(e) & 2) && !entry_out(e);
-    const int src = fl ? entry_idx(e) : k;
+    const int src = guard(d, fl ? entry_idx(e) : k, d.NF, GUARD_PULL);
     const float T = IO::load_dyn(d, fl ? i : Lattice<Q>::opp(i), src);
     const float4 S = fl ? ldv<COH>(d.S_src + src) : Sown;
     const float ev = (float)Lattice<Q>::ex(i) * S.y +
@@ -205,7 +205,7 @@ __device__ __forceinline__ void pull_sums(const Dom &d, int k, float4 Sown,
       const uint32_t e =
           __ldg(d.nbf + (long long)(Lattice<Q>::opp(i) - 1) * d.NFp + k);
       const bool fl = (entry_cls(e) & 2) && !entry_out(e);
-      const int src = fl ? entry_idx(e) : k;
+      const int src = guard(d, fl ? entry_idx(e) : k, d.NF, GUARD_PULL);
       ft[i] = IO::load_dyn(d, fl ? i : Lattice<Q>::opp(i), src);
       const float4 S = fl ? ldv<COH>(d.S_src + src) : Sown;
       const float ev = (float)Lattice<Q>::ex(i) * S.y +

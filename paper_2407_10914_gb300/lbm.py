@@ -31,6 +31,7 @@ EXPORTS = ("lbm_workspace_bytes", "lbm_init_geometry", "lbm_set_params",
            "lbm_init_state", "lbm_step", "lbm_step_timed", "lbm_macros",
            "lbm_reduce",
            "lbm_get_populations", "lbm_set_populations", "lbm_swap_inlet",
+           "lbm_debug_flags",
            "lbm_get_geometry",
            "lbm_counts", "lbm_colour_mass_noalloc", "lbm_last_error",
            "lbm_destroy",
@@ -98,6 +99,8 @@ def load_library(path: str = LIB_PATH):
     L.lbm_set_populations.argtypes = [vp, vp, vp]
     L.lbm_swap_inlet.restype = C.c_int
     L.lbm_swap_inlet.argtypes = [vp, C.c_int, vp]
+    L.lbm_debug_flags.restype = C.c_int
+    L.lbm_debug_flags.argtypes = [vp, C.POINTER(C.c_uint), vp]
     L.lbm_get_geometry.restype = C.c_int
     L.lbm_get_geometry.argtypes = [vp, vp, vp, vp]
     L.lbm_counts.restype = C.c_int
@@ -257,6 +260,13 @@ def lbm_get_populations(h, dst, stream):
 def lbm_set_populations(h, src, stream):
     _check(load_library().lbm_set_populations(h, _dptr(src), stream), h,
            "lbm_set_populations")
+
+
+def lbm_debug_flags(h, stream) -> int:
+    out = C.c_uint(0)
+    _check(load_library().lbm_debug_flags(h, C.byref(out), stream), h,
+           "lbm_debug_flags")
+    return int(out.value)
 
 
 def lbm_swap_inlet(h, colour: int, stream):
