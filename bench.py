@@ -36,7 +36,7 @@ One JSON line on rank 0:
              128^3 imbibition pack w.r.t. theta and g_x, beside central
              finite differences.
 
-`--impl reference` times the oracle (the reference arm of this build) on the
+`--impl reference` times the oracle (the reference arm) on the
 host cores instead. Several GPUs (torchrun) run independent replicas.
 """
 from __future__ import annotations
@@ -737,7 +737,7 @@ def run_16bit(args, torch, lbm, case, steps: int):
             "value": round(s.n_fluid / (ms * 1e-3) / 1e6, 2), "unit": "MLUPS",
             "ms_per_step": round(ms, 4),
             "pass_ms_per_step": {k: round(v / k2, 5) for k, v in pm.items()},
-            "bytes_per_update_survey": 2 * 2 * case.lattice * 2 + 4,
+            "bytes_per_update_2q_pops": 2 * 2 * case.lattice * 2 + 4,
             "error_vs_fp64_oracle": slab_err(storage),
             "error_sample": "32-plane slab of the rock, 10 steps from the "
                             "initial state, max relative population error",

@@ -17,9 +17,10 @@ The experiment it reproduces (a SCAL laboratory test):
   is reported as a negative capillary pressure; the stage stops when a
   further increase barely raises S_w.
 
-S_w is the fraction of fluid nodes with phi < 0 (LBM_SW_COUNT, P:608 of the
-paper); its smooth form (LBM_SW_SMOOTH) is recorded beside it. P_c is the
-imposed pressure difference (the paper's reading: P_c = P_nw - P_w).
+S_w is the fraction of fluid nodes with phi < 0 (LBM_SW_COUNT, as the paper
+defines it in Sec. IV.B); its smooth form (LBM_SW_SMOOTH) is recorded
+beside it. P_c is the imposed pressure difference (the paper's reading:
+P_c = P_nw - P_w).
 
 Drive (Sec. II.C): Type-I sets the Zou-He densities, rho_in = rho_out +
 3 Delta P; Type-II keeps rho_in = rho_out and applies the body acceleration

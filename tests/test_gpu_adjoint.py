@@ -58,7 +58,7 @@ def compare(torch, case, steps, freeze, cmin):
     """Every gradient component within 1e-3 of the FP64 tangent-linear
     value, relative to the size of the gradient it belongs to: theta on its
     own, g as a vector (a component that nearly cancels, like g_x on a
-    drop symmetric in x, is judged against |dJ/dg|). Both sides take the
+    drop symmetric in x, is measured against |dJ/dg|). Both sides take the
     same linearisation (freeze: Scheme-II, cmin: the normal n_c)."""
     from paper_2407_10914_gb300.adjoint import Run
     refs = [tlm(case, steps, a, freeze, cmin)

@@ -194,8 +194,9 @@ def test_one_step_16bit_storage(torch, storage, name, case, dev):
 
 
 def test_droplet_full_run_phase_and_angle(torch):
-    """configs[0]: the D2Q9 droplet, 2000 steps from the sharp initial state
-    on both sides: phase field within 1e-4, contact angle within 0.5 deg."""
+    """The D2Q9 droplet workload (128 x 64, R = 24, Scheme-II at 60 deg):
+    2000 steps from the sharp initial state on both sides; phase field
+    within 1e-4, contact angle within 0.5 deg."""
     case = W.droplet_2d()
     o = oracle_for(case)
     o.step(case.steps)
