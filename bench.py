@@ -69,19 +69,22 @@ def pass_bytes(Q: int, bpp: int) -> dict:
     as 5 x 4 B) and two offsets."""
     tab = (Q - 1) * 4
     return {
-        # T_i of the sources (each once), (q, v) 16 B, table, flags 1 B;
-        # writes f^t (Q planes), (rho^r, rho^b) 8 B, phase field 4 B
-        "stream": Q * bpp + 16 + tab + 1 + Q * bpp + 8 + 4,
+        # T_i of the sources (each once), (q, v) 16 B, table, flags 1 B,
+        # padded index 4 B; writes f^t (Q planes), (rho^r, rho^b) 8 B, the
+        # phase field 4 B and its dense copy 4 B
+        "stream": Q * bpp + 16 + tab + 1 + 4 + Q * bpp + 8 + 4 + 4,
         # U of the node (Q planes), flags, table entry of x - a, phase of
         # that node; at the outlet the colour split of the known
         # populations re-reads about 14 table entries and (q, v); writes
-        # 5 planes, (rho^r, rho^b), phase
-        "zh_fix": Q * bpp + 1 + 4 + 4 + 7 * (4 + 16) + 5 * bpp + 8 + 4,
-        # links + offsets, neighbour phase 4 B; write 4 B
-        "phi_solid": 5 * 4 + 8 + 4 + 4,
-        # table, phase field 4 B, flags, wall normal 16 B (fluid-boundary
-        # nodes, about 45 %: 7 B); write (n_c, |C|) 16 B
-        "gradient": tab + 4 + 1 + 7 + 16,
+        # 5 planes, (rho^r, rho^b), phase and its dense copy (padded index)
+        "zh_fix": Q * bpp + 1 + 4 + 4 + 7 * (4 + 16) + 5 * bpp + 8 + 4 + 8,
+        # links + offsets, neighbour phase 4 B; write 4 B, and the dense
+        # copy (padded index, face bits)
+        "phi_solid": 5 * 4 + 8 + 4 + 4 + 9,
+        # padded index 4 B, the dense phase field 4 B (no table), flags,
+        # wall normal 16 B (fluid-boundary nodes, about 45 %: 7 B); write
+        # (n_c, |C|) 16 B
+        "gradient": 4 + 4 + 1 + 7 + 16,
         # links + offsets, neighbour n_c 16 B; write 16 B
         "nc_solid": 5 * 4 + 8 + 16 + 16,
         # table, (n_c, |C|) 16 B, f^t, (rho^r, rho^b), phase 4 B; writes

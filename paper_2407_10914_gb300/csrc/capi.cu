@@ -45,7 +45,8 @@ long long count_solid(const uint8_t *solid, long long N) {
 // Byte offsets of every buffer inside the caller's workspace.
 struct Layout {
   size_t TA, TB, U, R, SA, SB, mf, ncf, nw, fg, macro;  // F-space
-  size_t ms, ncs, sg;                             // S-space
+  size_t ms, ncs, sg, sgp, sflag;                 // S-space
+  size_t phib, fgp;                               // dense phase field
   size_t nbf, soff, slink, fflag, zh;             // neighbour lookup
   size_t map, cls, mask, fbase, sbase, cntf, cnts, g0, g1;
   size_t red, out, cnt, total;
@@ -91,6 +92,10 @@ Layout make_layout(int Q, int nx, int ny, int nz, int storage, long long NF,
   L.ms = take(nsp * 4);
   L.ncs = take(nsp * 16);
   L.sg = take(nsp * 4);
+  L.sgp = take(nsp * 4);
+  L.sflag = take(nsp);
+  L.fgp = take(nfp * 4);
+  L.phib = take((size_t)(nx + 2) * (ny + 2) * (nz + 2) * 4);
   L.nbf = take((size_t)(Q - 1) * nfp * 4);
   L.soff = take((nsp + 1) * 4);
   L.slink = take((size_t)(Q - 1) * nsp * 4);  // bound: Q - 1 links a node
@@ -117,7 +122,8 @@ bool valid_shape(int lattice, int nx, int ny, int nz) {
   if (nx < 1 || ny < 1 || nz < 1) return false;
   if (lattice == 9 && nz != 1) return false;
   const long long N = (long long)nx * ny * nz;
-  return N < (1LL << 31);  // box indices are stored as int32
+  const long long P = (long long)(nx + 2) * (ny + 2) * (nz + 2);
+  return N < (1LL << 31) && P < (1LL << 31);  // box indices are int32
 }
 
 void swap_buffers(lbm_ctx *c) { lbm::swap_state(c); }
@@ -215,6 +221,12 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
   d.ncf = (float4 *)(base + L.ncf);
   d.ncs = (float4 *)(base + L.ncs);
   d.macro = (float4 *)(base + L.macro);
+  d.phib = (float *)(base + L.phib);
+  d.fgp = (const int *)(base + L.fgp);
+  d.sgp = (const int *)(base + L.sgp);
+  d.sflag = (const uint8_t *)(base + L.sflag);
+  d.px = nx + 2;
+  d.py = ny + 2;
   d.err = (unsigned *)(c->counters + 3);  // zeroed with the counters at set-up
   cudaError_t e = cudaMemcpyAsync(c->mask, solid_host, (size_t)N,
                                   cudaMemcpyHostToDevice, s);

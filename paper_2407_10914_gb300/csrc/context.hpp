@@ -84,6 +84,15 @@ struct Dom {
   float4 *ncf;          // [NF] (n_c, |C|)
   float4 *ncs;          // [NS] (n_c of Eq. 35, 0)
   float4 *macro;        // [NF] (u_x, u_y, u_z, rho) of the last macro step
+  // the phase field again as a dense box with a one-node halo (padded
+  // strides px = nx + 2, py = ny + 2): the gradient stencil reads it at the
+  // node's padded index plus a fixed offset per direction, with no
+  // neighbour-table entry (dense_store keeps the halo)
+  float *phib;          // [(nx + 2)(ny + 2)(nz + 2)]
+  const int *fgp;       // [NF] padded box index of fluid node k
+  const int *sgp;       // [NS] padded box index of solid-boundary node j
+  const uint8_t *sflag; // [NS] face bits as fflag (bits 1 + 2a, 2 + 2a)
+  int px, py;
   unsigned *err;        // error word of the bounds-checked build (guard())
   StepConst c;
 };

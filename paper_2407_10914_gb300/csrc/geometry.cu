@@ -405,6 +405,33 @@ __global__ void k_count_fbnd(Dom d, unsigned long long *__restrict__ c) {
   if (threadIdx.x == 0 && n) atomicAdd(c, (unsigned long long)n);
 }
 
+// Padded box index (one-node halo on every side) of each fluid and
+// solid-boundary node, and the face bits of the solid-boundary nodes (as
+// fflag: bit 1 + 2a on the first plane of axis a, bit 2 + 2a on the last).
+__global__ void k_padded_index(Dom d, int *__restrict__ fgp,
+                               int *__restrict__ sgp,
+                               uint8_t *__restrict__ sflag) {
+  const int k = blockIdx.x * GBLOCK + threadIdx.x;
+  const bool fluid = k < d.NF;
+  if (!fluid && k >= d.NF + d.NS) return;
+  const int g = fluid ? d.fg[k] : d.sg[k - d.NF];
+  int x, y, z;
+  box_coords(d, g, x, y, z);
+  const int gp = (x + 1) + d.px * ((y + 1) + d.py * (z + 1));
+  if (fluid) {
+    fgp[k] = gp;
+    return;
+  }
+  const int c[3] = {x, y, z}, n[3] = {d.nx, d.ny, d.nz};
+  uint8_t f = 0;
+  for (int a = 0; a < 3; ++a) {
+    if (c[a] == 0) f |= (uint8_t)(2u << (2 * a));
+    if (c[a] == n[a] - 1) f |= (uint8_t)(4u << (2 * a));
+  }
+  sgp[k - d.NF] = gp;
+  sflag[k - d.NF] = f;
+}
+
 cudaError_t build_geometry(lbm_ctx *c, cudaStream_t s) {
   Dom &d = c->d;
   const unsigned gN = gblocks(d.N);
@@ -498,6 +525,9 @@ cudaError_t build_geometry(lbm_ctx *c, cudaStream_t s) {
   e = cudaMemsetAsync(c->counters, 0, 4 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
   k_count_fbnd<<<gF, GBLOCK, 0, s>>>(d, c->counters);
+  k_padded_index<<<gblocks((long long)d.NF + d.NS), GBLOCK, 0, s>>>(
+      d, const_cast<int *>(d.fgp), const_cast<int *>(d.sgp),
+      const_cast<uint8_t *>(d.sflag));
   unsigned long long nfb = 0;
   e = cudaMemcpyAsync(&nfb, c->counters, sizeof(nfb), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -40,7 +40,9 @@ __device__ __forceinline__ void stream_node(const Dom &d, int k) {
 #pragma unroll
   for (int i = 0; i < Q; ++i) TIO<Q, ST>::store(d, d.U, i, k, ft[i]);
   d.R[k] = make_float2(rr, rb);
-  d.mf[k] = m_of(rr, rb);
+  const float m = m_of(rr, rb);
+  d.mf[k] = m;
+  dense_store<Q>(d, d.phib, __ldg(d.fgp + k), __ldg(d.fflag + k), m);
 }
 
 // App. B on the Zou-He planes (node jz of their list), after stream_node.
@@ -146,6 +148,7 @@ __device__ __forceinline__ void zh_fix_node(const Dom &d, int jz) {
   }
   d.R[k] = make_float2(rr, rb);
   d.mf[k] = m;
+  dense_store<Q>(d, d.phib, __ldg(d.fgp + k), __ldg(d.fflag + k), m);
 }
 
 // Eq. (34): phi at solid-boundary node j = w-weighted mean over its fluid
@@ -168,7 +171,9 @@ __device__ __forceinline__ void phi_solid_node(const Dom &d, int j) {
   }
   const bool blue = sphi < 0.f;
   const float ex = (blue ? ex_neg : ex_pos) / den;  // phi_s - s
-  d.ms[j] = m_pack(blue, blue ? 0.5f * ex : -0.5f * ex);
+  const float ms = m_pack(blue, blue ? 0.5f * ex : -0.5f * ex);
+  d.ms[j] = ms;
+  dense_store<Q>(d, d.phib, __ldg(d.sgp + j), __ldg(d.sflag + j), ms);
 }
 
 // Eq. (6) (c = dt = 1) and Eq. (27) at fluid node k, with phi(x + e_i) -
@@ -178,14 +183,17 @@ __device__ __forceinline__ void phi_solid_node(const Dom &d, int j) {
 // (no interface).
 template <int Q, bool COH>
 __device__ __forceinline__ void gradient_node(const Dom &d, int k) {
+  // the neighbours' phase from the dense box at fixed offsets (the values
+  // the neighbour table would reach: fluid, solid-boundary, or the halo cell
+  // of a wrapped or clamped neighbour)
+  const int gp = __ldg(d.fgp + k);
   const bool own_blue = m_blue(ldv<COH>(d.mf + k));
   float G[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
-    const uint32_t e = nb_f(d, i, k);
-    const bool fl = entry_cls(e) & 2;
-    const int idx = guard(d, entry_idx(e), fl ? d.NF : d.NS, GUARD_STENCIL);
-    const float m = fl ? ldv<COH>(d.mf + idx) : ldv<COH>(d.ms + idx);
+    const float m = ldv<COH>(d.phib + guard(d, gp + dense_off<Q>(d, i),
+                                            d.px * d.py * (d.nz + 2),
+                                            GUARD_STENCIL));
     const float p = 3.f * Lattice<Q>::w(i) * m_excess(m, own_blue);
     G[0] += (float)Lattice<Q>::ex(i) * p;
     G[1] += (float)Lattice<Q>::ey(i) * p;
@@ -237,6 +245,10 @@ __device__ __forceinline__ void nc_solid_node(const Dom &d, int j) {
 template <int Q, bool COH>
 __device__ __forceinline__ float curvature(const Dom &d, int k, float4 &c4) {
   float dn[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  // through the neighbour table: a dense copy of n_c (as the phase field
+  // has) was measured slower, 0.293 against 0.265 ms for the collision: a
+  // 16-byte gather from the dense box touches about 3.7 times more sectors
+  // than from the compact fluid list on the 256^3 rock
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     const uint32_t e = nb_f(d, i, k);

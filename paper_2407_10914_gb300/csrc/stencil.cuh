@@ -74,6 +74,49 @@ __device__ __forceinline__ int guard(const Dom &d, int idx, int bound,
   return idx;
 }
 
+// ------------------------------------------------------ dense fields
+// A node's value v in a dense box with a one-node halo (padded index gp),
+// and in the halo cells that stand for it: on a periodic axis a node of the
+// first plane is also the cell past the last plane and a node of the last
+// plane the cell before the first; on a non-periodic axis the stencils use
+// the clamped node, so each face node also fills the halo cell beside it.
+// Edge and corner nodes fill every combination. flags: face bits as fflag
+// (bit 1 + 2a first plane, 2 + 2a last plane of axis a). D2Q9 never reads
+// across z, so its z halo is left alone.
+template <int Q, class T>
+__device__ __forceinline__ void dense_store(const Dom &d, T *arr, int gp,
+                                            unsigned flags, T v) {
+  arr[gp] = v;
+  if (!(flags & 0x7Eu)) return;
+  const int stride[3] = {1, d.px, d.px * d.py};
+  const int ext[3] = {d.nx, d.ny, d.nz};
+  int off[3][3], n[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    n[a] = 1;
+    off[a][0] = 0;
+    if (Q == 9 && a == 2) continue;
+    const bool per = d.periodic & (1u << a);
+    if (flags & (2u << (2 * a))) off[a][n[a]++] = per ? ext[a] * stride[a] : -stride[a];
+    if (flags & (4u << (2 * a))) off[a][n[a]++] = per ? -ext[a] * stride[a] : stride[a];
+  }
+  // fixed bounds, fully unrolled: the offsets stay in registers
+#pragma unroll
+  for (int ia = 0; ia < 3; ++ia)
+#pragma unroll
+    for (int ib = 0; ib < 3; ++ib)
+#pragma unroll
+      for (int ic = 0; ic < 3; ++ic)
+        if ((ia | ib | ic) && ia < n[0] && ib < n[1] && ic < n[2])
+          arr[gp + off[0][ia] + off[1][ib] + off[2][ic]] = v;
+}
+
+// Offset of the neighbour x + e_i in the padded box.
+template <int Q>
+__device__ __forceinline__ int dense_off(const Dom &d, int i) {
+  return Lattice<Q>::ex(i) + d.px * (Lattice<Q>::ey(i) + d.py * Lattice<Q>::ez(i));
+}
+
 // ------------------------------------------------------ phase encoding
 // A node's colour split is kept as one float m: the minority fraction
 // mu = min(rho^r, rho^b)/rho with its own sign (it can be slightly negative,
