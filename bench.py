@@ -65,8 +65,8 @@ def pass_bytes(Q: int, bpp: int) -> dict:
     must read and write once (a gathered field counts once per node, since
     every element is read by a fixed number of neighbours that L2 serves).
     Fluid passes read the node's (Q - 1) x 4 B neighbour-table entries;
-    solid-boundary passes their CSR links (4.2 per node on the rock, taken
-    as 5 x 4 B) and two offsets."""
+    the Eq. 35 pass its CSR links (4.2 per node on the rock, taken as
+    5 x 4 B) and two offsets; the Eq. 34 pass a 4 B direction mask."""
     tab = (Q - 1) * 4
     return {
         # T_i of the sources (each once), (q, v) 16 B, table, flags 1 B,
@@ -78,9 +78,10 @@ def pass_bytes(Q: int, bpp: int) -> dict:
         # populations re-reads about 14 table entries and (q, v); writes
         # 5 planes, (rho^r, rho^b), phase and its dense copy (padded index)
         "zh_fix": Q * bpp + 1 + 4 + 4 + 7 * (4 + 16) + 5 * bpp + 8 + 4 + 8,
-        # links + offsets, neighbour phase 4 B; write 4 B, and the dense
-        # copy (padded index, face bits)
-        "phi_solid": 5 * 4 + 8 + 4 + 4 + 9,
+        # direction mask 4 B, padded index 4 B, face bits, the fluid
+        # neighbours' phase from the dense box 4 B; writes the phase 4 B and
+        # its dense copy 4 B
+        "phi_solid": 4 + 4 + 1 + 4 + 4 + 4,
         # padded index 4 B, the dense phase field 4 B (no table), flags,
         # wall normal 16 B (fluid-boundary nodes, about 45 %: 7 B); write
         # (n_c, |C|) 16 B

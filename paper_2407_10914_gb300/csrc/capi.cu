@@ -45,7 +45,7 @@ long long count_solid(const uint8_t *solid, long long N) {
 // Byte offsets of every buffer inside the caller's workspace.
 struct Layout {
   size_t TA, TB, U, R, SA, SB, mf, ncf, nw, fg, macro;  // F-space
-  size_t ms, ncs, sg, sgp, sflag;                 // S-space
+  size_t ms, ncs, sg, sgp, sflag, sdir;           // S-space
   size_t phib, fgp;                               // dense phase field
   size_t nbf, soff, slink, fflag, zh;             // neighbour lookup
   size_t map, cls, mask, fbase, sbase, cntf, cnts, g0, g1;
@@ -94,6 +94,7 @@ Layout make_layout(int Q, int nx, int ny, int nz, int storage, long long NF,
   L.sg = take(nsp * 4);
   L.sgp = take(nsp * 4);
   L.sflag = take(nsp);
+  L.sdir = take(nsp * 4);
   L.fgp = take(nfp * 4);
   L.phib = take((size_t)(nx + 2) * (ny + 2) * (nz + 2) * 4);
   L.nbf = take((size_t)(Q - 1) * nfp * 4);
@@ -225,6 +226,7 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
   d.fgp = (const int *)(base + L.fgp);
   d.sgp = (const int *)(base + L.sgp);
   d.sflag = (const uint8_t *)(base + L.sflag);
+  d.sdir = (const uint32_t *)(base + L.sdir);
   d.px = nx + 2;
   d.py = ny + 2;
   d.err = (unsigned *)(c->counters + 3);  // zeroed with the counters at set-up

@@ -92,6 +92,9 @@ struct Dom {
   const int *fgp;       // [NF] padded box index of fluid node k
   const int *sgp;       // [NS] padded box index of solid-boundary node j
   const uint8_t *sflag; // [NS] face bits as fflag (bits 1 + 2a, 2 + 2a)
+  // [NS] bit i set when x + e_i of solid-boundary node j is a fluid node:
+  // the directions of its links, so that Eq. 34 reads the dense box
+  const uint32_t *sdir;
   int px, py;
   unsigned *err;        // error word of the bounds-checked build (guard())
   StepConst c;

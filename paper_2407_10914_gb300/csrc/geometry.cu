@@ -287,13 +287,15 @@ __global__ void k_build_nbr(Dom d, uint32_t *__restrict__ nbf,
 // written from off[j] on as F-index | (diagonal direction) << 31.
 template <int Q>
 __global__ void k_s_links(Dom d, const int *__restrict__ off,
-                          uint32_t *__restrict__ links, int *__restrict__ cnt) {
+                          uint32_t *__restrict__ links, int *__restrict__ cnt,
+                          uint32_t *__restrict__ dirs) {
   const int j = blockIdx.x * GBLOCK + threadIdx.x;
   if (j >= d.NS) return;
   int x, y, z;
   box_coords(d, d.sg[j], x, y, z);
   const int at = links ? off[j] : 0;
   int n = 0;
+  uint32_t mask = 0;
   for (int i = 1; i < Q; ++i) {
     bool out = false;
     const int X = axis_step(x + Lattice<Q>::ex(i), d.nx, d.periodic & 1u, false, out);
@@ -305,9 +307,13 @@ __global__ void k_s_links(Dom d, const int *__restrict__ off,
     if (links)
       links[at + n] = (uint32_t)entry_idx(e) |
                       (Lattice<Q>::w(i) < Lattice<Q>::w(1) ? 0x80000000u : 0u);
+    mask |= 1u << i;
     ++n;
   }
-  if (!links) cnt[j] = n;
+  if (links)
+    dirs[j] = mask;
+  else
+    cnt[j] = n;
 }
 
 // Fluid node k on the first or last plane of axis a (a Zou-He plane).
@@ -499,18 +505,19 @@ cudaError_t build_geometry(lbm_ctx *c, cudaStream_t s) {
   const unsigned gS = gblocks(d.NS);
   int *soff = const_cast<int *>(d.soff);
   uint32_t *slink = const_cast<uint32_t *>(d.slink);
+  uint32_t *sdir = const_cast<uint32_t *>(d.sdir);
   if (d.NS > 0) {
     if (c->Q == 19)
-      k_s_links<19><<<gS, GBLOCK, 0, s>>>(d, nullptr, nullptr, cnt);
+      k_s_links<19><<<gS, GBLOCK, 0, s>>>(d, nullptr, nullptr, cnt, nullptr);
     else
-      k_s_links<9><<<gS, GBLOCK, 0, s>>>(d, nullptr, nullptr, cnt);
+      k_s_links<9><<<gS, GBLOCK, 0, s>>>(d, nullptr, nullptr, cnt, nullptr);
   }
   scan_exclusive(cnt, soff, d.NS, bsum, s);
   if (d.NS > 0) {
     if (c->Q == 19)
-      k_s_links<19><<<gS, GBLOCK, 0, s>>>(d, soff, slink, nullptr);
+      k_s_links<19><<<gS, GBLOCK, 0, s>>>(d, soff, slink, nullptr, sdir);
     else
-      k_s_links<9><<<gS, GBLOCK, 0, s>>>(d, soff, slink, nullptr);
+      k_s_links<9><<<gS, GBLOCK, 0, s>>>(d, soff, slink, nullptr, sdir);
   }
   // the Zou-He planes' fluid nodes per axis, in F order
   int zh_n[3] = {0, 0, 0};

@@ -156,14 +156,19 @@ __device__ __forceinline__ void zh_fix_node(const Dom &d, int jz) {
 // sign s of the mean.
 template <int Q, bool COH>
 __device__ __forceinline__ void phi_solid_node(const Dom &d, int j) {
+  // the fluid neighbours' phase from the dense box at fixed offsets, in
+  // the order of the node's links (ascending direction): one round of
+  // independent loads instead of a walk over the link list
+  const uint32_t dirs = __ldg(d.sdir + j);
+  const int gp = __ldg(d.sgp + j);
   float den = 0.f, sphi = 0.f, ex_pos = 0.f, ex_neg = 0.f;
-  const int e = __ldg(d.soff + j + 1);
-  for (int p = __ldg(d.soff + j); p < e; ++p) {
-    const uint32_t l =
-        __ldg(d.slink + guard(d, p, (Q - 1) * d.NS, GUARD_LINK));
-    const float w = link_w<Q>(l);
-    const float m =
-        ldv<COH>(d.mf + guard(d, (int)(l & 0x7FFFFFFFu), d.NF, GUARD_LINK));
+#pragma unroll
+  for (int i = 1; i < Q; ++i) {
+    if (!(dirs & (1u << i))) continue;
+    const float w = Lattice<Q>::w(i);
+    const float m = ldv<COH>(d.phib + guard(d, gp + dense_off<Q>(d, i),
+                                            d.px * d.py * (d.nz + 2),
+                                            GUARD_STENCIL));
     den += w;
     sphi += w * m_phi(m);
     ex_pos += w * m_excess(m, false);
