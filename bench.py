@@ -60,22 +60,24 @@ METRIC = "MLUPS & % HBM roofline: plain FP32 vs FP16-storage/batched at stated e
 BYTES_POP = {"fp32": 4, "fp16": 2, "bf16": 2}
 
 
-def pass_bytes(Q: int, bpp: int) -> dict:
+def pass_bytes(Q: int, bpp: int, ent: float) -> dict:
     """Algorithmic DRAM bytes per processed node of each pass: what the pass
     must read and write once (a gathered field counts once per node, since
     every element is read by a fixed number of neighbours that L2 serves).
-    Fluid passes read the node's (Q - 1) x 4 B neighbour-table entries;
-    the Eq. 35 pass its CSR links (4.2 per node on the rock, taken as
-    5 x 4 B) and two offsets; the Eq. 34 pass a 4 B direction mask."""
-    tab = (Q - 1) * 4
+    Fluid passes find their neighbours in the dense entry box, 4 B per cell
+    of the padded box, read once per pass: `ent` = 4 x cells / fluid nodes
+    bytes per fluid node (15 on the 256^3 rock); the Eq. 35 pass reads its
+    CSR links (4.2 per node on the rock, taken as 5 x 4 B) and two offsets;
+    the Eq. 34 pass a 4 B direction mask."""
+    ent = round(ent, 1)
     return {
-        # T_i of the sources (each once), (q, v) 16 B, table, flags 1 B,
-        # padded index 4 B; writes f^t (Q planes), (rho^r, rho^b) 8 B, the
-        # phase field 4 B and its dense copy 4 B
-        "stream": Q * bpp + 16 + tab + 1 + 4 + Q * bpp + 8 + 4 + 4,
-        # U of the node (Q planes), flags, table entry of x - a, phase of
+        # T_i of the sources (each once), (q, v) 16 B, the entries, flags
+        # 1 B, padded index 4 B; writes f^t (Q planes), (rho^r, rho^b) 8 B,
+        # the phase field 4 B and its dense copy 4 B
+        "stream": Q * bpp + 16 + ent + 1 + 4 + Q * bpp + 8 + 4 + 4,
+        # U of the node (Q planes), flags, the entry of x - a, phase of
         # that node; at the outlet the colour split of the known
-        # populations re-reads about 14 table entries and (q, v); writes
+        # populations re-reads about 14 entries and (q, v); writes
         # 5 planes, (rho^r, rho^b), phase and its dense copy (padded index)
         "zh_fix": Q * bpp + 1 + 4 + 4 + 7 * (4 + 16) + 5 * bpp + 8 + 4 + 8,
         # direction mask 4 B, padded index 4 B, face bits, the fluid
@@ -88,9 +90,9 @@ def pass_bytes(Q: int, bpp: int) -> dict:
         "gradient": 4 + 4 + 1 + 7 + 16,
         # links + offsets, neighbour n_c 16 B; write 16 B
         "nc_solid": 5 * 4 + 8 + 16 + 16,
-        # table, (n_c, |C|) 16 B, f^t, (rho^r, rho^b), phase 4 B; writes
-        # f'' (Q planes) and (q, v) 16 B
-        "collide": tab + 16 + Q * bpp + 8 + 4 + Q * bpp + 16,
+        # padded index 4 B, the entries, (n_c, |C|) 16 B, f^t,
+        # (rho^r, rho^b), phase 4 B; writes f'' (Q planes) and (q, v) 16 B
+        "collide": 4 + ent + 16 + Q * bpp + 8 + 4 + Q * bpp + 16,
     }
 
 
@@ -350,7 +352,9 @@ def run_ours(args):
     k2 = max(1, min(args.steps, 200))
     pass_ms = s.step_timed(k2)
     bpp = BYTES_POP[args.storage]
-    pb = pass_bytes(Q, bpp)
+    gz, gy, gx = case.solid.shape
+    cells = (gx + 2) * (gy + 2) * (gz + 2 if Q == 19 else 1)
+    pb = pass_bytes(Q, bpp, 4.0 * cells / nf)
     n_zh = s.n_zou_he
     n_of = {"stream": nf, "zh_fix": n_zh, "phi_solid": n_sbnd, "gradient": nf,
             "nc_solid": n_sbnd, "collide": nf}

@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(ABLOCK) k_adj_collide(Dom d, Adj a) {
     float dn[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-      const uint32_t e = nb_f(d, i, k);
+      const uint32_t e = nb_f<Q>(d, i, k);
       const int idx = entry_idx(e);
       const float4 v = (entry_cls(e) & 2) ? d.ncf[idx] : d.ncs[idx];
       const float w3 = 3.f * Lattice<Q>::w(i);
@@ -243,7 +243,7 @@ __global__ void __launch_bounds__(ABLOCK) k_adj_collide(Dom d, Adj a) {
                              (float)Lattice<Q>::ez(i)};
         const float en = e3[0] * n[0] + e3[1] * n[1] + e3[2] * n[2];
         const float c3 = 3.f * Lattice<Q>::w(i) * lkappa;
-        const uint32_t e = nb_f(d, i, k);
+        const uint32_t e = nb_f<Q>(d, i, k);
         const int idx = entry_idx(e);
         float4 *dst = (entry_cls(e) & 2) ? a.ln + idx : a.lns + idx;
         atomic_add3(dst, c3 * (n[0] * en - e3[0]), c3 * (n[1] * en - e3[1]),
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(ABLOCK) k_adj_gradient(Dom d, Adj a) {
     float G[3] = {0.f, 0.f, 0.f};
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
-      const uint32_t e = nb_f(d, i, k);
+      const uint32_t e = nb_f<Q>(d, i, k);
       const int idx = entry_idx(e);
       const float m = (entry_cls(e) & 2) ? d.mf[idx] : d.ms[idx];
       const float p = 3.f * Lattice<Q>::w(i) * m_excess(m, own_blue);
@@ -366,7 +366,7 @@ __global__ void __launch_bounds__(ABLOCK) k_adj_gradient(Dom d, Adj a) {
         const float v = 3.f * Lattice<Q>::w(i) *
                         ((float)Lattice<Q>::ex(i) * lC[0] + (float)Lattice<Q>::ey(i) * lC[1] +
                          (float)Lattice<Q>::ez(i) * lC[2]);
-        const uint32_t e = nb_f(d, i, k);
+        const uint32_t e = nb_f<Q>(d, i, k);
         const int idx = entry_idx(e);
         atomicAdd((entry_cls(e) & 2) ? a.lphi + idx : a.lphis + idx, v);
       }
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(ABLOCK) k_adj_stream(Dom d, Adj a) {
   for (int k = 0; k < Q; ++k) {
     int x = y, i = 0;
     if (k > 0) {
-      const uint32_t e = nb_f(d, k, y);
+      const uint32_t e = nb_f<Q>(d, k, y);
       const bool fl = (entry_cls(e) & 2) && !entry_out(e);
       x = fl ? entry_idx(e) : y;
       i = fl ? k : Lattice<Q>::opp(k);

@@ -47,7 +47,7 @@ struct Layout {
   size_t TA, TB, U, R, SA, SB, mf, ncf, nw, fg, macro;  // F-space
   size_t ms, ncs, sg, sgp, sflag, sdir;           // S-space
   size_t phib, fgp;                               // dense phase field
-  size_t nbf, soff, slink, fflag, zh;             // neighbour lookup
+  size_t nbd, soff, slink, fflag, zh;             // neighbour lookup
   size_t map, cls, mask, fbase, sbase, cntf, cnts, g0, g1;
   size_t red, out, cnt, total;
   long long NF, NFp, NS, ntiles;
@@ -97,7 +97,7 @@ Layout make_layout(int Q, int nx, int ny, int nz, int storage, long long NF,
   L.sdir = take(nsp * 4);
   L.fgp = take(nfp * 4);
   L.phib = take((size_t)(nx + 2) * (ny + 2) * (nz + 2) * 4);
-  L.nbf = take((size_t)(Q - 1) * nfp * 4);
+  L.nbd = take((size_t)(nx + 2) * (ny + 2) * (nz + 2) * 4);
   L.soff = take((nsp + 1) * 4);
   L.slink = take((size_t)(Q - 1) * nsp * 4);  // bound: Q - 1 links a node
   L.fflag = take(nfp);
@@ -203,7 +203,7 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
   d.fg = (const int *)(base + L.fg);
   d.sg = (const int *)(base + L.sg);
   d.cls = (const uint8_t *)(base + L.cls);
-  d.nbf = (const uint32_t *)(base + L.nbf);
+  d.nbd = (const uint32_t *)(base + L.nbd);
   d.soff = (const int *)(base + L.soff);
   d.slink = (const uint32_t *)(base + L.slink);
   d.fflag = (const uint8_t *)(base + L.fflag);

@@ -60,9 +60,12 @@ struct Dom {
   const int *fg;        // [NF] box index of fluid node k
   const int *sg;        // [NS] box index of solid-boundary node j
   const uint8_t *cls;   // [N]
-  // neighbour tables, one plane per direction i = 1..Q-1 (plane i - 1),
-  // entry = class << 30 | OUT << 29 | index (see tiles.cuh)
-  const uint32_t *nbf;  // [Q-1][NFp] of the fluid nodes
+  // lattice-neighbour entries over the padded box (strides px, py): the
+  // cell at padded position x + 1 holds class << 30 | OUT << 29 | index of
+  // the node x reaches, after wrapping the periodic axes and clamping the
+  // others (OUT set where it clamped); a fluid node reads its neighbours at
+  // its padded index plus a fixed offset per direction (see tiles.cuh)
+  const uint32_t *nbd;  // [(nx + 2)(ny + 2)(nz + 2)]
   // fluid lattice neighbours of the solid-boundary nodes (the terms of
   // Eqs. 34-35), node j's at [soff[j], soff[j+1]): F-index, bit 31 set for
   // a diagonal direction (weight w_diag instead of w_axis)

@@ -240,45 +240,52 @@ __global__ void k_tile_map(Dom d, uint16_t *__restrict__ map,
   }
 }
 
-// One block per tile: the neighbour tables of the tile's fluid nodes, from
-// the staged tile table. An off-box neighbour on a non-periodic axis gets
-// the entry of the clamped position with the OUT bit. Node flags: bit 0
-// fluid-boundary; bit 1 + 2a / 2 + 2a the first / last plane along axis a.
-template <int Q>
-__global__ void k_build_nbr(Dom d, uint32_t *__restrict__ nbf,
-                            uint8_t *__restrict__ fflag) {
-  using G = TileGeo<Q>;
-  __shared__ uint32_t tab[G::HN];
-  __shared__ uint16_t fpos[G::TN];
-  __shared__ uint16_t spos[G::TN];
-  const int t = blockIdx.x;
-  const int fb0 = d.fbase[t], nf = d.fbase[t + 1] - fb0;
-  if (nf == 0) return;
-  int X0, Y0, Z0;
-  stage_tile<Q>(d, t, tab, fpos, spos, X0, Y0, Z0);
-  for (int r = threadIdx.x; r < nf; r += GBLOCK) {
-    int x, y, z, p0;
-    local_node<Q>(fpos[r], X0, Y0, Z0, x, y, z, p0);
-    for (int i = 1; i < Q; ++i) {
-      const int dx = Lattice<Q>::ex(i), dy = Lattice<Q>::ey(i),
-                dz = Lattice<Q>::ez(i);
-      uint32_t e = tab[p0 + G::off(dx, dy, dz)];
-      if (e == ENTRY_OUT) {
-        const int cx = (x + dx < 0 || x + dx >= d.nx) ? 0 : dx;
-        const int cy = (y + dy < 0 || y + dy >= d.ny) ? 0 : dy;
-        const int cz = (z + dz < 0 || z + dz >= d.nz) ? 0 : dz;
-        e = tab[p0 + G::off(cx, cy, cz)] | OUT_BIT;
-      }
-      nbf[(long long)(i - 1) * d.NFp + fb0 + r] = e;
-    }
-    uint8_t f = entry_cls(tab[p0]) == CLS_FLUID_BND ? 1u : 0u;
-    const int c[3] = {x, y, z}, n[3] = {d.nx, d.ny, d.nz};
-    for (int a = 0; a < 3; ++a) {
-      if (c[a] == 0) f |= (uint8_t)(2u << (2 * a));
-      if (c[a] == n[a] - 1) f |= (uint8_t)(4u << (2 * a));
-    }
-    fflag[fb0 + r] = f;
+// Flags of fluid node k: bit 0 fluid-boundary; bit 1 + 2a / 2 + 2a on the
+// first / last plane along axis a.
+__global__ void k_fluid_flags(Dom d, uint8_t *__restrict__ fflag) {
+  const int k = blockIdx.x * GBLOCK + threadIdx.x;
+  if (k >= d.NF) return;
+  const int g = d.fg[k];
+  int x, y, z;
+  box_coords(d, g, x, y, z);
+  uint8_t f = d.cls[g] == CLS_FLUID_BND ? 1u : 0u;
+  const int c[3] = {x, y, z}, n[3] = {d.nx, d.ny, d.nz};
+  for (int a = 0; a < 3; ++a) {
+    if (c[a] == 0) f |= (uint8_t)(2u << (2 * a));
+    if (c[a] == n[a] - 1) f |= (uint8_t)(4u << (2 * a));
   }
+  fflag[k] = f;
+}
+
+// One thread per cell of the padded box: the entry of the node that the
+// lattice position x (padded position x + 1) stands for. A periodic axis
+// wraps; on a non-periodic one an off-box coordinate is clamped to the face
+// (the stencils' zero-gradient rule) and the OUT bit is set (the pull
+// bounces back, the extrapolations skip it). Since x + e_i, clamped, is x
+// or one of its lattice neighbours, a fluid node only ever reaches fluid
+// or solid-boundary entries.
+template <int Q>
+__global__ void k_dense_entries(Dom d, uint32_t *__restrict__ nbd) {
+  const long long p = (long long)blockIdx.x * GBLOCK + threadIdx.x;
+  if (p >= (long long)d.px * d.py * (d.nz + 2)) return;
+  const int hx = (int)(p % d.px);
+  const long long r = p / d.px;
+  const int hy = (int)(r % d.py);
+  const int hz = (int)(r / d.py);
+  int c[3] = {hx - 1, hy - 1, hz - 1};
+  const int n[3] = {d.nx, d.ny, d.nz};
+  bool out = false;
+  for (int a = 0; a < 3; ++a) {
+    if (c[a] >= 0 && c[a] < n[a]) continue;
+    if (d.periodic & (1u << a)) {
+      c[a] = c[a] < 0 ? n[a] - 1 : 0;
+    } else {
+      c[a] = c[a] < 0 ? 0 : n[a] - 1;
+      out = true;
+    }
+  }
+  const uint32_t e = box_entry<Q>(d, c[0], c[1], c[2]);
+  nbd[p] = out ? (e | OUT_BIT) : e;
 }
 
 // One thread per solid-boundary node: its fluid lattice neighbours that are
@@ -472,12 +479,14 @@ cudaError_t build_geometry(lbm_ctx *c, cudaStream_t s) {
   c->n_fluid = tot[0];
   c->n_sbnd = tot[1];
   {
-    uint32_t *nbf = const_cast<uint32_t *>(d.nbf);
-    uint8_t *ff = const_cast<uint8_t *>(d.fflag);
+    uint32_t *nbd = const_cast<uint32_t *>(d.nbd);
+    const long long P = (long long)d.px * d.py * (d.nz + 2);
+    k_fluid_flags<<<gblocks(d.NF), GBLOCK, 0, s>>>(
+        d, const_cast<uint8_t *>(d.fflag));
     if (c->Q == 19)
-      k_build_nbr<19><<<nt, GBLOCK, 0, s>>>(d, nbf, ff);
+      k_dense_entries<19><<<gblocks(P), GBLOCK, 0, s>>>(d, nbd);
     else
-      k_build_nbr<9><<<nt, GBLOCK, 0, s>>>(d, nbf, ff);
+      k_dense_entries<9><<<gblocks(P), GBLOCK, 0, s>>>(d, nbd);
   }
   // Eq. (25) three times, then Eq. (26) at the fluid-boundary nodes
   k_indicator<<<gN, GBLOCK, 0, s>>>(d.N, c->mask, c->g0);

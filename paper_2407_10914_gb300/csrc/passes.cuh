@@ -11,17 +11,19 @@
 //   collide_node    (fluid)  Eq. (12), (5), (36); Eq. (2) single-rate on
 //                   the stored f^t; stores f'' and (q, v), the recoloured
 //                   state of Eqs. (20)-(21).
-// Every lattice neighbour of a fluid node is one entry of its precomputed
-// neighbour table (geometry.cu). COH selects loads that bypass L1 for the
-// values that change within a step (see ldv).
+// Every lattice neighbour of a fluid node is one read of the dense entry box
+// (geometry.cu) at the node's padded index plus a fixed offset. COH selects
+// loads that bypass L1 for the values that change within a step (see ldv).
 #pragma once
 
 #include "tiles.cuh"
 
 namespace lbm {
 
+// Entry of the lattice neighbour x + e_dir of fluid node k.
+template <int Q>
 __device__ __forceinline__ uint32_t nb_f(const Dom &d, int dir, int k) {
-  return __ldg(d.nbf + (long long)(dir - 1) * d.NFp + k);
+  return nb_entry<Q>(d, __ldg(d.fgp + k), dir);
 }
 
 // Weight of a solid-boundary link (bit 31: diagonal direction).
@@ -36,13 +38,14 @@ __device__ __forceinline__ float link_w(uint32_t l) {
 template <int Q, int ST, bool COH>
 __device__ __forceinline__ void stream_node(const Dom &d, int k) {
   float ft[Q], rr, rb;
-  pull_sums<Q, ST, COH>(d, k, ldv<COH>(d.S_src + k), ft, rr, rb);
+  const int gp = __ldg(d.fgp + k);
+  pull_sums<Q, ST, COH>(d, k, gp, ldv<COH>(d.S_src + k), ft, rr, rb);
 #pragma unroll
   for (int i = 0; i < Q; ++i) TIO<Q, ST>::store(d, d.U, i, k, ft[i]);
   d.R[k] = make_float2(rr, rb);
   const float m = m_of(rr, rb);
   d.mf[k] = m;
-  dense_store<Q>(d, d.phib, __ldg(d.fgp + k), __ldg(d.fflag + k), m);
+  dense_store<Q>(d, d.phib, gp, __ldg(d.fflag + k), m);
 }
 
 // App. B on the Zou-He planes (node jz of their list), after stream_node.
@@ -67,6 +70,7 @@ __device__ __forceinline__ void zh_fix_node(const Dom &d, int jz) {
   // through the read-only path
   using IO = TIO<Q, ST, true>;
   const int k = guard(d, __ldg(d.zh_list + jz), d.NF, GUARD_ZOU_HE);
+  const int gp = __ldg(d.fgp + k);
   const int a = d.c.axis;
   const bool inlet = __ldg(d.fflag + k) & (2u << (2 * a));
   const int in_dir = inlet ? -1 : 1;  // e.a of the known, inward populations
@@ -102,7 +106,10 @@ __device__ __forceinline__ void zh_fix_node(const Dom &d, int jz) {
     m = d.c.m_in;
   } else {
     jt = (K0d + 2.f * Kind) - (d.c.rho_out - d.c.rho0);
-    const uint32_t e = nb_f(d, 2 * a + 2, k);  // the node at x - a
+    // the node at x - a
+    const int sa = a == 0 ? 1 : (a == 1 ? d.px : d.px * d.py);
+    const uint32_t e = __ldg(
+        d.nbd + guard(d, gp - sa, d.px * d.py * (d.nz + 2), GUARD_ZOU_HE));
     const float2 Rk = ldv<true>(d.R + k);
     m = ((entry_cls(e) & 2) && !entry_out(e))
             ? ldv<COH>(d.mf + guard(d, entry_idx(e), d.NF, GUARD_ZOU_HE))
@@ -118,7 +125,7 @@ __device__ __forceinline__ void zh_fix_node(const Dom &d, int jz) {
       if (i == 0) {
         rebuild<Q>(ft[0], Sown, 0, fr, fb);
       } else {
-        const uint32_t es = nb_f(d, Lattice<Q>::opp(i), k);
+        const uint32_t es = nb_entry<Q>(d, gp, Lattice<Q>::opp(i));
         const bool fl = (entry_cls(es) & 2) && !entry_out(es);
         const float4 S =
             fl ? ldv<COH>(d.S_src + guard(d, entry_idx(es), d.NF, GUARD_ZOU_HE))
@@ -148,7 +155,7 @@ __device__ __forceinline__ void zh_fix_node(const Dom &d, int jz) {
   }
   d.R[k] = make_float2(rr, rb);
   d.mf[k] = m;
-  dense_store<Q>(d, d.phib, __ldg(d.fgp + k), __ldg(d.fflag + k), m);
+  dense_store<Q>(d, d.phib, gp, __ldg(d.fflag + k), m);
 }
 
 // Eq. (34): phi at solid-boundary node j = w-weighted mean over its fluid
@@ -188,9 +195,9 @@ __device__ __forceinline__ void phi_solid_node(const Dom &d, int j) {
 // (no interface).
 template <int Q, bool COH>
 __device__ __forceinline__ void gradient_node(const Dom &d, int k) {
-  // the neighbours' phase from the dense box at fixed offsets (the values
-  // the neighbour table would reach: fluid, solid-boundary, or the halo cell
-  // of a wrapped or clamped neighbour)
+  // the neighbours' phase from the dense box at fixed offsets (the nodes the
+  // dense entry box names: fluid, solid-boundary, or the halo cell of a
+  // wrapped or clamped neighbour)
   const int gp = __ldg(d.fgp + k);
   const bool own_blue = m_blue(ldv<COH>(d.mf + k));
   float G[3] = {0.f, 0.f, 0.f};
@@ -250,13 +257,14 @@ __device__ __forceinline__ void nc_solid_node(const Dom &d, int j) {
 template <int Q, bool COH>
 __device__ __forceinline__ float curvature(const Dom &d, int k, float4 &c4) {
   float dn[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
-  // through the neighbour table: a dense copy of n_c (as the phase field
-  // has) was measured slower, 0.293 against 0.265 ms for the collision: a
-  // 16-byte gather from the dense box touches about 3.7 times more sectors
-  // than from the compact fluid list on the 256^3 rock
+  // n_c from the compact lists through the dense entry box: a dense copy of
+  // n_c (as the phase field has) was measured slower, 0.293 against 0.265 ms
+  // for the collision: a 16-byte gather from the dense box touches about 3.7
+  // times more sectors than from the compact fluid list on the 256^3 rock
+  const int gp = __ldg(d.fgp + k);
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
-    const uint32_t e = nb_f(d, i, k);
+    const uint32_t e = nb_entry<Q>(d, gp, i);
     const bool fl = entry_cls(e) & 2;
     const int idx = guard(d, entry_idx(e), fl ? d.NF : d.NS, GUARD_STENCIL);
     const float4 v = fl ? ldv<COH>(d.ncf + idx) : ldv<COH>(d.ncs + idx);

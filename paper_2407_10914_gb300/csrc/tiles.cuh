@@ -1,4 +1,5 @@
-// Tiles of the box and the shared-memory neighbour table.
+// Tiles of the box, the entries that name a box position's node, and the
+// pull of Eq. (1).
 //
 // The box is cut into tiles of TX x TY x TZ nodes (32 x 8 x 8 for D3Q19,
 // 64 x 32 x 1 for D2Q9). Fluid nodes are numbered tile by tile (F-space),
@@ -8,10 +9,12 @@
 // and its rank among the nodes of its kind in its tile (bits 0-13); with the
 // per-tile bases fbase/sbase this gives its F- or S-index.
 //
-// One CTA works on one tile. It first stages, for the tile and a one-node
-// halo, an entry (class << 30 | index) per box position in shared memory
-// (OUT for a position off a non-periodic axis). Every lattice neighbour of a
-// tile node is then one shared-memory read at a compile-time offset.
+// At set-up one CTA works on one tile: it stages, for the tile and a
+// one-node halo, an entry (class << 30 | index) per box position in shared
+// memory (OUT for a position off a non-periodic axis). In the step, a fluid
+// node finds its lattice neighbours in the dense entry box (one entry per
+// cell of the box padded by one node; geometry.cu), at its padded index
+// plus a compile-time offset per direction.
 #pragma once
 
 #include "stencil.cuh"
@@ -51,10 +54,10 @@ struct TileGeo {
 };
 
 // Entries: class << 30 | index (index < 2^29). A staged position off a
-// non-periodic axis holds ENTRY_OUT. In the per-node neighbour tables an
-// off-box neighbour holds the entry of the clamped position (the stencils'
-// zero-gradient rule) with the OUT bit set (the pull bounces back, the
-// extrapolations skip it).
+// non-periodic axis holds ENTRY_OUT. In the dense entry box a halo cell off
+// a non-periodic axis holds the entry of the clamped position (the stencils'
+// zero-gradient rule; periodic axes wrap) with the OUT bit set (the pull
+// bounces back, the extrapolations skip it).
 constexpr uint32_t ENTRY_OUT = 0x3FFFFFFFu;  // class 0, staging only
 constexpr uint32_t OUT_BIT = 1u << 29;
 __device__ __forceinline__ int entry_cls(uint32_t e) { return (int)(e >> 30); }
@@ -159,39 +162,25 @@ __device__ __forceinline__ uint32_t clamped_entry(const Dom &d,
   return e;
 }
 
-// Eq. (1) propagation through the neighbour table: f^s_i(x) = f^s_i'(x - e_i)
-// from a fluid source (entry of direction opp(i), which points to x - e_i),
-// else the halfway bounce-back f^s_opp(i)'(x).
-template <int Q, int ST, bool COH = false>
-__device__ __forceinline__ void pull_nb(const Dom &d, int k, float4 Sown,
-                                        float *fr, float *fb) {
-  using IO = TIO<Q, ST, COH>;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    if (i == 0) {
-      rebuild<Q>(IO::load(d, 0, k), Sown, 0, fr[0], fb[0]);
-      continue;
-    }
-    const uint32_t e =
-        __ldg(d.nbf + (long long)(Lattice<Q>::opp(i) - 1) * d.NFp + k);
-    const bool fl = (entry_cls(e) & 2) && !entry_out(e);
-    const int src = guard(d, fl ? entry_idx(e) : k, d.NF, GUARD_PULL);
-    const float T = IO::load_dyn(d, fl ? i : Lattice<Q>::opp(i), src);
-    const float4 S = fl ? ldv<COH>(d.S_src + src) : Sown;
-    const float ev = (float)Lattice<Q>::ex(i) * S.y +
-                     (float)Lattice<Q>::ey(i) * S.z +
-                     (float)Lattice<Q>::ez(i) * S.w;
-    rebuild_ev<Q>(T, S.x, fl ? ev : -ev, i, fr[i], fb[i]);
-  }
+// Entry of the lattice neighbour x + e_dir of the fluid node at padded box
+// index gp (the dense entry box: the same cell for every node that reaches
+// that position, so the reads of neighbouring nodes share cache lines).
+template <int Q>
+__device__ __forceinline__ uint32_t nb_entry(const Dom &d, int gp, int dir) {
+  return __ldg(d.nbd + guard(d, gp + dense_off<Q>(d, dir),
+                             d.px * d.py * (d.nz + 2), GUARD_STENCIL));
 }
 
-// The same pull reduced to what the collision needs away from Zou-He
-// planes: f^t_i = f^r_i + f^b_i (which is f''_i of the source, no colour
-// rebuild) and the colour densities rho^r, rho^b (the rebuilt colours
-// summed as they arrive), so no per-colour arrays stay live.
+// Eq. (1) propagation of fluid node k (padded index gp): f^s_i(x) =
+// f^s_i'(x - e_i) from a fluid source (the entry of direction opp(i), which
+// points to x - e_i), else the halfway bounce-back f^s_opp(i)'(x). Kept is
+// what the collision needs: f^t_i = f^r_i + f^b_i (which is f''_i of the
+// source, no colour rebuild) and the colour densities rho^r, rho^b (the
+// rebuilt colours summed as they arrive), so no per-colour arrays stay live.
 template <int Q, int ST, bool COH = false>
-__device__ __forceinline__ void pull_sums(const Dom &d, int k, float4 Sown,
-                                          float *ft, float &rr, float &rb) {
+__device__ __forceinline__ void pull_sums(const Dom &d, int k, int gp,
+                                          float4 Sown, float *ft, float &rr,
+                                          float &rb) {
   using IO = TIO<Q, ST, COH>;
   rr = 0.f;
   rb = 0.f;
@@ -202,8 +191,7 @@ __device__ __forceinline__ void pull_sums(const Dom &d, int k, float4 Sown,
       ft[0] = IO::load(d, 0, k);
       rebuild<Q>(ft[0], Sown, 0, fr, fb);
     } else {
-      const uint32_t e =
-          __ldg(d.nbf + (long long)(Lattice<Q>::opp(i) - 1) * d.NFp + k);
+      const uint32_t e = nb_entry<Q>(d, gp, Lattice<Q>::opp(i));
       const bool fl = (entry_cls(e) & 2) && !entry_out(e);
       const int src = guard(d, fl ? entry_idx(e) : k, d.NF, GUARD_PULL);
       ft[i] = IO::load_dyn(d, fl ? i : Lattice<Q>::opp(i), src);

@@ -81,7 +81,27 @@ def cases():
     out.append(("droplet3d_schemeII", c, 120))
     c = W.laplace_drop(19, 24, 6.0, tau_r=1.0, tau_b=0.6)
     out.append(("laplace3d_periodic", c, 100))
+    out.append(("zou_he_periodic_edges", edge_drop(), 40))
     return out
+
+
+def edge_drop(shape=(14, 18, 24), radius=5.0):
+    """A red drop centred on the edge where the Zou-He outlet plane (x = nx-1,
+    non-periodic) meets the periodic y faces: the stencils there reach
+    positions that are off the box on both axes, which wrap on y and clamp
+    on x (reading 13 of the off-box rule), so n_c and the curvature at the
+    edge nodes come from the far side of the y period."""
+    nz, ny, nx = shape
+    z, y, x = np.mgrid[0:nz, 0:ny, 0:nx].astype(np.float64)
+    dy = np.minimum(y, ny - y)  # distance to the plane y = 0 across the period
+    r2 = (x - (nx - 1)) ** 2 + dy ** 2 + (z - nz / 2.0) ** 2
+    phi0 = np.tanh((radius - np.sqrt(r2)) / 1.5)
+    solid = np.zeros(shape, np.uint8)
+    p = W.base_params(tau_r=1.0, tau_b=0.8, gamma=0.01, beta=0.95,
+                      zou_he=1, flow_axis=0, rho_in=1.0, rho_out=1.0,
+                      zeta_r=0.0)
+    return W.Case("edge_drop", 19, solid, (False, True, True),
+                  np.ascontiguousarray(phi0), p)
 
 
 CASES = cases()
