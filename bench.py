@@ -90,9 +90,12 @@ def pass_bytes(Q: int, bpp: int, ent: float) -> dict:
         "gradient": 4 + 4 + 1 + 7 + 16,
         # links + offsets, neighbour n_c 16 B; write 16 B
         "nc_solid": 5 * 4 + 8 + 16 + 16,
-        # padded index 4 B, the entries, (n_c, |C|) 16 B, f^t,
-        # (rho^r, rho^b), phase 4 B; writes f'' (Q planes) and (q, v) 16 B
-        "collide": 4 + ent + 16 + Q * bpp + 8 + 4 + Q * bpp + 16,
+        # padded index 4 B, the entries, the neighbours' (n_c, |C|) 16 B;
+        # writes the curvature 4 B
+        "curvature": 4 + ent + 16 + 4,
+        # the curvature 4 B, (n_c, |C|) 16 B, f^t, (rho^r, rho^b), phase
+        # 4 B; writes f'' (Q planes) and (q, v) 16 B
+        "collide": 4 + 16 + Q * bpp + 8 + 4 + Q * bpp + 16,
     }
 
 
@@ -357,7 +360,7 @@ def run_ours(args):
     pb = pass_bytes(Q, bpp, 4.0 * cells / nf)
     n_zh = s.n_zou_he
     n_of = {"stream": nf, "zh_fix": n_zh, "phi_solid": n_sbnd, "gradient": nf,
-            "nc_solid": n_sbnd, "collide": nf}
+            "nc_solid": n_sbnd, "curvature": nf, "collide": nf}
     peak, peak_src = measured_peaks()
     passes_out = {}
     for p, t in pass_ms.items():
@@ -373,13 +376,13 @@ def run_ours(args):
     kern = {"stream": "k_stream", "zh_fix": "k_zh_fix",
             "phi_solid": "k_phi_solid",
             "gradient": "k_gradient", "nc_solid": "k_nc_solid",
-            "collide": "k_collide"}[dom]
+            "curvature": "k_curvature", "collide": "k_collide"}[dom]
     alg_bytes = pb[dom] * n_of[dom]
     dom_ms = passes_out[dom]["ms"]
     achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
     traffic = recorded_traffic(kern, name)
     step_bytes = (2 * 2 * Q * bpp + 4) * nf  # populations read+written + link bits
-    launches_per_step = 3 + (2 if n_sbnd > 0 else 0) + (1 if n_zh > 0 else 0)
+    launches_per_step = 4 + (2 if n_sbnd > 0 else 0) + (1 if n_zh > 0 else 0)
 
     e2e = None
     if not args.no_e2e:

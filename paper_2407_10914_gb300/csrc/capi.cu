@@ -44,7 +44,7 @@ long long count_solid(const uint8_t *solid, long long N) {
 
 // Byte offsets of every buffer inside the caller's workspace.
 struct Layout {
-  size_t TA, TB, U, R, SA, SB, mf, ncf, nw, fg, macro;  // F-space
+  size_t TA, TB, U, R, SA, SB, mf, ncf, kap, nw, fg, macro;  // F-space
   size_t ms, ncs, sg, sgp, sflag, sdir;           // S-space
   size_t phib, fgp;                               // dense phase field
   size_t nbd, soff, slink, fflag, zh;             // neighbour lookup
@@ -86,6 +86,7 @@ Layout make_layout(int Q, int nx, int ny, int nz, int storage, long long NF,
   L.SB = take(nfp * 16);
   L.mf = take(nfp * 4);
   L.ncf = take(nfp * 16);
+  L.kap = take(nfp * 4);
   L.nw = take(nfp * 16);
   L.fg = take(nfp * 4);
   L.macro = take(nfp * 16);
@@ -220,6 +221,7 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
   d.mf = (float *)(base + L.mf);
   d.ms = (float *)(base + L.ms);
   d.ncf = (float4 *)(base + L.ncf);
+  d.kap = (float *)(base + L.kap);
   d.ncs = (float4 *)(base + L.ncs);
   d.macro = (float4 *)(base + L.macro);
   d.phib = (float *)(base + L.phib);

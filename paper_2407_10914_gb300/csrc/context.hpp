@@ -85,6 +85,7 @@ struct Dom {
   float *mf;            // [NF] encoded phase field
   float *ms;            // [NS] encoded phase field (Eq. 34)
   float4 *ncf;          // [NF] (n_c, |C|)
+  float *kap;           // [NF] curvature of Eq. (12), for the collision
   float4 *ncs;          // [NS] (n_c of Eq. 35, 0)
   float4 *macro;        // [NF] (u_x, u_y, u_z, rho) of the last macro step
   // the phase field again as a dense box with a one-node halo (padded

@@ -285,16 +285,31 @@ __device__ __forceinline__ float curvature(const Dom &d, int k, float4 &c4) {
          (dn[0][2] + dn[2][0]) * nx_ * nz_ + (dn[2][1] + dn[1][2]) * nz_ * ny_;
 }
 
+// Eq. (12) at fluid node k, stored for the collision pass.
+template <int Q, bool COH>
+__device__ __forceinline__ void curvature_node(const Dom &d, int k) {
+  float4 c4;
+  d.kap[k] = curvature<Q, COH>(d, k, c4);
+}
+
 // Eq. (5) F = 1/2 gamma kappa C (C = |C| n_c) plus rho g (Eq. 36), the
 // collision (Eq. 2) of the stored f^t, and the store of the recoloured
 // state of fluid node k: f''_i and (q, v) with q the encoded rho^r/rho and
 // v = beta rho^r rho^b / rho n (Eqs. 20-21). The relaxation rate follows
 // the node's phase field (Eq. 39's value on the outlet plane).
-template <int Q, int ST, bool MACROS, bool COH, int MRT = -1>
+// KAP: the curvature was stored by curvature_node (the same float, so both
+// forms agree bit for bit); else it is computed here.
+template <int Q, int ST, bool MACROS, bool COH, int MRT = -1, bool KAP = false>
 __device__ __forceinline__ void collide_node(const Dom &d, int k) {
   using IO = TIO<Q, ST, COH>;
   float4 c4;
-  const float kappa = curvature<Q, COH>(d, k, c4);
+  float kappa;
+  if (KAP) {
+    kappa = ldv<COH>(d.kap + k);
+    c4 = ldv<COH>(d.ncf + k);
+  } else {
+    kappa = curvature<Q, COH>(d, k, c4);
+  }
   float ft[Q];
 #pragma unroll
   for (int i = 0; i < Q; ++i) ft[i] = IO::load_from(d, d.U, i, k);

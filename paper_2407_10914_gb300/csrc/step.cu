@@ -1,4 +1,4 @@
-// The time step as five dependent passes. Each pass needs the previous one's
+// The time step as six dependent passes. Each pass needs the previous one's
 // values at lattice neighbours:
 //   1 k_stream     (fluid)  pull of Eq. (1), Eqs. (7)-(9): stores f^t,
 //                  (rho^r, rho^b) and the phase field; k_zh_fix then applies
@@ -6,9 +6,10 @@
 //   2 k_phi_solid  (solid-boundary) Eq. (34)
 //   3 k_gradient   (fluid)  Eqs. (6), (27) and wetting, Eqs. (28)-(33)
 //   4 k_nc_solid   (solid-boundary) Eq. (35)
-//   5 k_collide    (fluid)  Eq. (12), (5), (36); Eq. (2) single-rate on the
-//                  stored f^t; store f'' and (q, v), i.e. the recoloured
-//                  state of Eqs. (20)-(21)
+//   5 k_curvature  (fluid)  Eq. (12), stored per node
+//   6 k_collide    (fluid)  Eqs. (5), (36); Eq. (2) single-rate or MRT on
+//                  the stored f^t; store f'' and (q, v), i.e. the
+//                  recoloured state of Eqs. (20)-(21)
 // One thread per node of the compact fluid (F) or solid-boundary (S) list;
 // the work of a node is in passes.cuh.
 #include <cuda_runtime.h>
@@ -24,9 +25,11 @@ constexpr int BLOCK = 256;
 // Blocks per SM, measured on the 256^3 rock: the gather passes are bound by
 // load latency, so the stream and gradient passes run with 32 registers
 // (7-8 resident blocks of 256 threads; the gradient pass gains 14 % over its
-// unbounded 34 registers, the stream pass 4 % over 40). The collision (with
-// its sums in deviation form) needs 80 registers: 3 blocks, 5 % faster than
-// 4 blocks with 64 registers and spills.
+// unbounded 34 registers, the stream pass 4 % over 40); so does the
+// curvature, a gather of the neighbours' n_c split off the collision. The
+// single-rate collision then runs 4 blocks (64 registers, 28 B of spills),
+// 4 % faster than 3 blocks with 80; the MRT collision keeps 3 blocks (it
+// would spill 84 B at 64 registers).
 template <int Q, int ST>
 __global__ void __launch_bounds__(BLOCK, 7) k_stream(Dom d) {
   const int k = blockIdx.x * BLOCK + threadIdx.x;
@@ -57,11 +60,17 @@ __global__ void __launch_bounds__(BLOCK) k_nc_solid(Dom d) {
   if (j < d.NS) nc_solid_node<Q, false>(d, j);
 }
 
+template <int Q>
+__global__ void __launch_bounds__(BLOCK, 8) k_curvature(Dom d) {
+  const int k = blockIdx.x * BLOCK + threadIdx.x;
+  if (k < d.NF) curvature_node<Q, false>(d, k);
+}
+
 // MRT: the collision compiled for the single rate (0) or the MRT rates (1)
 template <int Q, int ST, bool MACROS, int MRT>
-__global__ void __launch_bounds__(BLOCK, 3) k_collide(Dom d) {
+__global__ void __launch_bounds__(BLOCK, MRT ? 3 : 4) k_collide(Dom d) {
   const int k = blockIdx.x * BLOCK + threadIdx.x;
-  if (k < d.NF) collide_node<Q, ST, MACROS, false, MRT>(d, k);
+  if (k < d.NF) collide_node<Q, ST, MACROS, false, MRT, true>(d, k);
 }
 
 // NVTX range around the launch of one pass (header-only NVTX: a no-op
@@ -106,7 +115,12 @@ static void launch_step_t(const Dom &d, cudaStream_t s, bool macros,
   }
   if (ev) cudaEventRecord(ev[5], s);
   const bool mrt = Q == 19 && d.c.mrt;
-  PassRange r("curvature, collision, recolouring (Eq. 12, 5, 2, 20-21)");
+  {
+    PassRange r("curvature (Eq. 12)");
+    k_curvature<Q><<<g, BLOCK, 0, s>>>(d);
+  }
+  if (ev) cudaEventRecord(ev[6], s);
+  PassRange r("force, collision, recolouring (Eq. 5, 2, 20-21)");
   if (macros) {
     if (mrt) k_collide<Q, ST, true, 1><<<g, BLOCK, 0, s>>>(d);
     else k_collide<Q, ST, true, 0><<<g, BLOCK, 0, s>>>(d);
@@ -114,7 +128,7 @@ static void launch_step_t(const Dom &d, cudaStream_t s, bool macros,
     if (mrt) k_collide<Q, ST, false, 1><<<g, BLOCK, 0, s>>>(d);
     else k_collide<Q, ST, false, 0><<<g, BLOCK, 0, s>>>(d);
   }
-  if (ev) cudaEventRecord(ev[6], s);
+  if (ev) cudaEventRecord(ev[7], s);
 }
 
 template <int Q, int ST>
