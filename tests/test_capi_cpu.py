@@ -89,3 +89,21 @@ def test_batch_entry_points_host_only(lib):
     assert lib.lbm_batch_step(None, 1, None) == -1
     assert lib.lbm_batch_set_config(None, 0, 256, 1, None) == -1
     assert lib.lbm_batch_last_error(None) == b"null batch"
+
+
+def test_pass_list_matches_header_and_byte_model():
+    """lbm_step_timed reports LBM_N_PASSES kernels; the binding names them
+    and bench.py's byte model has an entry for each."""
+    import importlib.util
+    from paper_2407_10914_gb300 import lbm
+    src = open(os.path.join(ROOT, "include", "lbmgb.h")).read()
+    n = int(re.search(r"#define LBM_N_PASSES (\d+)", src).group(1))
+    assert len(lbm.PASSES) == n
+    spec = importlib.util.spec_from_file_location(
+        "bench_module", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    for q in (9, 19):
+        pb = bench.pass_bytes(q, 4, 15.0)
+        assert set(pb) == set(lbm.PASSES)
+        assert all(v > 0 for v in pb.values())
