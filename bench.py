@@ -570,7 +570,7 @@ def run_tube(torch, lbm):
             "speed": U, "speed_eq47": U_ref,
             "speed_error_pct": round(100 * abs(U / U_ref - 1), 2),
             "r_eff": round(float(np.sqrt(8 * mu * L * U / dP)), 3),
-            "note": "launch-bound at this size (six kernels per step)"}
+            "note": "launch-bound at this size (seven kernels per step)"}
 
 
 def run_laplace(lbm):

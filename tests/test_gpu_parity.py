@@ -274,7 +274,7 @@ def test_step_graph_equals_single_steps(torch):
     state equals that of n single steps bit for bit, for odd and even n,
     across both orientations of the state buffers, and after new
     parameters (the graph is recorded again)."""
-    case = CASES[2][1]  # Zou-He planes and solids: all six kernels
+    case = CASES[2][1]  # Zou-He planes and solids: all seven kernels
     a = gpu_session(torch, case)
     b = gpu_session(torch, case)
     for s in (a, b):
