@@ -27,7 +27,7 @@ Drive (Sec. II.C): Type-I sets the Zou-He densities, rho_in = rho_out +
 g = Delta P / (rho0 L) along the flow axis, L the distance between the
 Zou-He planes, so both impose the same mean gradient.
 
-The driver is host logic only. Its `engine` is any object with
+The runner is host logic only. Its `engine` is any object with
 ``set_params(**params)``, ``step(n)``, ``reduce(kind) -> float`` and
 ``swap_inlet(colour)``: the GPU session (:class:`lbm.Session`) for runs.
 """
