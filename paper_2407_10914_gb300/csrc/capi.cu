@@ -100,7 +100,10 @@ Layout make_layout(int Q, int nx, int ny, int nz, int storage, long long NF,
   L.phib = take((size_t)(nx + 2) * (ny + 2) * (nz + 2) * 4);
   L.nbd = take((size_t)(nx + 2) * (ny + 2) * (nz + 2) * 4);
   L.soff = take((nsp + 1) * 4);
-  L.slink = take((size_t)(Q - 1) * nsp * 4);  // bound: Q - 1 links a node
+  // Links of the solid-boundary nodes: at most Q - 1 per node, and, since
+  // each link reversed is a distinct (fluid node, direction) pair, at most
+  // Q - 1 per fluid node too
+  L.slink = take((size_t)(Q - 1) * (nsp < nfp ? nsp : nfp) * 4);
   L.fflag = take(nfp);
   L.zh = take(3 * nfp * 4);
   L.map = take((size_t)N * 2);
