@@ -58,3 +58,36 @@ def test_translation_along_the_flow_axis_is_not_a_symmetry():
               np.ascontiguousarray(np.roll(phi0, 2, axis=2)), p, 6)
     want = np.roll(ref, 2, axis=4)
     assert np.abs(got - want).max() > 1e-6 * np.abs(ref).max()
+
+
+def edge_case_2d(nx=40, ny=24):
+    """D2Q9: a wetting wall row at y = 0, a clamped top edge, x periodic; a
+    red drop centred on the top edge at the x period boundary."""
+    y, x = np.mgrid[0:ny, 0:nx].astype(np.float64)
+    solid = np.zeros((1, ny, nx), np.uint8)
+    solid[0, 0, :] = 1
+    dx = np.minimum(x, nx - x)  # distance to x = 0 across the period
+    r = np.sqrt(dx ** 2 + (y - (ny - 1)) ** 2)
+    phi0 = np.tanh((9.0 - r) / 1.5)[None]
+    phi0[solid == 1] = 0.0
+    p = W.base_params(tau_r=1.0, tau_b=0.7, gamma=0.01, beta=0.9,
+                      theta_deg=50.0, wetting=2)
+    return solid, np.ascontiguousarray(phi0), p
+
+
+def run_2d(solid, phi0, p, steps):
+    o = O.Oracle(9, solid, (True, False, True))
+    o.set_params(**p)
+    o.init_state(phi0)
+    o.step(steps)
+    return o.pops
+
+
+@pytest.mark.parametrize("shift", [1, 7, 20])
+def test_d2q9_step_commutes_with_periodic_translation(shift):
+    solid, phi0, p = edge_case_2d()
+    ref = run_2d(solid, phi0, p, 8)
+    got = run_2d(np.ascontiguousarray(np.roll(solid, shift, axis=2)),
+                 np.ascontiguousarray(np.roll(phi0, shift, axis=2)), p, 8)
+    want = np.roll(ref, shift, axis=4)
+    assert np.abs(got - want).max() <= 1e-13 * np.abs(ref).max()
