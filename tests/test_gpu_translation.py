@@ -10,7 +10,7 @@ arithmetic per node does not depend on the order of nodes)."""
 import numpy as np
 import pytest
 
-from test_oracle_translation import edge_case
+from test_oracle_translation import edge_case, edge_case_2d
 
 pytestmark = pytest.mark.gpu
 
@@ -41,4 +41,22 @@ def test_gpu_step_commutes_with_periodic_translation(lbm, axis, shift):
     got = gpu_run(lbm, np.ascontiguousarray(np.roll(solid, shift, axis=axis)),
                   np.ascontiguousarray(np.roll(phi0, shift, axis=axis)), p, 6)
     want = np.roll(ref, shift, axis=axis + 2)
+    assert np.abs(got - want).max() <= 1e-6 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("shift", [1, 7, 20])
+def test_gpu_d2q9_step_commutes_with_periodic_translation(lbm, shift):
+    solid, phi0, p = edge_case_2d()
+
+    def run(sol, ph):
+        s = lbm.Session(9, sol, (True, False, True))
+        s.set_params(**p)
+        s.init_state(ph.astype(np.float32))
+        s.step(8)
+        return s.get_populations().cpu().numpy().astype(np.float64)
+
+    ref = run(solid, phi0)
+    got = run(np.ascontiguousarray(np.roll(solid, shift, axis=2)),
+              np.ascontiguousarray(np.roll(phi0, shift, axis=2)))
+    want = np.roll(ref, shift, axis=4)
     assert np.abs(got - want).max() <= 1e-6 * np.abs(ref).max()
