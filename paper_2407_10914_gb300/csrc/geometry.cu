@@ -57,8 +57,8 @@ __global__ void k_tile_count(Dom d, int *__restrict__ cf, int *__restrict__ cs) 
   const int Y0 = (q % d.nty) * G::TY, Z0 = (q / d.nty) * G::TZ;
   int nf = 0, ns = 0;
   for (int lp = threadIdx.x; lp < G::TN; lp += GBLOCK) {
-    int x, y, z, p0;
-    local_node<Q>(lp, X0, Y0, Z0, x, y, z, p0);
+    int x, y, z;
+    local_node<Q>(lp, X0, Y0, Z0, x, y, z);
     if (x >= d.nx || y >= d.ny || z >= d.nz) continue;
     const int c = d.cls[x + d.nx * (y + d.ny * z)];
     nf += (c & 2) ? 1 : 0;
@@ -194,8 +194,8 @@ __global__ void k_tile_map(Dom d, uint16_t *__restrict__ map,
   for (int pass = face_tile ? 0 : 1; pass < 2; ++pass) {
     for (int c0 = 0; c0 < G::TN; c0 += GBLOCK) {
       const int lp = c0 + threadIdx.x;
-      int x, y, z, p0;
-      local_node<Q>(lp, X0, Y0, Z0, x, y, z, p0);
+      int x, y, z;
+      local_node<Q>(lp, X0, Y0, Z0, x, y, z);
       const bool valid = x < d.nx && y < d.ny && z < d.nz;
       const int g = valid ? x + d.nx * (y + d.ny * z) : 0;
       const int c = valid ? d.cls[g] : CLS_SOLID;

@@ -44,8 +44,6 @@ __device__ __forceinline__ int axis_step(int v, int m, bool per, bool clamp,
   return v;
 }
 
-__device__ __forceinline__ bool is_fluid_cls(int c) { return c & 2; }
-
 // ------------------------------------------------------ index guards
 // Every gathered index goes through guard(). In a build with
 // LBM_BOUNDS_CHECK defined (build.build(check=True): liblbmgb_check.so) an
@@ -259,95 +257,11 @@ __device__ __forceinline__ void rebuild(float T, float4 S, int i, float &fr,
   rebuild_ev<Q>(T, S.x, ev, i, fr, fb);
 }
 
-// ------------------------------------------------------------- Zou-He
-// Appendix B on a flow axis a. Inlet (coordinate 0), per colour with the
-// species density rho_s = rho_in zeta^s:
-//   j = rho_s - [sum_{e.a=0} f + 2 sum_{e.a=-1} f],
-//   N_t = 1/2 sum_{e.a=0} (e.t) f,
-//   f_i = f_opp(i) + 6 w_i j - sum_{t != a} (e_i.t) N_t      (e_i.a = +1).
-template <int Q>
-__device__ __forceinline__ void zou_he_inlet(float *f, float rho_s, int a) {
-  float known = 0.f, Nt[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const int ea = Lattice<Q>::e(i, a);
-    if (ea == 0) {
-      known += f[i];
-#pragma unroll
-      for (int t = 0; t < 3; ++t)
-        if (t != a) Nt[t] += 0.5f * (float)Lattice<Q>::e(i, t) * f[i];
-    } else if (ea == -1) {
-      known += 2.f * f[i];
-    }
-  }
-  const float j = rho_s - known;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    if (Lattice<Q>::e(i, a) != 1) continue;
-    float corr = 0.f;
-#pragma unroll
-    for (int t = 0; t < 3; ++t)
-      if (t != a) corr += (float)Lattice<Q>::e(i, t) * Nt[t];
-    f[i] = f[Lattice<Q>::opp(i)] + 6.f * Lattice<Q>::w(i) * j - corr;
-  }
-}
-
-// Outlet (last coordinate): total j^t = -rho_out + [sum_{e.a=0} f^t +
-// 2 sum_{e.a=+1} f^t] (B.9); per colour, with chi^s of (B.12)-(B.13):
-//   f_i = f_opp(i) - 6 w_i j^t chi^s - sum_{t != a} (e_i.t) N_t (e_i.a = -1).
-template <int Q>
-__device__ __forceinline__ void zou_he_outlet(float *fr, float *fb,
-                                              float rho_out, float phi_out,
-                                              int a) {
-  float known = 0.f;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const int ea = Lattice<Q>::e(i, a);
-    if (ea == 0) known += fr[i] + fb[i];
-    if (ea == 1) known += 2.f * (fr[i] + fb[i]);
-  }
-  const float jt = known - rho_out;
-  const float chi[2] = {0.5f * (1.f + phi_out), 0.5f * (1.f - phi_out)};
-#pragma unroll
-  for (int s = 0; s < 2; ++s) {
-    float *f = s == 0 ? fr : fb;
-    float Nt[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      if (Lattice<Q>::e(i, a) != 0) continue;
-#pragma unroll
-      for (int t = 0; t < 3; ++t)
-        if (t != a) Nt[t] += 0.5f * (float)Lattice<Q>::e(i, t) * f[i];
-    }
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      if (Lattice<Q>::e(i, a) != -1) continue;
-      float corr = 0.f;
-#pragma unroll
-      for (int t = 0; t < 3; ++t)
-        if (t != a) corr += (float)Lattice<Q>::e(i, t) * Nt[t];
-      f[i] = f[Lattice<Q>::opp(i)] - 6.f * Lattice<Q>::w(i) * jt * chi[s] - corr;
-    }
-  }
-}
-
 __device__ __forceinline__ int axis_coord(int x, int y, int z, int a) {
   return a == 0 ? x : (a == 1 ? y : z);
 }
 __device__ __forceinline__ int axis_extent(const Dom &d, int a) {
   return a == 0 ? d.nx : (a == 1 ? d.ny : d.nz);
-}
-
-template <int Q>
-__device__ __forceinline__ void sum_colours(const float *fr, const float *fb,
-                                            float &rr, float &rb) {
-  rr = 0.f;
-  rb = 0.f;
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    rr += fr[i];
-    rb += fb[i];
-  }
 }
 
 // ------------------------------------------------------------ wetting
