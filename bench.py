@@ -4,18 +4,22 @@
 
 One JSON line on rank 0:
   value      fluid-node updates per second / 1e6 (MLUPS), whole job over all
-             ranks, populations resident in HBM, CUDA events around K steps;
+             ranks, populations resident in HBM, CUDA events around K steps,
+             the median of --repeats timed regions (each K steps);
   e2e        the same metric through the public API from host buffers: the
              solid image and phi0 copied in from pinned memory, geometry set-up,
              K steps each followed by the FP64 saturation read-back (8 bytes),
              the final phase field copied out;
-  roofline   the dominant pass (the longest; the stream pass on the rock)
-             against the measured HBM copy bandwidth, with the pass's
-             algorithmic bytes per fluid node (pass_bytes below) times the
-             nodes it processes; every pass's figures are under "passes";
-  step_bandwidth  the step-level accounting of 308 B per fluid-node update
-             (2 x 2Q populations of 4 B plus a 4 B link mask);
-  cpu_baseline  the FP64 oracle on a bounded slab of the same rock;
+  roofline   the whole step against the measured HBM copy bandwidth, with
+             308 B per fluid-node update (2 x 2Q populations of 4 B read and
+             written plus a 4 B link mask) over the median step time;
+             `traffic` the ncu DRAM bytes of the step's kernels summed;
+  passes     every kernel of the step: CUDA-event time, its own
+             algorithmic bytes (pass_bytes below) and ncu DRAM bytes;
+             dominant_pass the longest of them;
+  node_schedule  the same rock stepped by the node schedule, for comparison;
+  cpu_baseline  the FP64 oracle on a bounded slab of the same rock, on all
+             host cores and on one;
   tube       the capillary-tube workload (256 x 20 x 20, r = 8, Type-I,
              20000 steps): throughput, and the interface speed beside the
              Washburn law for equal viscosities (Eq. 47);
@@ -60,16 +64,36 @@ METRIC = "MLUPS & % HBM roofline: plain FP32 vs FP16-storage/batched at stated e
 BYTES_POP = {"fp32": 4, "fp16": 2, "bf16": 2}
 
 
-def pass_bytes(Q: int, bpp: int, ent: float) -> dict:
-    """Algorithmic DRAM bytes per processed node of each pass: what the pass
-    must read and write once (a gathered field counts once per node, since
-    every element is read by a fixed number of neighbours that L2 serves).
-    Fluid passes find their neighbours in the dense entry box, 4 B per cell
-    of the padded box, read once per pass: `ent` = 4 x cells / fluid nodes
-    bytes per fluid node (15 on the 256^3 rock); the Eq. 35 pass reads its
-    CSR links (4.2 per node on the rock, taken as 5 x 4 B) and two offsets;
-    the Eq. 34 pass a 4 B direction mask."""
-    ent = round(ent, 1)
+def pass_bytes(Q: int, bpp: int, sched: str = "tiles",
+               cells_per_node: float = 3.66) -> dict:
+    """Algorithmic DRAM bytes per processed node of each pass of a schedule:
+    what the pass must read and write once (a gathered field counts once per
+    node, since every element is read by a fixed number of neighbours that
+    L2 serves). cells_per_node = box cells per fluid node (3.66 on the 256^3
+    rock). The tile passes find their neighbours through the row words
+    (16 B per 32 box cells, 0.5 B per cell); the node passes through the
+    dense entry box (4 B per cell of the padded box), the Eq. 35 pass
+    through its CSR links (4.2 per node on the rock, taken as 5 x 4 B and
+    two offsets), the Eq. 34 pass through a 4 B direction mask."""
+    rw = round(0.5 * cells_per_node, 2)
+    ent = round(4.0 * cells_per_node, 1)
+    if sched == "tiles":
+        return {
+            # T_i of the sources (Q planes), (q, v) 16 B, row words; writes
+            # (rho^r, rho^b) 8 B and the phase field 4 B
+            "pull": Q * bpp + 16 + rw + 8 + 4,
+            # per plane node: flags 1 B, padded index 4 B, the entry of
+            # x - a 4 B, its phase 4 B, (rho^r, rho^b) 8 B; writes the phase
+            "planes": 1 + 4 + 4 + 4 + 8 + 4,
+            # row words, the phase field 4 B, wall normal 16 B at the
+            # fluid-boundary nodes (about 45 %: 7 B); writes (n_c, |C|) 16 B
+            "gradient": rw + 4 + 7 + 16,
+            # row words, (n_c, |C|) 16 B; writes the curvature 4 B
+            "curvature": rw + 16 + 4,
+            # row words, T_i of the sources, (rho^r, rho^b) 8 B, curvature
+            # 4 B, (n_c, |C|) 16 B; writes f'' (Q planes) and (q, v) 16 B
+            "collide": rw + Q * bpp + 8 + 4 + 16 + Q * bpp + 16,
+        }
     return {
         # T_i of the sources (each once), (q, v) 16 B, the entries, flags
         # 1 B, padded index 4 B; writes f^t (Q planes), (rho^r, rho^b) 8 B,
@@ -99,6 +123,18 @@ def pass_bytes(Q: int, bpp: int, ent: float) -> dict:
     }
 
 
+# the kernel of each pass, by schedule (names as ncu lists them)
+PASS_KERNEL = {
+    "tiles": {"pull": "kt_pull", "planes": "kt_planes",
+              "gradient": "kt_gradient", "curvature": "kt_curvature",
+              "collide": "kt_collide"},
+    "nodes": {"stream": "k_stream", "zh_fix": "k_zh_fix",
+              "phi_solid": "k_phi_solid", "gradient": "k_gradient",
+              "nc_solid": "k_nc_solid", "curvature": "k_curvature",
+              "collide": "k_collide"},
+}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -126,6 +162,13 @@ def parse():
                     help="skip the FP16/BF16-storage objects")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the gradient (adjoint) object")
+    ap.add_argument("--repeats", type=int, default=5,
+                    help="repeats of the timed region (median reported)")
+    ap.add_argument("--no-node-schedule", action="store_true",
+                    help="skip timing the node schedule beside the tiles")
+    ap.add_argument("--oracle-sample", nargs=3, type=int, default=None,
+                    metavar=("PLANES", "STEPS", "SIZE"),
+                    help=argparse.SUPPRESS)
     ap.add_argument("--adjoint-size", type=int, default=128)
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     return ap.parse_args()
@@ -237,8 +280,8 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha1()
-    for f in ("step.cu", "passes.cuh", "tiles.cuh", "stencil.cuh",
-              "lattice.cuh", "context.hpp", "geometry.cu"):
+    for f in ("step.cu", "step_tiles.cu", "passes.cuh", "tiles.cuh",
+              "stencil.cuh", "lattice.cuh", "context.hpp", "geometry.cu"):
         h.update(open(os.path.join(ROOT, "paper_2407_10914_gb300", "csrc", f),
                       "rb").read())
     return h.hexdigest()[:12]
@@ -291,6 +334,69 @@ def time_oracle(case, planes: int, steps: int, warmup: int = 0):
                 seconds=dt)
 
 
+def oracle_single_core(args, planes: int, steps: int):
+    """The oracle on one host core (OMP_NUM_THREADS=1, a child process, so
+    that the OpenMP runtime starts with one thread) on a smaller slab of the
+    same rock."""
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-sample",
+           str(planes), str(steps), str(args.size), "--drive", args.drive]
+    try:
+        r = subprocess.run(cmd, env=env, capture_output=True, text=True,
+                           timeout=600)
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except (subprocess.SubprocessError, ValueError, IndexError):
+        return None
+
+
+def run_oracle_sample(args):
+    planes, steps, size = args.oracle_sample
+    args.size = size
+    case, _ = workload(args)
+    res = time_oracle(case, planes, steps, 0)
+    print(json.dumps({k: res[k] for k in ("value", "unit", "cores", "kind",
+                                          "sample")}), flush=True)
+
+
+def node_schedule(args, torch, lbm, s, Q, bpp, cells, nf, n_sbnd, n_zh,
+                  peak, name):
+    """The same session stepped by the node schedule (seven passes, the
+    streamed populations stored): its step time and per-pass times, for
+    comparison. The session's state advances; its schedule is put back."""
+    stream = torch.cuda.current_stream()
+    s.set_schedule("nodes")
+    steps = min(args.steps, 200)
+    s.step(3)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    k2 = min(steps, 100)
+    pm = s.step_timed(k2)
+    pb = pass_bytes(Q, bpp, "nodes", cells)
+    n_of = {"stream": nf, "zh_fix": n_zh, "phi_solid": n_sbnd, "gradient": nf,
+            "nc_solid": n_sbnd, "curvature": nf, "collide": nf}
+    out = {"ms_per_step": round(ms, 5),
+           "value": round(nf / (ms * 1e-3) / 1e6, 2), "unit": "MLUPS",
+           "frac": round((2 * 2 * Q * bpp + 4) * nf / (ms * 1e-3) / 1e9 / peak, 4),
+           "passes": {}}
+    for p, t in pm.items():
+        if t <= 0 or n_of[p] == 0:
+            continue
+        t1 = t / k2
+        b = pb[p] * n_of[p]
+        kern = PASS_KERNEL["nodes"][p]
+        out["passes"][p] = {"kernel": kern, "ms": round(t1, 5),
+                            "GBps": round(b / (t1 * 1e-3) / 1e9, 1),
+                            "dram_bytes_per_launch": recorded_traffic(kern, name)}
+    s.set_schedule("tiles")
+    return out
+
+
 def run_reference(args):
     ws, rank, _ = dist_init(args)
     if rank != 0:
@@ -337,30 +443,38 @@ def run_ours(args):
     s.step(args.warmup)
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
-    barrier(ws)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    s.step(args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier(ws)
-    ms = e0.elapsed_time(e1)
+    # the timed region, repeated: each repeat is `steps` steps between a
+    # barrier and CUDA events on the launching stream; the population
+    # buffers (2 x 0.42 GB on the rock) exceed the 129 MB L2 every step
+    rep_ms = []
+    for _ in range(max(1, args.repeats)):
+        barrier(ws)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        s.step(args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        rep_ms.append(e0.elapsed_time(e1))
     clk = clocks.stop()
+    ms = float(np.median(rep_ms))
     ms_max = max_over_ranks(ms, ws)
     value = whole_job_value(ws, nf, args.steps, ms_max)
+    step_ms = ms_max / args.steps
 
     # per-pass times (events inside the library, on the same stream)
     k2 = max(1, min(args.steps, 200))
+    sched = s.schedule
     pass_ms = s.step_timed(k2)
     bpp = BYTES_POP[args.storage]
-    gz, gy, gx = case.solid.shape
-    cells = (gx + 2) * (gy + 2) * (gz + 2 if Q == 19 else 1)
-    pb = pass_bytes(Q, bpp, 4.0 * cells / nf)
+    cells = float(case.n_nodes) / nf
+    pb = pass_bytes(Q, bpp, sched, cells)
     n_zh = s.n_zou_he
-    n_of = {"stream": nf, "zh_fix": n_zh, "phi_solid": n_sbnd, "gradient": nf,
-            "nc_solid": n_sbnd, "curvature": nf, "collide": nf}
+    n_of = {"pull": nf, "planes": n_zh, "stream": nf, "zh_fix": n_zh,
+            "phi_solid": n_sbnd, "gradient": nf, "nc_solid": n_sbnd,
+            "curvature": nf, "collide": nf}
     peak, peak_src = measured_peaks()
     passes_out = {}
     for p, t in pass_ms.items():
@@ -368,21 +482,29 @@ def run_ours(args):
             continue
         t1 = t / k2
         b = pb[p] * n_of[p]
-        passes_out[p] = {"ms": round(t1, 5), "bytes_per_node": pb[p],
-                         "nodes": n_of[p],
+        kern = PASS_KERNEL[sched][p]
+        tr = recorded_traffic(kern, name)
+        passes_out[p] = {"kernel": kern, "ms": round(t1, 5),
+                         "bytes_per_node": pb[p], "nodes": n_of[p],
                          "GBps": round(b / (t1 * 1e-3) / 1e9, 1),
-                         "frac": round(b / (t1 * 1e-3) / 1e9 / peak, 4)}
+                         "frac": round(b / (t1 * 1e-3) / 1e9 / peak, 4),
+                         "dram_bytes_per_launch": tr,
+                         "dram_GBps": (round(tr / (t1 * 1e-3) / 1e9, 1)
+                                       if tr else None)}
     dom = max(passes_out, key=lambda p: passes_out[p]["ms"])
-    kern = {"stream": "k_stream", "zh_fix": "k_zh_fix",
-            "phi_solid": "k_phi_solid",
-            "gradient": "k_gradient", "nc_solid": "k_nc_solid",
-            "curvature": "k_curvature", "collide": "k_collide"}[dom]
-    alg_bytes = pb[dom] * n_of[dom]
-    dom_ms = passes_out[dom]["ms"]
-    achieved = alg_bytes / (dom_ms * 1e-3) / 1e9
-    traffic = recorded_traffic(kern, name)
-    step_bytes = (2 * 2 * Q * bpp + 4) * nf  # populations read+written + link bits
-    launches_per_step = 4 + (2 if n_sbnd > 0 else 0) + (1 if n_zh > 0 else 0)
+    # the step against the survey's 308 B per fluid-node update (38 pops
+    # read and written, 4 B link mask)
+    upd_bytes = 2 * 2 * Q * bpp + 4
+    step_alg = upd_bytes * nf
+    achieved = step_alg / (step_ms * 1e-3) / 1e9
+    step_traffic = None
+    if passes_out and all(v["dram_bytes_per_launch"] for v in passes_out.values()):
+        step_traffic = sum(v["dram_bytes_per_launch"] for v in passes_out.values())
+    launches_per_step = len(passes_out)
+    nodes_sched = None
+    if not args.no_node_schedule and rank == 0:
+        nodes_sched = node_schedule(args, torch, lbm, s, Q, bpp, cells, nf,
+                                    n_sbnd, n_zh, peak, name)
 
     e2e = None
     if not args.no_e2e:
@@ -419,6 +541,9 @@ def run_ours(args):
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         cpu = time_oracle(case, 32, 6, 0)
         cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        one = oracle_single_core(args, 8, 2)
+        if one:
+            cpu["single_core"] = one
 
     if rank == 0:
         line = {
@@ -436,28 +561,38 @@ def run_ours(args):
                 "l2": "inputs larger than L2 (two population buffers of "
                       f"{2 * Q * bpp * case.n_nodes / 1e9:.2f} GB)",
             },
-            "roofline": {"bound": "hbm", "kernel": kern,
+            "roofline": {"bound": "hbm",
+                         "kernel": "the whole step (" + ", ".join(
+                             PASS_KERNEL[sched][p] for p in passes_out) + ")",
                          "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
-                         "traffic": traffic, "peak_source": peak_src,
-                         "algorithmic_bytes_per_launch": alg_bytes,
-                         "avg_launch_ms": dom_ms,
-                         "timing": "CUDA events around the pass on the "
-                                   "launching stream, mean of "
-                                   f"{k2} steps"},
+                         "traffic": step_traffic, "peak_source": peak_src,
+                         "bytes_per_update": upd_bytes,
+                         "algorithmic_bytes_per_step": step_alg,
+                         "ms_per_step": round(step_ms, 5),
+                         "timing": "CUDA events on the launching stream "
+                                   f"around {args.steps} steps, median of "
+                                   f"{len(rep_ms)} repeats",
+                         "traffic_note": "sum over the step's kernels of "
+                                         "ncu dram__bytes_read.sum + "
+                                         "dram__bytes_write.sum per launch "
+                                         "(profiles/dram_traffic.txt, current "
+                                         "kernel source only)"},
+            "dominant_pass": dict(passes_out[dom], name=dom),
+            "schedule": sched,
             "passes": passes_out,
-            "step_bandwidth": {"bytes_per_update": 2 * 2 * Q * bpp + 4,
-                               "GBps": round(step_bytes / (ms_max / args.steps
-                                                           * 1e-3) / 1e9, 1),
-                               "frac_of_measured_peak": round(
-                                   step_bytes / (ms_max / args.steps * 1e-3)
-                                   / 1e9 / peak, 4)},
+            "repeats_ms_per_step": [round(x / args.steps, 5) for x in rep_ms],
+            "spread_pct": round(100 * (max(rep_ms) - min(rep_ms)) / ms, 2),
             "pass_ms_per_step": {k: round(v / k2, 5) for k, v in pass_ms.items()},
-            "gpu_launches": launches_per_step * args.steps,
+            "gpu_launches": launches_per_step * args.steps * len(rep_ms),
             "clocks": clk,
             "total_node_MLUPS": round(ws * case.n_nodes * args.steps
                                       / (ms_max * 1e-3) / 1e6, 1),
         }
+        if clk and clk.get("sm_mhz"):
+            line["time_x_sm_mhz"] = round(step_ms * clk["sm_mhz"], 3)
+        if nodes_sched:
+            line["node_schedule"] = nodes_sched
         if e2e:
             line["e2e"] = e2e
         if tube:
@@ -870,7 +1005,9 @@ def run_adjoint(args, torch, lbm):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.oracle_sample:
+        run_oracle_sample(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

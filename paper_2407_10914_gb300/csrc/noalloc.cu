@@ -123,6 +123,18 @@ extern "C" lbm_status lbm_colour_mass_noalloc(int lattice, int64_t n_nodes,
   if ((lattice != 9 && lattice != 19) || !pops_dev || !mass_host)
     return LBM_ERR_ARG;
   if (n_nodes < 1 || n_nodes > LBM_NOALLOC_MAX_NODES) return LBM_ERR_ARG;
+  // the kernel reads pops_dev: it must be memory of the current device (a
+  // host pointer or another GPU's memory would be an illegal access)
+  int dev = -1;
+  cudaPointerAttributes at{};
+  if (cudaGetDevice(&dev) != cudaSuccess) return LBM_ERR_CUDA;
+  if (cudaPointerGetAttributes(&at, pops_dev) != cudaSuccess) {
+    cudaGetLastError();  // clear the error of an unknown pointer
+    return LBM_ERR_ARG;
+  }
+  if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) ||
+      at.device != dev)
+    return LBM_ERR_ARG;
   double *scratch = nullptr;
   cudaError_t e = scratch_for_current_device(&scratch);
   if (e != cudaSuccess) return LBM_ERR_CUDA;

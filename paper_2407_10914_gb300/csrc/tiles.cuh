@@ -2,10 +2,9 @@
 // pull of Eq. (1).
 //
 // The box is cut into tiles of TX x TY x TZ nodes (32 x 8 x 8 for D3Q19,
-// 64 x 32 x 1 for D2Q9). Fluid nodes are numbered tile by tile (F-space),
-// and within a tile the fluid nodes on the box's x faces first, then the
-// others in (z, y, x) order; solid-boundary nodes in (z, y, x) order
-// (S-space). The uint16 map over the box holds a node's class (bits 14-15)
+// 32 x 32 x 1 for D2Q9; TX = 32 always, so that one row of a tile is one
+// 32-bit mask). Fluid nodes are numbered tile by tile (F-space), and within
+// a tile in (z, y, x) order; so are the solid-boundary nodes (S-space). The uint16 map over the box holds a node's class (bits 14-15)
 // and its rank among the nodes of its kind in its tile (bits 0-13); with the
 // per-tile bases fbase/sbase this gives its F- or S-index.
 //
@@ -30,7 +29,7 @@ struct Tile<19> {
 
 template <>
 struct Tile<9> {
-  static constexpr int TX = 64, TY = 32, TZ = 1, LX = 6, LY = 5, LZ = 0;
+  static constexpr int TX = 32, TY = 32, TZ = 1, LX = 5, LY = 5, LZ = 0;
 };
 
 template <int Q>

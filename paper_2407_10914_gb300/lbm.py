@@ -25,10 +25,13 @@ STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA",
           -3: "LBM_ERR_STATE", -4: "LBM_ERR_NONFINITE", -5: "LBM_ERR_TIMEOUT",
           -6: "LBM_ERR_NOMEM"}
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
+# kernel schedules of lbm_step (LBM_SCHED_TILES, LBM_SCHED_NODES)
+SCHEDULE = {"tiles": 0, "nodes": 1}
 (LBM_MASS_R, LBM_MASS_B, LBM_SW_COUNT, LBM_SW_SMOOTH, LBM_DP, LBM_CA_R,
  LBM_CA_B) = range(7)
 EXPORTS = ("lbm_workspace_bytes", "lbm_init_geometry", "lbm_set_params",
-           "lbm_init_state", "lbm_step", "lbm_step_timed", "lbm_macros",
+           "lbm_init_state", "lbm_step", "lbm_step_timed",
+           "lbm_set_schedule", "lbm_get_schedule", "lbm_macros",
            "lbm_reduce",
            "lbm_get_populations", "lbm_set_populations", "lbm_swap_inlet",
            "lbm_debug_flags",
@@ -89,6 +92,10 @@ def load_library(path: str = LIB_PATH):
     L.lbm_step.argtypes = [vp, C.c_int, vp]
     L.lbm_step_timed.restype = C.c_int
     L.lbm_step_timed.argtypes = [vp, C.c_int, vp, C.POINTER(C.c_double)]
+    L.lbm_set_schedule.restype = C.c_int
+    L.lbm_set_schedule.argtypes = [vp, C.c_int]
+    L.lbm_get_schedule.restype = C.c_int
+    L.lbm_get_schedule.argtypes = [vp]
     L.lbm_macros.restype = C.c_int
     L.lbm_macros.argtypes = [vp, vp, vp, vp, vp]
     L.lbm_reduce.restype = C.c_int
@@ -230,15 +237,35 @@ def lbm_step(h, nsteps, stream):
     _check(load_library().lbm_step(h, int(nsteps), stream), h, "lbm_step")
 
 
-PASSES = ("stream", "zh_fix", "phi_solid", "gradient", "nc_solid",
-          "curvature", "collide")
+# the slots of lbm_step_timed per schedule (None: a slot the schedule
+# leaves empty because the work is part of the next kernel)
+PASSES = {
+    "nodes": ("stream", "zh_fix", "phi_solid", "gradient", "nc_solid",
+              "curvature", "collide"),
+    "tiles": ("pull", "planes", None, "gradient", None, "curvature",
+              "collide"),
+}
+
+
+def lbm_set_schedule(h, schedule: str):
+    _check(load_library().lbm_set_schedule(h, SCHEDULE[schedule]), h,
+           "lbm_set_schedule")
+
+
+def lbm_get_schedule(h) -> str:
+    v = load_library().lbm_get_schedule(h)
+    for k, x in SCHEDULE.items():
+        if x == v:
+            return k
+    raise LbmError(f"lbm_get_schedule: {v}")
 
 
 def lbm_step_timed(h, nsteps, stream) -> dict:
-    ms = (C.c_double * len(PASSES))()
+    names = PASSES[lbm_get_schedule(h)]
+    ms = (C.c_double * len(names))()
     _check(load_library().lbm_step_timed(h, int(nsteps), stream, ms), h,
            "lbm_step_timed")
-    return dict(zip(PASSES, ms[:]))
+    return {n: v for n, v in zip(names, ms[:]) if n is not None}
 
 
 def lbm_macros(h, rho, phi, u, stream):
@@ -291,7 +318,26 @@ def lbm_counts(h):
 def lbm_colour_mass_noalloc(lattice, pops, stream):
     """Red and blue masses of a dense float32 population tensor
     (2, Q, ...) on the device, computed without any device allocation by
-    the library (for callers that cannot allocate; see the C header)."""
+    the library (for callers that cannot allocate; see the C header).
+    The tensor must be a contiguous float32 CUDA tensor on the current
+    device with shape (2, Q, ...); anything else is refused here, before
+    the library sees a pointer."""
+    import torch
+    if lattice not in (9, 19):
+        raise LbmError("lbm_colour_mass_noalloc: lattice must be 9 or 19")
+    if not isinstance(pops, torch.Tensor) or not pops.is_cuda:
+        raise LbmError("lbm_colour_mass_noalloc: pops must be a CUDA tensor")
+    torch = _torch()
+    if pops.device.index != torch.cuda.current_device():
+        raise LbmError("lbm_colour_mass_noalloc: pops is not on the "
+                       "current device")
+    if pops.dtype != torch.float32 or not pops.is_contiguous():
+        raise LbmError("lbm_colour_mass_noalloc: pops must be contiguous "
+                       "float32")
+    if (pops.dim() < 3 or pops.shape[0] != 2 or pops.shape[1] != lattice
+            or pops.numel() % (2 * lattice)):
+        raise LbmError("lbm_colour_mass_noalloc: pops must have shape "
+                       "(2, Q, ...)")
     out = (C.c_double * 2)()
     n = pops.numel() // (2 * lattice)
     _check(load_library().lbm_colour_mass_noalloc(lattice, n, _dptr(pops),
@@ -371,6 +417,14 @@ class Session:
     def step_timed(self, n: int = 1) -> dict:
         """Per-pass milliseconds summed over n steps (CUDA events)."""
         return lbm_step_timed(self.h, n, self.stream())
+
+    def set_schedule(self, schedule: str):
+        """Kernel schedule of step(): "tiles" (default) or "nodes"."""
+        lbm_set_schedule(self.h, schedule)
+
+    @property
+    def schedule(self) -> str:
+        return lbm_get_schedule(self.h)
 
     def macros(self):
         t = self.torch

@@ -92,18 +92,37 @@ def test_batch_entry_points_host_only(lib):
 
 
 def test_pass_list_matches_header_and_byte_model():
-    """lbm_step_timed reports LBM_N_PASSES kernels; the binding names them
-    and bench.py's byte model has an entry for each."""
+    """lbm_step_timed reports LBM_N_PASSES slots in either schedule; the
+    binding names them and bench.py's byte model has an entry for each
+    named pass."""
     import importlib.util
     from paper_2407_10914_gb300 import lbm
     src = open(os.path.join(ROOT, "include", "lbmgb.h")).read()
     n = int(re.search(r"#define LBM_N_PASSES (\d+)", src).group(1))
-    assert len(lbm.PASSES) == n
+    assert set(lbm.PASSES) == set(lbm.SCHEDULE)
+    for sched, v in lbm.SCHEDULE.items():
+        m = re.search(r"LBM_SCHED_%s = (\d+)" % sched.upper(), src)
+        assert m and int(m.group(1)) == v
+        assert len(lbm.PASSES[sched]) == n
     spec = importlib.util.spec_from_file_location(
         "bench_module", os.path.join(ROOT, "bench.py"))
     bench = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(bench)
     for q in (9, 19):
-        pb = bench.pass_bytes(q, 4, 15.0)
-        assert set(pb) == set(lbm.PASSES)
-        assert all(v > 0 for v in pb.values())
+        for sched in lbm.SCHEDULE:
+            pb = bench.pass_bytes(q, 4, sched)
+            assert set(pb) == {p for p in lbm.PASSES[sched] if p}
+            assert all(v > 0 for v in pb.values())
+
+
+def test_noalloc_refuses_host_tensor_before_any_launch():
+    """The binding of lbm_colour_mass_noalloc refuses a host tensor (a
+    host pointer handed to the kernel would be an illegal access) before it
+    reaches the library, GPU or not."""
+    torch = pytest.importorskip("torch")
+    from paper_2407_10914_gb300 import lbm
+    pops = torch.zeros((2, 19, 4, 4, 4), dtype=torch.float32)
+    with pytest.raises(lbm.LbmError, match="CUDA tensor"):
+        lbm.lbm_colour_mass_noalloc(19, pops, None)
+    with pytest.raises(lbm.LbmError, match="lattice"):
+        lbm.lbm_colour_mass_noalloc(7, pops, None)
