@@ -760,20 +760,14 @@ template <int Q>
 __global__ void k_phi_solid_links(Dom d) {
   const int j = blockIdx.x * GBLOCK + threadIdx.x;
   if (j >= d.NS) return;
-  float den = 0.f, sphi = 0.f, ex_pos = 0.f, ex_neg = 0.f;
+  Eq34 acc;
   const int e = d.soff[j + 1];
   for (int p = d.soff[j]; p < e; ++p) {
     const uint32_t l = d.slink[p];
-    const float w = (l >> 31) ? Lattice<Q>::w(Q - 1) : Lattice<Q>::w(1);
-    const float m = d.mf[l & 0x7FFFFFFFu];
-    den += w;
-    sphi += w * m_phi(m);
-    ex_pos += w * m_excess(m, false);
-    ex_neg += w * m_excess(m, true);
+    acc.add((l >> 31) ? Lattice<Q>::w(Q - 1) : Lattice<Q>::w(1),
+            d.mf[l & 0x7FFFFFFFu]);
   }
-  const bool blue = sphi < 0.f;
-  const float ex = (blue ? ex_neg : ex_pos) / den;
-  d.ms[j] = m_pack(blue, blue ? 0.5f * ex : -0.5f * ex);
+  d.ms[j] = acc.finish();
 }
 
 void launch_export_macros(int Q, const Dom &d, float *rho, float *phi,

@@ -48,11 +48,11 @@ __device__ __forceinline__ void stream_node(const Dom &d, int k) {
   dense_store<Q>(d, d.phib, gp, __ldg(d.fflag + k), m);
 }
 
-// App. B on the Zou-He planes (node jz of their list), after stream_node.
-// Its per-colour rules are linear in the populations, and the collision
-// needs only f^t = f^r + f^b and rho^r, rho^b, so the unknown populations
-// are rebuilt in totals: with K0 the sum of the known f^t with e.a = 0, Kin
-// that of the known ones with e.a pointing into the box, and
+// App. B in totals on the pulled f^t of a Zou-He plane node, shared by both
+// step schedules. Its per-colour rules are linear in the populations, and
+// the collision needs only f^t = f^r + f^b and rho^r, rho^b, so the unknown
+// populations are rebuilt in totals: with K0 the sum of the known f^t with
+// e.a = 0, Kin that of the known ones with e.a pointing into the box, and
 // N_t = 1/2 sum_{e.a=0} (e.t) f^t (t != a),
 //   inlet  (B.1-B.8):  j = rho_in - (K0 + 2 Kin),
 //                      f_i = f_opp(i) + 6 w_i j - sum_t (e_i.t) N_t, e_i.a = +1;
@@ -61,22 +61,18 @@ __device__ __forceinline__ void stream_node(const Dom &d, int k) {
 // (chi^r + chi^b = 1). Summing the per-colour rules over i gives the colour
 // densities: rho^s = rho_in zeta^s at the inlet, and at the outlet
 // rho^s = K0^s + 2 Kin^s - j chi^s with chi^r = (1 + phi_out)/2, where the
-// red sums K0^r, Kin^r come from the pull's colour split. The phase field
-// is zeta^r - zeta^b at the inlet and phi(x - a), Eq. (39), at the outlet
-// (the node's own value if that node is solid).
-template <int Q, int ST, bool COH>
-__device__ __forceinline__ void zh_fix_node(const Dom &d, int jz) {
-  // U and R of the node are read and then rewritten by this thread: never
-  // through the read-only path
-  using IO = TIO<Q, ST, true>;
-  const int k = guard(d, __ldg(d.zh_list + jz), d.NF, GUARD_ZOU_HE);
-  const int gp = __ldg(d.fgp + k);
-  const int a = d.c.axis;
-  const bool inlet = __ldg(d.fflag + k) & (2u << (2 * a));
+// red sums K0^r, Kin^r come from the pull's colour split. m: the node's
+// phase field (Eq. 39's value at the outlet); Sown its (q, v). srcS(i, fl),
+// for a known direction i > 0 with e_i.a >= 0, returns the (q, v) of the node
+// the pull took f_i from and sets fl when that node is a fluid source (else
+// it is the node itself, by bounce-back). ft is updated in place (the
+// unknowns only).
+template <int Q, class SrcS>
+__device__ __forceinline__ void zou_he_totals(const StepConst &cc, float *ft,
+                                              bool inlet, float m, float4 Sown,
+                                              SrcS srcS, float &rr, float &rb) {
+  const int a = cc.axis;
   const int in_dir = inlet ? -1 : 1;  // e.a of the known, inward populations
-  float ft[Q];
-#pragma unroll
-  for (int i = 0; i < Q; ++i) ft[i] = IO::load_from(d, d.U, i, k);
   // K0, Kin and N_t from the deviations f_i - w_i rho0 (exact in float32,
   // and small): the weights of the known populations add up to
   // sum_{e.a=0} w + 2 sum_{e.a=in} w = 1 and sum_{e.a=0} (e.t) w = 0, so
@@ -86,36 +82,29 @@ __device__ __forceinline__ void zh_fix_node(const Dom &d, int jz) {
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
     const int ea = Lattice<Q>::e(i, a);
-    const float dv = ft[i] - __fmul_rn(Lattice<Q>::w(i), d.c.rho0);
+    const float dv = __fsub_rn(ft[i], __fmul_rn(Lattice<Q>::w(i), cc.rho0));
     if (ea == 0) {
-      K0 += ft[i];
-      K0d += dv;
+      K0 = __fadd_rn(K0, ft[i]);
+      K0d = __fadd_rn(K0d, dv);
 #pragma unroll
-      for (int t = 0; t < 3; ++t)
-        if (t != a) N[t] += 0.5f * (float)Lattice<Q>::e(i, t) * dv;
+      for (int t = 0; t < 3; ++t) {
+        const int et = Lattice<Q>::e(i, t);
+        if (t != a && et) N[t] = __fadd_rn(N[t], __fmul_rn(et > 0 ? 0.5f : -0.5f, dv));
+      }
     } else if (ea == in_dir) {
-      Kin += ft[i];
-      Kind += dv;
+      Kin = __fadd_rn(Kin, ft[i]);
+      Kind = __fadd_rn(Kind, dv);
     }
   }
-  float rr, rb, m, jt;
+  float jt;
   if (inlet) {
-    jt = (d.c.rho_in_r + d.c.rho_in_b - d.c.rho0) - (K0d + 2.f * Kind);
-    rr = d.c.rho_in_r;
-    rb = d.c.rho_in_b;
-    m = d.c.m_in;
+    jt = __fsub_rn(__fsub_rn(__fadd_rn(cc.rho_in_r, cc.rho_in_b), cc.rho0),
+                   __fmaf_rn(2.f, Kind, K0d));
+    rr = cc.rho_in_r;
+    rb = cc.rho_in_b;
   } else {
-    jt = (K0d + 2.f * Kind) - (d.c.rho_out - d.c.rho0);
-    // the node at x - a
-    const int sa = a == 0 ? 1 : (a == 1 ? d.px : d.px * d.py);
-    const uint32_t e = __ldg(
-        d.nbd + guard(d, gp - sa, d.px * d.py * (d.nz + 2), GUARD_ZOU_HE));
-    const float2 Rk = ldv<true>(d.R + k);
-    m = ((entry_cls(e) & 2) && !entry_out(e))
-            ? ldv<COH>(d.mf + guard(d, entry_idx(e), d.NF, GUARD_ZOU_HE))
-                                               : m_of(Rk.x, Rk.y);
+    jt = __fsub_rn(__fmaf_rn(2.f, Kind, K0d), __fsub_rn(cc.rho_out, cc.rho0));
     // red parts of the known populations (e.a >= 0), as the pull split them
-    const float4 Sown = ldv<COH>(d.S_src + k);
     float K0r = 0.f, Kinr = 0.f;
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
@@ -125,22 +114,18 @@ __device__ __forceinline__ void zh_fix_node(const Dom &d, int jz) {
       if (i == 0) {
         rebuild<Q>(ft[0], Sown, 0, fr, fb);
       } else {
-        const uint32_t es = nb_entry<Q>(d, gp, Lattice<Q>::opp(i));
-        const bool fl = (entry_cls(es) & 2) && !entry_out(es);
-        const float4 S =
-            fl ? ldv<COH>(d.S_src + guard(d, entry_idx(es), d.NF, GUARD_ZOU_HE))
-               : Sown;
-        const float ev = (float)Lattice<Q>::ex(i) * S.y +
-                         (float)Lattice<Q>::ey(i) * S.z +
-                         (float)Lattice<Q>::ez(i) * S.w;
+        bool fl;
+        const float4 S = srcS(i, fl);
+        const float ev = edot<Q>(i, S.y, S.z, S.w);
         rebuild_ev<Q>(ft[i], S.x, fl ? ev : -ev, i, fr, fb);
       }
-      if (ea == 0) K0r += fr;
-      else Kinr += fr;
+      if (ea == 0) K0r = __fadd_rn(K0r, fr);
+      else Kinr = __fadd_rn(Kinr, fr);
     }
-    const float chi_r = 0.5f * (1.f + m_phi(m));
-    rr = K0r + 2.f * Kinr - jt * chi_r;
-    rb = (K0 - K0r) + 2.f * (Kin - Kinr) - jt * (1.f - chi_r);
+    const float chi_r = __fmul_rn(0.5f, __fadd_rn(1.f, m_phi(m)));
+    rr = __fsub_rn(__fmaf_rn(2.f, Kinr, K0r), __fmul_rn(jt, chi_r));
+    rb = __fsub_rn(__fmaf_rn(2.f, __fsub_rn(Kin, Kinr), __fsub_rn(K0, K0r)),
+                   __fmul_rn(jt, __fsub_rn(1.f, chi_r)));
     jt = -jt;  // the outlet rule subtracts 6 w_i j
   }
 #pragma unroll
@@ -148,11 +133,56 @@ __device__ __forceinline__ void zh_fix_node(const Dom &d, int jz) {
     if (Lattice<Q>::e(i, a) != -in_dir) continue;
     float corr = 0.f;
 #pragma unroll
-    for (int t = 0; t < 3; ++t)
-      if (t != a) corr += (float)Lattice<Q>::e(i, t) * N[t];
-    IO::store(d, d.U, i, k,
-              ft[Lattice<Q>::opp(i)] + 6.f * Lattice<Q>::w(i) * jt - corr);
+    for (int t = 0; t < 3; ++t) {
+      const int et = Lattice<Q>::e(i, t);
+      if (t != a && et) corr = __fadd_rn(corr, et > 0 ? N[t] : -N[t]);
+    }
+    ft[i] = __fsub_rn(__fmaf_rn(6.f * Lattice<Q>::w(i), jt, ft[Lattice<Q>::opp(i)]),
+                      corr);
   }
+}
+
+// App. B on the Zou-He planes (node jz of their list), after stream_node:
+// the unknown populations and the colour densities stored back into U and
+// R, and the planes' phase field: zeta^r - zeta^b at the inlet, phi(x - a)
+// (Eq. 39) at the outlet (the node's own value if that node is solid).
+template <int Q, int ST, bool COH>
+__device__ __forceinline__ void zh_fix_node(const Dom &d, int jz) {
+  // U and R of the node are read and then rewritten by this thread: never
+  // through the read-only path
+  using IO = TIO<Q, ST, true>;
+  const int k = guard(d, __ldg(d.zh_list + jz), d.NF, GUARD_ZOU_HE);
+  const int gp = __ldg(d.fgp + k);
+  const int a = d.c.axis;
+  const bool inlet = __ldg(d.fflag + k) & (2u << (2 * a));
+  float ft[Q];
+#pragma unroll
+  for (int i = 0; i < Q; ++i) ft[i] = IO::load_from(d, d.U, i, k);
+  float m;
+  if (inlet) {
+    m = d.c.m_in;
+  } else {
+    const int sa = a == 0 ? 1 : (a == 1 ? d.px : d.px * d.py);
+    const uint32_t e = __ldg(
+        d.nbd + guard(d, gp - sa, d.px * d.py * (d.nz + 2), GUARD_ZOU_HE));
+    const float2 Rk = ldv<true>(d.R + k);
+    m = ((entry_cls(e) & 2) && !entry_out(e))
+            ? ldv<COH>(d.mf + guard(d, entry_idx(e), d.NF, GUARD_ZOU_HE))
+            : m_of(Rk.x, Rk.y);
+  }
+  const float4 Sown = ldv<COH>(d.S_src + k);
+  auto srcS = [&](int i, bool &fl) {
+    const uint32_t es = nb_entry<Q>(d, gp, Lattice<Q>::opp(i));
+    fl = (entry_cls(es) & 2) && !entry_out(es);
+    return fl ? ldv<COH>(d.S_src + guard(d, entry_idx(es), d.NF, GUARD_ZOU_HE))
+              : Sown;
+  };
+  float rr, rb;
+  zou_he_totals<Q>(d.c, ft, inlet, m, Sown, srcS, rr, rb);
+  const int in_dir = inlet ? -1 : 1;
+#pragma unroll
+  for (int i = 0; i < Q; ++i)
+    if (Lattice<Q>::e(i, a) == -in_dir) IO::store(d, d.U, i, k, ft[i]);
   d.R[k] = make_float2(rr, rb);
   d.mf[k] = m;
   dense_store<Q>(d, d.phib, gp, __ldg(d.fflag + k), m);
@@ -168,22 +198,15 @@ __device__ __forceinline__ void phi_solid_node(const Dom &d, int j) {
   // independent loads instead of a walk over the link list
   const uint32_t dirs = __ldg(d.sdir + j);
   const int gp = __ldg(d.sgp + j);
-  float den = 0.f, sphi = 0.f, ex_pos = 0.f, ex_neg = 0.f;
+  Eq34 acc;
 #pragma unroll
   for (int i = 1; i < Q; ++i) {
     if (!(dirs & (1u << i))) continue;
-    const float w = Lattice<Q>::w(i);
-    const float m = ldv<COH>(d.phib + guard(d, gp + dense_off<Q>(d, i),
-                                            d.px * d.py * (d.nz + 2),
-                                            GUARD_STENCIL));
-    den += w;
-    sphi += w * m_phi(m);
-    ex_pos += w * m_excess(m, false);
-    ex_neg += w * m_excess(m, true);
+    acc.add(Lattice<Q>::w(i),
+            ldv<COH>(d.phib + guard(d, gp + dense_off<Q>(d, i),
+                                    d.px * d.py * (d.nz + 2), GUARD_STENCIL)));
   }
-  const bool blue = sphi < 0.f;
-  const float ex = (blue ? ex_neg : ex_pos) / den;  // phi_s - s
-  const float ms = m_pack(blue, blue ? 0.5f * ex : -0.5f * ex);
+  const float ms = acc.finish();
   d.ms[j] = ms;
   dense_store<Q>(d, d.phib, __ldg(d.sgp + j), __ldg(d.sflag + j), ms);
 }
@@ -200,63 +223,37 @@ __device__ __forceinline__ void gradient_node(const Dom &d, int k) {
   // wrapped or clamped neighbour)
   const int gp = __ldg(d.fgp + k);
   const bool own_blue = m_blue(ldv<COH>(d.mf + k));
-  float G[3] = {0.f, 0.f, 0.f};
+  Grad<Q> g;
 #pragma unroll
-  for (int i = 1; i < Q; ++i) {
-    const float m = ldv<COH>(d.phib + guard(d, gp + dense_off<Q>(d, i),
-                                            d.px * d.py * (d.nz + 2),
-                                            GUARD_STENCIL));
-    const float p = 3.f * Lattice<Q>::w(i) * m_excess(m, own_blue);
-    G[0] += (float)Lattice<Q>::ex(i) * p;
-    G[1] += (float)Lattice<Q>::ey(i) * p;
-    G[2] += (float)Lattice<Q>::ez(i) * p;
-  }
-  const float mag = sqrtf(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
-  if (!(mag > EPS_C)) {
-    d.ncf[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-    return;
-  }
-  const float im = 1.f / mag;
-  float nc[3] = {G[0] * im, G[1] * im, G[2] * im};
-  if (d.c.wetting && (__ldg(d.fflag + k) & 1u)) {
-    const float4 w4 = __ldg(d.nw + k);
-    const float nw[3] = {w4.x, w4.y, w4.z};
-    if (nw[0] != 0.f || nw[1] != 0.f || nw[2] != 0.f) {
-      if (d.c.wetting == 1)
-        scheme1(nc, nw, d.c.cos_t);
-      else
-        scheme2(nc, nw, d.c.cos_t, d.c.sin_t);
-    }
-  }
-  d.ncf[k] = make_float4(nc[0], nc[1], nc[2], mag);
+  for (int i = 1; i < Q; ++i)
+    g.add(i,
+          ldv<COH>(d.phib + guard(d, gp + dense_off<Q>(d, i),
+                                  d.px * d.py * (d.nz + 2), GUARD_STENCIL)),
+          own_blue);
+  d.ncf[k] = normal_and_wetting(d.c, g, (__ldg(d.fflag + k) & 1u) != 0, d.nw + k);
 }
 
 // Eq. (35): n_c at solid-boundary node j = w-weighted mean of the fluid
 // neighbours' (post-wetting) n_c, not renormalised.
 template <int Q, bool COH>
 __device__ __forceinline__ void nc_solid_node(const Dom &d, int j) {
-  float num[3] = {0.f, 0.f, 0.f}, den = 0.f;
+  Eq35 acc;
   const int e = __ldg(d.soff + j + 1);
   for (int p = __ldg(d.soff + j); p < e; ++p) {
     const uint32_t l =
         __ldg(d.slink + guard(d, p, (Q - 1) * d.NS, GUARD_LINK));
-    const float w = link_w<Q>(l);
     const float4 v =
         ldv<COH>(d.ncf + guard(d, (int)(l & 0x7FFFFFFFu), d.NF, GUARD_LINK));
-    num[0] += w * v.x;
-    num[1] += w * v.y;
-    num[2] += w * v.z;
-    den += w;
+    acc.add(link_w<Q>(l), v.x, v.y, v.z);
   }
-  const float id = 1.f / den;
-  d.ncs[j] = make_float4(num[0] * id, num[1] * id, num[2] * id, 0.f);
+  d.ncs[j] = acc.finish();
 }
 
 // Eq. (12) with d_b n_a by the Eq. (6) stencil on each component (off-box
 // neighbours clamped); returns kappa and the node's (n_c, |C|).
 template <int Q, bool COH>
 __device__ __forceinline__ float curvature(const Dom &d, int k, float4 &c4) {
-  float dn[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  Curv<Q> cv;
   // n_c from the compact lists through the dense entry box: a dense copy of
   // n_c (as the phase field has) was measured slower, 0.293 against 0.265 ms
   // for the collision: a 16-byte gather from the dense box touches about 3.7
@@ -268,21 +265,10 @@ __device__ __forceinline__ float curvature(const Dom &d, int k, float4 &c4) {
     const bool fl = entry_cls(e) & 2;
     const int idx = guard(d, entry_idx(e), fl ? d.NF : d.NS, GUARD_STENCIL);
     const float4 v = fl ? ldv<COH>(d.ncf + idx) : ldv<COH>(d.ncs + idx);
-    const float w3 = 3.f * Lattice<Q>::w(i);
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const int eb = Lattice<Q>::e(i, b);
-      if (eb == 0) continue;
-      dn[0][b] += w3 * (float)eb * v.x;
-      dn[1][b] += w3 * (float)eb * v.y;
-      dn[2][b] += w3 * (float)eb * v.z;
-    }
+    cv.add(i, v.x, v.y, v.z);
   }
   c4 = ldv<COH>(d.ncf + k);
-  const float nx_ = c4.x, ny_ = c4.y, nz_ = c4.z;
-  return (nx_ * nx_ - 1.f) * dn[0][0] + (ny_ * ny_ - 1.f) * dn[1][1] +
-         (nz_ * nz_ - 1.f) * dn[2][2] + (dn[0][1] + dn[1][0]) * nx_ * ny_ +
-         (dn[0][2] + dn[2][0]) * nx_ * nz_ + (dn[2][1] + dn[1][2]) * nz_ * ny_;
+  return cv.kappa(c4.x, c4.y, c4.z);
 }
 
 // Eq. (12) at fluid node k, stored for the collision pass.
@@ -315,16 +301,12 @@ __device__ __forceinline__ void collide_node(const Dom &d, int k) {
   for (int i = 0; i < Q; ++i) ft[i] = IO::load_from(d, d.U, i, k);
   const float2 R = ldv<COH>(d.R + k);
   const float rr = R.x, rb = R.y;
-  const float rho = rr + rb;
-  const float hk = 0.5f * d.c.gamma * kappa * c4.w;
-  const float F[3] = {hk * c4.x + rho * d.c.g[0], hk * c4.y + rho * d.c.g[1],
-                      hk * c4.z + rho * d.c.g[2]};
-  float u[3];
+  float F[3], u[3];
+  const float rho = force(d.c, rr, rb, kappa, c4, F);
   collide<Q, MRT>(d.c, ft, rho, F, m_phi(ldv<COH>(d.mf + k)), u);
 #pragma unroll
   for (int i = 0; i < Q; ++i) IO::store(d, d.T_dst, i, k, ft[i]);
-  const float seg = d.c.beta * rr * rb / rho;
-  d.S_dst[k] = make_float4(m_of(rr, rb), seg * c4.x, seg * c4.y, seg * c4.z);
+  d.S_dst[k] = recoloured_split(d.c, rr, rb, rho, c4);
   if (MACROS) d.macro[k] = make_float4(u[0], u[1], u[2], rho);
 }
 

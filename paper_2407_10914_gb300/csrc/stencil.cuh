@@ -238,12 +238,31 @@ struct TIO<Q, LBM_STORAGE_BF16, COH> {
 // with ev = e_i.v, the minority colour is mu f''_i -+ w_i ev (exact up to
 // rounding, and to full relative accuracy when that colour is scarce), the
 // majority the rest.
+// Every helper from here on fixes its rounding: each product and sum is one
+// explicit IEEE operation (__fmul_rn, __fadd_rn, __fsub_rn and __fmaf_rn are
+// never fused or reassociated by the compiler). The kernels of both step
+// schedules, the batch and the set-up inline them, so they all compute the
+// same float32 numbers bit for bit; left to the compiler, a*b + c may be
+// fused in one kernel and not in another.
+//
+// e_i . (a, b, c): the components of e_i are 0 or +-1, so the dot product
+// is a signed sum of at most three of a, b, c, in axis order.
+template <int Q>
+__device__ __forceinline__ float edot(int i, float a, float b, float c) {
+  const int ex = Lattice<Q>::ex(i), ey = Lattice<Q>::ey(i), ez = Lattice<Q>::ez(i);
+  float s = ex ? (ex > 0 ? a : -a) : 0.f;
+  if (ey) s = ex ? __fadd_rn(s, ey > 0 ? b : -b) : (ey > 0 ? b : -b);
+  if (ez) s = (ex || ey) ? __fadd_rn(s, ez > 0 ? c : -c) : (ez > 0 ? c : -c);
+  return s;
+}
+
 template <int Q>
 __device__ __forceinline__ void rebuild_ev(float T, float q, float ev, int i,
                                            float &fr, float &fb) {
   const bool blue = m_blue(q);  // blue majority: red is the minority
-  const float minor = q * T + (blue ? Lattice<Q>::w(i) : -Lattice<Q>::w(i)) * ev;
-  const float major = T - minor;  // the minority keeps its relative accuracy
+  const float minor = __fmaf_rn(
+      q, T, __fmul_rn(blue ? Lattice<Q>::w(i) : -Lattice<Q>::w(i), ev));
+  const float major = __fsub_rn(T, minor);  // the minority keeps its accuracy
   fr = blue ? minor : major;
   fb = blue ? major : minor;
 }
@@ -251,10 +270,7 @@ __device__ __forceinline__ void rebuild_ev(float T, float q, float ev, int i,
 template <int Q>
 __device__ __forceinline__ void rebuild(float T, float4 S, int i, float &fr,
                                         float &fb) {
-  const float ev = (float)Lattice<Q>::ex(i) * S.y +
-                   (float)Lattice<Q>::ey(i) * S.z +
-                   (float)Lattice<Q>::ez(i) * S.w;
-  rebuild_ev<Q>(T, S.x, ev, i, fr, fb);
+  rebuild_ev<Q>(T, S.x, edot<Q>(i, S.y, S.z, S.w), i, fr, fb);
 }
 
 __device__ __forceinline__ int axis_coord(int x, int y, int z, int a) {
@@ -266,13 +282,13 @@ __device__ __forceinline__ int axis_extent(const Dom &d, int a) {
 
 // ------------------------------------------------------------ wetting
 __device__ __forceinline__ float dot3(const float *a, const float *b) {
-  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+  return __fmaf_rn(a[2], b[2], __fmaf_rn(a[1], b[1], __fmul_rn(a[0], b[0])));
 }
 
 // Eq. (28): f(v) = v.n_w - |v| cos(theta)
 __device__ __forceinline__ float secant_f(const float *v, const float *nw,
                                           float cth) {
-  return dot3(v, nw) - sqrtf(dot3(v, v)) * cth;
+  return __fsub_rn(dot3(v, nw), __fmul_rn(sqrtf(dot3(v, v)), cth));
 }
 
 // Scheme-I, Eqs. (29)-(31): v0 = n_c, v1 = n_c - (n_c + n_w)/2, three secant
@@ -283,18 +299,19 @@ __device__ __forceinline__ void scheme1(float *nc, const float *nw, float cth) {
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     vm2[a] = nc[a];
-    vm1[a] = nc[a] - 0.5f * (nc[a] + nw[a]);
+    vm1[a] = __fsub_rn(nc[a], __fmul_rn(0.5f, __fadd_rn(nc[a], nw[a])));
   }
 #pragma unroll
   for (int it = 2; it <= 4; ++it) {
     const float f1 = secant_f(vm1, nw, cth);
     const float f2 = secant_f(vm2, nw, cth);
-    const float den = f1 - f2;
+    const float den = __fsub_rn(f1, f2);
     if (fabsf(den) < EPS_SECANT) break;
     const float inv = 1.f / den;
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      const float vn = (vm2[a] * f1 - vm1[a] * f2) * inv;
+      const float vn =
+          __fmul_rn(__fsub_rn(__fmul_rn(vm2[a], f1), __fmul_rn(vm1[a], f2)), inv);
       vm2[a] = vm1[a];
       vm1[a] = vn;
     }
@@ -303,7 +320,7 @@ __device__ __forceinline__ void scheme1(float *nc, const float *nw, float cth) {
   if (m > 0.f) {
     const float im = 1.f / m;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) nc[a] = vm1[a] * im;
+    for (int a = 0; a < 3; ++a) nc[a] = __fmul_rn(vm1[a], im);
   }
 }
 
@@ -317,21 +334,152 @@ __device__ __forceinline__ void scheme1(float *nc, const float *nw, float cth) {
 __device__ __forceinline__ void scheme2(float *nc, const float *nw, float cth,
                                         float sth) {
   const float c = fminf(1.f, fmaxf(-1.f, dot3(nw, nc)));
-  float t[3] = {nc[0] - c * nw[0], nc[1] - c * nw[1], nc[2] - c * nw[2]};
+  float t[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) t[a] = __fsub_rn(nc[a], __fmul_rn(c, nw[a]));
   const float sp = sqrtf(dot3(t, t));
   if (sp < EPS_SIN) return;
   const float k = sth / sp;
   float np_[3], nm_[3], dp = 0.f, dm = 0.f;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    np_[a] = cth * nw[a] + k * t[a];
-    nm_[a] = cth * nw[a] - k * t[a];
-    dp += (np_[a] - nc[a]) * (np_[a] - nc[a]);
-    dm += (nm_[a] - nc[a]) * (nm_[a] - nc[a]);
+    const float cw = __fmul_rn(cth, nw[a]), kt = __fmul_rn(k, t[a]);
+    np_[a] = __fadd_rn(cw, kt);
+    nm_[a] = __fsub_rn(cw, kt);
+    const float ep = __fsub_rn(np_[a], nc[a]), em = __fsub_rn(nm_[a], nc[a]);
+    dp = __fmaf_rn(ep, ep, dp);
+    dm = __fmaf_rn(em, em, dm);
   }
   const bool plus = dp <= dm;
 #pragma unroll
   for (int a = 0; a < 3; ++a) nc[a] = plus ? np_[a] : nm_[a];
+}
+
+// ------------------------------------------------- stencil accumulators
+// Eq. (34): phi at a solid-boundary node, the w-weighted mean over its
+// in-box fluid neighbours, kept in the encoded form (the mean of phi - s for
+// the sign s of the mean). add() once per neighbour in direction order.
+struct Eq34 {
+  float den = 0.f, sphi = 0.f, ex_pos = 0.f, ex_neg = 0.f;
+  __device__ __forceinline__ void add(float w, float m) {
+    den = __fadd_rn(den, w);
+    sphi = __fmaf_rn(w, m_phi(m), sphi);
+    ex_pos = __fmaf_rn(w, m_excess(m, false), ex_pos);
+    ex_neg = __fmaf_rn(w, m_excess(m, true), ex_neg);
+  }
+  __device__ __forceinline__ float finish() const {
+    const bool blue = sphi < 0.f;
+    const float ex = (blue ? ex_neg : ex_pos) / den;  // phi_s - s
+    return m_pack(blue, __fmul_rn(blue ? 0.5f : -0.5f, ex));
+  }
+};
+
+// Eq. (6) (c = dt = 1) as 3 sum_i w_i e_i (phi(x + e_i) - s(x)), the same sum
+// since sum_i w_i e_i = 0, from the encoded neighbour values.
+template <int Q>
+struct Grad {
+  float G[3] = {0.f, 0.f, 0.f};
+  __device__ __forceinline__ void add(int i, float m_nb, bool own_blue) {
+    const float p = __fmul_rn(3.f * Lattice<Q>::w(i), m_excess(m_nb, own_blue));
+    const int e[3] = {Lattice<Q>::ex(i), Lattice<Q>::ey(i), Lattice<Q>::ez(i)};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (e[a]) G[a] = __fadd_rn(G[a], e[a] > 0 ? p : -p);
+  }
+  __device__ __forceinline__ float mag() const { return sqrtf(dot3(G, G)); }
+};
+
+// Eq. (35): n_c at a solid-boundary node, the w-weighted mean of its in-box
+// fluid neighbours' n_c, not renormalised.
+struct Eq35 {
+  float num[3] = {0.f, 0.f, 0.f}, den = 0.f;
+  __device__ __forceinline__ void add(float w, float vx, float vy, float vz) {
+    num[0] = __fmaf_rn(w, vx, num[0]);
+    num[1] = __fmaf_rn(w, vy, num[1]);
+    num[2] = __fmaf_rn(w, vz, num[2]);
+    den = __fadd_rn(den, w);
+  }
+  __device__ __forceinline__ float4 finish() const {
+    const float id = 1.f / den;
+    return make_float4(__fmul_rn(num[0], id), __fmul_rn(num[1], id),
+                       __fmul_rn(num[2], id), 0.f);
+  }
+};
+
+// Eq. (12) with d_b n_a by the Eq. (6) stencil on each component:
+// dn[a][b] = 3 sum_i w_i e_ib n_a(x + e_i).
+template <int Q>
+struct Curv {
+  float dn[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  __device__ __forceinline__ void add(int i, float vx, float vy, float vz) {
+    const float w3 = 3.f * Lattice<Q>::w(i);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int eb = Lattice<Q>::e(i, b);
+      if (eb == 0) continue;
+      const float c = eb > 0 ? w3 : -w3;
+      dn[0][b] = __fmaf_rn(c, vx, dn[0][b]);
+      dn[1][b] = __fmaf_rn(c, vy, dn[1][b]);
+      dn[2][b] = __fmaf_rn(c, vz, dn[2][b]);
+    }
+  }
+  // kappa = sum_ab (n_a n_b - delta_ab) d_b n_a for the node's n_c
+  __device__ __forceinline__ float kappa(float x, float y, float z) const {
+    float k = __fmul_rn(__fmaf_rn(x, x, -1.f), dn[0][0]);
+    k = __fmaf_rn(__fmaf_rn(y, y, -1.f), dn[1][1], k);
+    k = __fmaf_rn(__fmaf_rn(z, z, -1.f), dn[2][2], k);
+    k = __fmaf_rn(__fmul_rn(__fadd_rn(dn[0][1], dn[1][0]), x), y, k);
+    k = __fmaf_rn(__fmul_rn(__fadd_rn(dn[0][2], dn[2][0]), x), z, k);
+    return __fmaf_rn(__fmul_rn(__fadd_rn(dn[2][1], dn[1][2]), z), y, k);
+  }
+};
+
+// Eq. (11) n_c = C/|C| (zero where |C| <= EPS_C: no interface) and, at a
+// fluid-boundary node with wetting on, Scheme-I or Scheme-II turning n_c
+// with |C| kept (Eq. 27); returns (n_c, |C|).
+template <int Q>
+__device__ __forceinline__ float4 normal_and_wetting(const StepConst &c,
+                                                     const Grad<Q> &g,
+                                                     bool fluid_bnd,
+                                                     const float4 *nw_at) {
+  const float mag = g.mag();
+  if (!(mag > EPS_C)) return make_float4(0.f, 0.f, 0.f, 0.f);
+  const float im = 1.f / mag;
+  float nc[3] = {__fmul_rn(g.G[0], im), __fmul_rn(g.G[1], im),
+                 __fmul_rn(g.G[2], im)};
+  if (c.wetting && fluid_bnd) {
+    const float4 w4 = __ldg(nw_at);
+    const float nw[3] = {w4.x, w4.y, w4.z};
+    if (nw[0] != 0.f || nw[1] != 0.f || nw[2] != 0.f) {
+      if (c.wetting == 1)
+        scheme1(nc, nw, c.cos_t);
+      else
+        scheme2(nc, nw, c.cos_t, c.sin_t);
+    }
+  }
+  return make_float4(nc[0], nc[1], nc[2], mag);
+}
+
+// Eq. (5) F = 1/2 gamma kappa C with C = |C| n_c (c4 = (n_c, |C|)), plus the
+// body force rho g (Eq. 36); returns rho = rho^r + rho^b.
+__device__ __forceinline__ float force(const StepConst &c, float rr, float rb,
+                                       float kappa, float4 c4, float *F) {
+  const float rho = __fadd_rn(rr, rb);
+  const float hk = __fmul_rn(__fmul_rn(__fmul_rn(0.5f, c.gamma), kappa), c4.w);
+  F[0] = __fmaf_rn(rho, c.g[0], __fmul_rn(hk, c4.x));
+  F[1] = __fmaf_rn(rho, c.g[1], __fmul_rn(hk, c4.y));
+  F[2] = __fmaf_rn(rho, c.g[2], __fmul_rn(hk, c4.z));
+  return rho;
+}
+
+// The stored colour split of the recoloured state (Eqs. 20-21): q, the
+// encoded rho^r/rho, and v = beta rho^r rho^b / rho n_c.
+__device__ __forceinline__ float4 recoloured_split(const StepConst &c, float rr,
+                                                   float rb, float rho,
+                                                   float4 c4) {
+  const float seg = __fmul_rn(__fmul_rn(c.beta, rr), rb) / rho;
+  return make_float4(m_of(rr, rb), __fmul_rn(seg, c4.x), __fmul_rn(seg, c4.y),
+                     __fmul_rn(seg, c4.z));
 }
 
 // ----------------------------------------------------------- collision
@@ -339,8 +487,9 @@ __device__ __forceinline__ void scheme2(float *nc, const float *nw, float cth,
 __device__ __forceinline__ float relaxation_rate(const StepConst &c,
                                                  float phi) {
   const float pc = fminf(1.f, fmaxf(-1.f, phi));
-  const float inv_nu = (1.f + pc) / (2.f * c.nu_r) + (1.f - pc) / (2.f * c.nu_b);
-  return 1.f / (3.f / inv_nu + 0.5f);
+  const float inv_nu = __fadd_rn(__fadd_rn(1.f, pc) / (2.f * c.nu_r),
+                                 __fsub_rn(1.f, pc) / (2.f * c.nu_b));
+  return 1.f / __fadd_rn(3.f / inv_nu, 0.5f);
 }
 
 // Eq. (2) with one rate S for all non-conserved moments and rate 0 for rho
@@ -372,25 +521,27 @@ __device__ __forceinline__ void collide(const StepConst &c, float *ft,
   float j[3] = {0.f, 0.f, 0.f};
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const float di = ft[i] - __fmul_rn(Lattice<Q>::w(i), c.rho0);
+    const float di = __fsub_rn(ft[i], __fmul_rn(Lattice<Q>::w(i), c.rho0));
     d[i] = di;
-    drho += di;
-    j[0] += (float)Lattice<Q>::ex(i) * di;
-    j[1] += (float)Lattice<Q>::ey(i) * di;
-    j[2] += (float)Lattice<Q>::ez(i) * di;
+    drho = __fadd_rn(drho, di);
+    const int e[3] = {Lattice<Q>::ex(i), Lattice<Q>::ey(i), Lattice<Q>::ez(i)};
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (e[a]) j[a] = __fadd_rn(j[a], e[a] > 0 ? di : -di);
   }
-  rho = c.rho0 + drho;
+  rho = __fadd_rn(c.rho0, drho);
   const float irho = 1.f / rho;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) u[a] = (j[a] + 0.5f * F[a]) * irho;
+  for (int a = 0; a < 3; ++a) u[a] = __fmul_rn(__fmaf_rn(0.5f, F[a], j[a]), irho);
   const float S = relaxation_rate(c, phi);
-  const float uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+  const float uu = dot3(u, u);
   float b[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
-    b[a] = S * (j[a] - c.rho0 * u[a] + 0.5f * F[a]) * (1.f / Lattice<Q>::E2);
-  const float kf = 1.f - 0.5f * S;
-  const float uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+    b[a] = __fmul_rn(__fmul_rn(S, __fmaf_rn(0.5f, F[a], __fmaf_rn(-c.rho0, u[a], j[a]))),
+                     1.f / Lattice<Q>::E2);
+  const float kf = __fsub_rn(1.f, __fmul_rn(0.5f, S));
+  const float uF = dot3(u, F);
   // MRT (D3Q19): Eq. (2) with the rates of Eq. (4), S_e = S_eps = S_pi =
   // S_nu (Eq. 15) and S_q = S_m from Eq. (16). It differs from the
   // single-rate form only in the rows of q (4, 6, 8) and m (16-18) of M
@@ -408,54 +559,58 @@ __device__ __forceinline__ void collide(const StepConst &c, float *ft,
       for (int i = 1; i < Q; ++i) {
         const int ex = Lattice<Q>::ex(i), ey = Lattice<Q>::ey(i),
                   ez = Lattice<Q>::ez(i);
-        const float c5 = (float)(5 * (ex * ex + ey * ey + ez * ez) - 9);
+        const int c5 = 5 * (ex * ex + ey * ey + ez * ez) - 9;
+        const int e[3] = {ex, ey, ez};
+        const int mm[3] = {ex * (ey * ey - ez * ez), ey * (ez * ez - ex * ex),
+                           ez * (ex * ex - ey * ey)};
         const float di = d[i];
-        q[0] += c5 * (float)ex * di;
-        q[1] += c5 * (float)ey * di;
-        q[2] += c5 * (float)ez * di;
-        m[0] += (float)(ex * (ey * ey - ez * ez)) * di;
-        m[1] += (float)(ey * (ez * ez - ex * ex)) * di;
-        m[2] += (float)(ez * (ex * ex - ey * ey)) * di;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          if (e[a]) q[a] = __fmaf_rn((float)(c5 * e[a]), di, q[a]);
+          if (mm[a]) m[a] = __fadd_rn(m[a], mm[a] > 0 ? di : -di);
+        }
       }
-      const float Sq = 8.f * (2.f - S) / (8.f - S);  // Eq. (16)
-      const float dS = Sq - S;
+      const float Sq = 8.f * __fsub_rn(2.f, S) / __fsub_rn(8.f, S);  // Eq. (16)
+      const float dS = __fsub_rn(Sq, S);
+      const float r23 = __fmul_rn(2.f / 3.f, c.rho0);
 #pragma unroll
       for (int a = 0; a < 3; ++a) {
-        aq[a] = -dS * (q[a] + (2.f / 3.f) * c.rho0 * u[a] - (1.f / 3.f) * F[a]) *
-                (1.f / 40.f);
-        am[a] = -dS * m[a] * (1.f / 8.f);
+        const float t = __fmaf_rn(-(1.f / 3.f), F[a], __fmaf_rn(r23, u[a], q[a]));
+        aq[a] = __fmul_rn(__fmul_rn(-dS, t), 1.f / 40.f);
+        am[a] = __fmul_rn(__fmul_rn(-dS, m[a]), 0.125f);
       }
     }
   }
 #pragma unroll
   for (int i = 0; i < Q; ++i) {
-    const float ex = (float)Lattice<Q>::ex(i), ey = (float)Lattice<Q>::ey(i),
-                ez = (float)Lattice<Q>::ez(i);
     const float w = Lattice<Q>::w(i);
-    const float eu = ex * u[0] + ey * u[1] + ez * u[2];
-    const float eF = ex * F[0] + ey * F[1] + ez * F[2];
+    const float eu = edot<Q>(i, u[0], u[1], u[2]);
+    const float eF = edot<Q>(i, F[0], F[1], F[2]);
     // f - feq in deviations: d_i - w_i (drho + rho0 (3 e.u + ...))
-    const float P = 3.f * eu + 4.5f * eu * eu - 1.5f * uu;
+    const float P = __fmaf_rn(-1.5f, uu, __fmaf_rn(__fmul_rn(4.5f, eu), eu,
+                                                   __fmul_rn(3.f, eu)));
     const float dneq =
         __fsub_rn(d[i], __fmul_rn(w, __fmaf_rn(c.rho0, P, drho)));
-    const float guo = w * (3.f * (eF - uF) + 9.f * eu * eF);
+    const float guo = __fmul_rn(
+        w, __fmaf_rn(__fmul_rn(9.f, eu), eF, __fmul_rn(3.f, __fsub_rn(eF, uF))));
     // the update is summed apart from f_i and added last: it keeps the
     // precision of the deviations (the full droplet and tube runs stay
     // within 1e-4 of the FP64 oracle in phi this way, and not when f_i is
-    // updated term by term). The two products are fused explicitly: left
-    // to the compiler, either could join the addition, and kernels that
-    // inline this (the batch's persistent one) differed in the last bit.
+    // updated term by term)
     const float upd = __fmaf_rn(-S, dneq, __fmul_rn(kf, guo));
-    ft[i] = ft[i] + (upd + (ex * b[0] + ey * b[1] + ez * b[2]));
+    ft[i] = __fadd_rn(ft[i], __fadd_rn(upd, edot<Q>(i, b[0], b[1], b[2])));
     if constexpr (Q == 19 && MRT != 0) {
       if (mrt && i > 0) {
         const int ix = Lattice<Q>::ex(i), iy = Lattice<Q>::ey(i),
                   iz = Lattice<Q>::ez(i);
         const float c5 = (float)(5 * (ix * ix + iy * iy + iz * iz) - 9);
-        ft[i] += c5 * (ex * aq[0] + ey * aq[1] + ez * aq[2]) +
-                 (float)(ix * (iy * iy - iz * iz)) * am[0] +
-                 (float)(iy * (iz * iz - ix * ix)) * am[1] +
-                 (float)(iz * (ix * ix - iy * iy)) * am[2];
+        const int mm[3] = {ix * (iy * iy - iz * iz), iy * (iz * iz - ix * ix),
+                           iz * (ix * ix - iy * iy)};
+        float cm = 0.f;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          if (mm[a]) cm = __fadd_rn(cm, mm[a] > 0 ? am[a] : -am[a]);
+        ft[i] = __fadd_rn(ft[i], __fmaf_rn(c5, edot<Q>(i, aq[0], aq[1], aq[2]), cm));
       }
     }
   }

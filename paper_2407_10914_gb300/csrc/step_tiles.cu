@@ -27,8 +27,8 @@
 // both schedules give the same float32 numbers bit for bit.
 #include <cuda_runtime.h>
 
+#include "passes.cuh"
 #include "step.hpp"
-#include "tiles.cuh"
 
 namespace lbm {
 namespace tp {
@@ -105,34 +105,123 @@ __device__ __forceinline__ void slab_of(const Dom &d, int b, int &X0, int &Y0,
   n = end - base;
 }
 
-// Entries of every region cell, one warp per region row.
+// Entry of bit b of a row word, with the OUT flag.
+__device__ __forceinline__ uint32_t entry_of(uint4 w, int b, bool out) {
+  const uint32_t bit = 1u << b;
+  uint32_t e = (w.x & bit) ? w.z + (uint32_t)__popc(w.x & (bit - 1u)) : E_SOLID;
+  if (w.y & bit) e |= E_BND;
+  if (out) e |= E_OUT;
+  return e;
+}
+
+// Canonical position of region row `row`: the tile-row offset of its (y, z)
+// and whether y or z was clamped.
+template <int Q, class R, int H>
+__device__ __forceinline__ void row_of(const Dom &d, int Y0, int Z0, int row,
+                                       int &tyz, int &rw, bool &out) {
+  const int ry = row % R::RY, rz = row / R::RY;
+  out = false;
+  const int y = canon(Y0 - H + ry, d.ny, d.periodic & 2u, out);
+  const int z = Q == 19 ? canon(Z0 - R::HZ + rz, d.nz, d.periodic & 4u, out) : 0;
+  tyz = d.ntx * ((y >> R::LY) + d.nty * (z >> Tile<Q>::LZ));
+  rw = (y & (R::TY - 1)) + R::TY * (z & (R::TZ - 1));
+}
+
+// Entries of every region cell. All global loads are issued together: one
+// thread per region row loads the row word of the block's own x-range, and
+// the halo cells of every row (H on each side) load their own words; the
+// interior cells are then filled from the staged words (W, one per row).
+// The caller synchronises before reading E.
 template <int Q, int H, int SZ>
 __device__ __forceinline__ void stage(const Dom &d, int X0, int Y0, int Z0,
-                                      uint32_t *E) {
+                                      uint32_t *E, uint4 *W) {
   using R = Reg<Q, H, SZ>;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int row = warp; row < R::NROW; row += TB / 32) {
-    const int ry = row % R::RY, rz = row / R::RY;
-    bool out = false;
-    const int y = canon(Y0 - H + ry, d.ny, d.periodic & 2u, out);
-    const int z = Q == 19 ? canon(Z0 - R::HZ + rz, d.nz, d.periodic & 4u, out) : 0;
-    const int tyz = d.ntx * ((y >> R::LY) + d.nty * (z >> Tile<Q>::LZ));
-    const int rw = (y & (R::TY - 1)) + R::TY * (z & (R::TZ - 1));
+  constexpr int NH = 2 * H * R::NROW;
+  constexpr int IT = (NH + TB - 1) / TB;
+  static_assert(R::NROW <= TB, "one row word per thread");
+  const int tid = threadIdx.x;
+  uint4 wo = make_uint4(0u, 0u, 0u, 0u);
+  bool oo = false;
+  if (tid < R::NROW) {
+    int tyz, rw;
+    row_of<Q, R, H>(d, Y0, Z0, tid, tyz, rw, oo);
+    wo = __ldg(d.rows + (size_t)((X0 >> 5) + tyz) * R::RPT + rw);
+  }
+  uint32_t eh[IT];
+  int ch[IT];
 #pragma unroll
-    for (int rx0 = 0; rx0 < R::RX; rx0 += 32) {
-      const int rx = rx0 + lane;
-      if (rx < R::RX) {
-        bool o = out;
-        const int x = canon(X0 - H + rx, d.nx, d.periodic & 1u, o);
-        const uint4 w = __ldg(d.rows + (size_t)((x >> 5) + tyz) * R::RPT + rw);
-        const uint32_t bit = 1u << (x & 31);
-        uint32_t e = (w.x & bit) ? w.z + (uint32_t)__popc(w.x & (bit - 1u))
-                                 : E_SOLID;
-        if (w.y & bit) e |= E_BND;
-        if (o) e |= E_OUT;
-        E[rx + R::RX * row] = e;
-      }
+  for (int it = 0; it < IT; ++it) {
+    const int t = tid + it * TB;
+    ch[it] = -1;
+    eh[it] = 0u;
+    if (t < NH) {
+      const int row = t / (2 * H), p = t % (2 * H);
+      const int rx = p < H ? p : R::RX - 2 * H + p;
+      int tyz, rw;
+      bool o;
+      row_of<Q, R, H>(d, Y0, Z0, row, tyz, rw, o);
+      const int x = canon(X0 - H + rx, d.nx, d.periodic & 1u, o);
+      const uint4 w = __ldg(d.rows + (size_t)((x >> 5) + tyz) * R::RPT + rw);
+      eh[it] = entry_of(w, x & 31, o);
+      ch[it] = rx + R::RX * row;
     }
+  }
+  if (tid < R::NROW) {
+    wo.w = oo ? 1u : 0u;
+    W[tid] = wo;
+  }
+#pragma unroll
+  for (int it = 0; it < IT; ++it)
+    if (ch[it] >= 0) E[ch[it]] = eh[it];
+  __syncthreads();
+  for (int c = tid; c < R::NROW * 32; c += TB) {
+    const int row = c >> 5, lx = c & 31;
+    const uint4 w = W[row];
+    const int x = X0 + lx;
+    uint32_t e;
+    if (x < d.nx) {
+      e = entry_of(w, lx, w.w != 0u);
+    } else {  // past the box's end: wrapped or clamped like a halo cell
+      int tyz, rw;
+      bool o;
+      row_of<Q, R, H>(d, Y0, Z0, row, tyz, rw, o);
+      const int xc = canon(x, d.nx, d.periodic & 1u, o);
+      const uint4 w2 = __ldg(d.rows + (size_t)((xc >> 5) + tyz) * R::RPT + rw);
+      e = entry_of(w2, xc & 31, o);
+    }
+    E[lx + H + R::RX * row] = e;
+  }
+}
+
+// Region cells q of the one-node box (the cells within one node of the
+// slab) of a two-node region.
+template <class R>
+struct Box1 {
+  static constexpr int HZ1 = R::HZ / 2;
+  static constexpr int IX = R::RX - 2, IY = R::RY - 2, IZ = R::RZ - 2 * HZ1;
+  static constexpr int N = IX * IY * IZ;
+  __device__ static constexpr int cell(int q) {
+    return (q % IX + 1) + R::RX * ((q / IX) % IY + 1 + R::RY * (q / (IX * IY) + HZ1));
+  }
+};
+
+// sl[0..*ns) = the one-node box's solid-boundary cells that lie on the box
+// (not OUT): where Eqs. (34)-(35) are evaluated. Warp-aggregated append.
+template <class R>
+__device__ __forceinline__ void solid_list(const uint32_t *E, uint16_t *sl,
+                                           int *ns) {
+  using B = Box1<R>;
+  const int lane = threadIdx.x & 31;
+  for (int q0 = threadIdx.x - lane; q0 < B::N; q0 += TB) {
+    const int q = q0 + lane;
+    const int c = B::cell(q < B::N ? q : 0);
+    const bool want = q < B::N &&
+                      (E[c] & (E_SOLID | E_BND | E_OUT)) == (E_SOLID | E_BND);
+    const unsigned m = __ballot_sync(0xffffffffu, want);
+    int at = 0;
+    if (lane == 0 && m) at = atomicAdd(ns, __popc(m));
+    at = __shfl_sync(0xffffffffu, at, 0);
+    if (want) sl[at + __popc(m & ((1u << lane) - 1u))] = (uint16_t)c;
   }
 }
 
@@ -188,11 +277,12 @@ __global__ void __launch_bounds__(TB, 6) kt_pull(Dom d) {
   using R = Reg<Q, 1, Tile<Q>::TZ>;
   using IO = TIO<Q, ST>;
   __shared__ uint32_t E[R::NC];
+  __shared__ uint4 W[R::NROW];
   __shared__ uint16_t list[R::NOWN];
   int X0, Y0, Z0, base, n;
   slab_of<R>(d, blockIdx.x, X0, Y0, Z0, base, n);
   if (n == 0) return;
-  stage<Q, 1, Tile<Q>::TZ>(d, X0, Y0, Z0, E);
+  stage<Q, 1, Tile<Q>::TZ>(d, X0, Y0, Z0, E, W);
   __syncthreads();
   own_list<Q, 1, Tile<Q>::TZ>(d, X0, Y0, Z0, base, E, list);
   __syncthreads();
@@ -211,13 +301,11 @@ __global__ void __launch_bounds__(TB, 6) kt_pull(Dom d) {
         const int src = guard(d, fl ? e_idx(e) : k, d.NF, GUARD_PULL);
         const float t = IO::load_dyn(d, fl ? i : Lattice<Q>::opp(i), src);
         const float4 S = fl ? __ldg(d.S_src + src) : Sown;
-        const float ev = (float)Lattice<Q>::ex(i) * S.y +
-                         (float)Lattice<Q>::ey(i) * S.z +
-                         (float)Lattice<Q>::ez(i) * S.w;
+        const float ev = edot<Q>(i, S.y, S.z, S.w);
         rebuild_ev<Q>(t, S.x, fl ? ev : -ev, i, fr, fb);
       }
-      rr += fr;
-      rb += fb;
+      rr = __fadd_rn(rr, fr);
+      rb = __fadd_rn(rb, fb);
     }
     d.R[k] = make_float2(rr, rb);
     d.mf[k] = m_of(rr, rb);
@@ -252,47 +340,53 @@ __global__ void __launch_bounds__(TB) kt_planes(Dom d) {
 template <int Q, int SZ>
 __global__ void __launch_bounds__(TB) kt_gradient(Dom d) {
   using R = Reg<Q, 2, SZ>;
+  using B = Box1<R>;
   __shared__ uint32_t E[R::NC];
   __shared__ float P[R::NC];
+  __shared__ uint4 W[R::NROW];
   __shared__ uint16_t list[R::NOWN];
+  __shared__ uint16_t sl[B::N];
+  __shared__ int ns;
   int X0, Y0, Z0, base, n;
   slab_of<R>(d, blockIdx.x, X0, Y0, Z0, base, n);
   if (n == 0) return;
-  stage<Q, 2, SZ>(d, X0, Y0, Z0, E);
+  if (threadIdx.x == 0) ns = 0;
+  stage<Q, 2, SZ>(d, X0, Y0, Z0, E, W);
   __syncthreads();
   own_list<Q, 2, SZ>(d, X0, Y0, Z0, base, E, list);
-  for (int c = threadIdx.x; c < R::NC; c += TB) {
-    const uint32_t e = E[c];
-    if (e_fluid(e)) P[c] = __ldg(d.mf + guard(d, e_idx(e), d.NF, GUARD_STENCIL));
+  solid_list<R>(E, sl, &ns);
+  // the fluid cells' phase field, FU loads in flight per thread
+  constexpr int FU = 8;
+  for (int c0 = threadIdx.x; c0 < R::NC; c0 += TB * FU) {
+    float v[FU];
+#pragma unroll
+    for (int u = 0; u < FU; ++u) {
+      const int c = c0 + u * TB;
+      v[u] = 0.f;
+      if (c < R::NC) {
+        const uint32_t e = E[c];
+        if (e_fluid(e)) v[u] = __ldg(d.mf + guard(d, e_idx(e), d.NF, GUARD_STENCIL));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < FU; ++u)
+      if (c0 + u * TB < R::NC) P[c0 + u * TB] = v[u];
   }
   __syncthreads();
   // Eq. (34) over the in-box fluid neighbours, in direction order
-  constexpr int IX = R::RX - 2, IY = R::RY - 2, IZ = R::RZ - 2 * (R::HZ / 2);
-  constexpr int HZ1 = R::HZ / 2;
-  for (int q = threadIdx.x; q < IX * IY * IZ; q += TB) {
-    const int c = (q % IX + 1) + R::RX * ((q / IX) % IY + 1 + R::RY * (q / (IX * IY) + HZ1));
-    const uint32_t e = E[c];
-    if ((e & (E_SOLID | E_BND | E_OUT)) != (E_SOLID | E_BND)) continue;
-    float den = 0.f, sphi = 0.f, ex_pos = 0.f, ex_neg = 0.f;
+  for (int j = threadIdx.x; j < ns; j += TB) {
+    const int c = sl[j];
+    Eq34 acc;
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      if (!e_link(E[c + R::off(i)])) continue;
-      const float w = Lattice<Q>::w(i);
-      const float m = P[c + R::off(i)];
-      den += w;
-      sphi += w * m_phi(m);
-      ex_pos += w * m_excess(m, false);
-      ex_neg += w * m_excess(m, true);
-    }
-    const bool blue = sphi < 0.f;
-    const float ex = (blue ? ex_neg : ex_pos) / den;
-    P[c] = m_pack(blue, blue ? 0.5f * ex : -0.5f * ex);
+    for (int i = 1; i < Q; ++i)
+      if (e_link(E[c + R::off(i)])) acc.add(Lattice<Q>::w(i), P[c + R::off(i)]);
+    P[c] = acc.finish();
   }
   __syncthreads();
   // a solid cell off a non-periodic face holds the node it stands for
   if (d.periodic != 7u) {
-    for (int q = threadIdx.x; q < IX * IY * IZ; q += TB) {
-      const int c = (q % IX + 1) + R::RX * ((q / IX) % IY + 1 + R::RY * (q / (IX * IY) + HZ1));
+    for (int q = threadIdx.x; q < B::N; q += TB) {
+      const int c = B::cell(q);
       const uint32_t e = E[c];
       if ((e & (E_SOLID | E_OUT)) == (E_SOLID | E_OUT))
         P[c] = P[clamp_cell<Q, 2, SZ>(d, X0, Y0, Z0, c)];
@@ -302,32 +396,10 @@ __global__ void __launch_bounds__(TB) kt_gradient(Dom d) {
   for (int j = threadIdx.x; j < n; j += TB) {
     const int c = R::own(list[j]), k = base + j;
     const bool own_blue = m_blue(P[c]);
-    float G[3] = {0.f, 0.f, 0.f};
+    Grad<Q> g;
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const float p = 3.f * Lattice<Q>::w(i) * m_excess(P[c + R::off(i)], own_blue);
-      G[0] += (float)Lattice<Q>::ex(i) * p;
-      G[1] += (float)Lattice<Q>::ey(i) * p;
-      G[2] += (float)Lattice<Q>::ez(i) * p;
-    }
-    const float mag = sqrtf(G[0] * G[0] + G[1] * G[1] + G[2] * G[2]);
-    if (!(mag > EPS_C)) {
-      d.ncf[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-      continue;
-    }
-    const float im = 1.f / mag;
-    float nc[3] = {G[0] * im, G[1] * im, G[2] * im};
-    if (d.c.wetting && (E[c] & E_BND)) {
-      const float4 w4 = __ldg(d.nw + k);
-      const float nw[3] = {w4.x, w4.y, w4.z};
-      if (nw[0] != 0.f || nw[1] != 0.f || nw[2] != 0.f) {
-        if (d.c.wetting == 1)
-          scheme1(nc, nw, d.c.cos_t);
-        else
-          scheme2(nc, nw, d.c.cos_t, d.c.sin_t);
-      }
-    }
-    d.ncf[k] = make_float4(nc[0], nc[1], nc[2], mag);
+    for (int i = 1; i < Q; ++i) g.add(i, P[c + R::off(i)], own_blue);
+    d.ncf[k] = normal_and_wetting(d.c, g, (E[c] & E_BND) != 0u, d.nw + k);
   }
 }
 
@@ -340,57 +412,72 @@ template <int Q, int SZ>
 __global__ void __launch_bounds__(TB) kt_curvature(Dom d) {
   using R = Reg<Q, 2, SZ>;
   using R1 = Reg<Q, 1, SZ>;
+  using B = Box1<R>;
+  static_assert(B::N == R1::NC, "the one-node box is the one-node region");
   __shared__ uint32_t E[R::NC];
   __shared__ float NX[R1::NC], NY[R1::NC], NZ[R1::NC];
+  __shared__ uint4 W[R::NROW];
   __shared__ uint16_t list[R::NOWN];
+  __shared__ uint16_t sl[B::N];
+  __shared__ int ns;
   int X0, Y0, Z0, base, n;
   slab_of<R>(d, blockIdx.x, X0, Y0, Z0, base, n);
   if (n == 0) return;
-  stage<Q, 2, SZ>(d, X0, Y0, Z0, E);
+  if (threadIdx.x == 0) ns = 0;
+  stage<Q, 2, SZ>(d, X0, Y0, Z0, E, W);
   __syncthreads();
   own_list<Q, 2, SZ>(d, X0, Y0, Z0, base, E, list);
-  // cell q of the one-node region is cell c2(q) of the two-node one
-  auto c2 = [](int q) {
-    return (q % R1::RX + 1) +
-           R::RX * ((q / R1::RX) % R1::RY + 1 + R::RY * (q / (R1::RX * R1::RY) + (R::HZ - R1::HZ)));
-  };
-  for (int q = threadIdx.x; q < R1::NC; q += TB) {
-    const uint32_t e = E[c2(q)];
-    if (e_fluid(e)) {
-      const float4 v = __ldg(d.ncf + guard(d, e_idx(e), d.NF, GUARD_STENCIL));
-      NX[q] = v.x;
-      NY[q] = v.y;
-      NZ[q] = v.z;
+  solid_list<R>(E, sl, &ns);
+  // the fluid cells' n_c within one node of the slab, FU loads in flight
+  constexpr int FU = 4;
+  for (int q0 = threadIdx.x; q0 < R1::NC; q0 += TB * FU) {
+    float4 v[FU];
+#pragma unroll
+    for (int u = 0; u < FU; ++u) {
+      const int q = q0 + u * TB;
+      v[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (q < R1::NC) {
+        const uint32_t e = E[B::cell(q)];
+        if (e_fluid(e)) v[u] = __ldg(d.ncf + guard(d, e_idx(e), d.NF, GUARD_STENCIL));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < FU; ++u) {
+      const int q = q0 + u * TB;
+      if (q < R1::NC) {
+        NX[q] = v[u].x;
+        NY[q] = v[u].y;
+        NZ[q] = v[u].z;
+      }
     }
   }
   __syncthreads();
   // Eq. (35): w-weighted mean of the in-box fluid neighbours' n_c, not
-  // renormalised, in direction order
-  for (int q = threadIdx.x; q < R1::NC; q += TB) {
-    const int c = c2(q);
-    const uint32_t e = E[c];
-    if ((e & (E_SOLID | E_BND | E_OUT)) != (E_SOLID | E_BND)) continue;
-    float num[3] = {0.f, 0.f, 0.f}, den = 0.f;
+  // renormalised, in direction order (terms up to two nodes out are read
+  // from the compact list)
+  for (int j = threadIdx.x; j < ns; j += TB) {
+    const int c = sl[j];
+    Eq35 acc;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       const uint32_t en = E[c + R::off(i)];
       if (!e_link(en)) continue;
-      const float w = Lattice<Q>::w(i);
       const float4 v = __ldg(d.ncf + guard(d, e_idx(en), d.NF, GUARD_LINK));
-      num[0] += w * v.x;
-      num[1] += w * v.y;
-      num[2] += w * v.z;
-      den += w;
+      acc.add(Lattice<Q>::w(i), v.x, v.y, v.z);
     }
-    const float id = 1.f / den;
-    NX[q] = num[0] * id;
-    NY[q] = num[1] * id;
-    NZ[q] = num[2] * id;
+    const float4 nv = acc.finish();
+    // the region cell c is one-node cell q of the same position
+    const int rx = c % R::RX - 1, ry = (c / R::RX) % R::RY - 1,
+              rz = c / (R::RX * R::RY) - B::HZ1;
+    const int q = rx + R1::RX * (ry + R1::RY * rz);
+    NX[q] = nv.x;
+    NY[q] = nv.y;
+    NZ[q] = nv.z;
   }
   __syncthreads();
   if (d.periodic != 7u) {
     for (int q = threadIdx.x; q < R1::NC; q += TB) {
-      const uint32_t e = E[c2(q)];
+      const uint32_t e = E[B::cell(q)];
       if ((e & (E_SOLID | E_OUT)) == (E_SOLID | E_OUT)) {
         const int cc = clamp_cell<Q, 1, SZ>(d, X0, Y0, Z0, q);
         NX[q] = NX[cc];
@@ -402,100 +489,17 @@ __global__ void __launch_bounds__(TB) kt_curvature(Dom d) {
   }
   for (int j = threadIdx.x; j < n; j += TB) {
     const int c = R1::own(list[j]), k = base + j;
-    float dn[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    Curv<Q> cv;
 #pragma unroll
     for (int i = 1; i < Q; ++i) {
       const int cn = c + R1::off(i);
-      const float vx = NX[cn], vy = NY[cn], vz = NZ[cn];
-      const float w3 = 3.f * Lattice<Q>::w(i);
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const int eb = Lattice<Q>::e(i, b);
-        if (eb == 0) continue;
-        dn[0][b] += w3 * (float)eb * vx;
-        dn[1][b] += w3 * (float)eb * vy;
-        dn[2][b] += w3 * (float)eb * vz;
-      }
+      cv.add(i, NX[cn], NY[cn], NZ[cn]);
     }
-    const float nx_ = NX[c], ny_ = NY[c], nz_ = NZ[c];
-    d.kap[k] = (nx_ * nx_ - 1.f) * dn[0][0] + (ny_ * ny_ - 1.f) * dn[1][1] +
-               (nz_ * nz_ - 1.f) * dn[2][2] + (dn[0][1] + dn[1][0]) * nx_ * ny_ +
-               (dn[0][2] + dn[2][0]) * nx_ * nz_ + (dn[2][1] + dn[1][2]) * nz_ * ny_;
+    d.kap[k] = cv.kappa(NX[c], NY[c], NZ[c]);
   }
 }
 
 // ------------------------------------------------------------------ pass 4
-// App. B on a Zou-He plane node, in totals on the pulled f^t (the
-// arithmetic of zh_fix_node): the unknown populations, and the colour
-// densities rho^r, rho^b. m: the node's phase field (Eq. 39's value at the
-// outlet). c: the node's region cell, E the staged entries.
-template <int Q, class R>
-__device__ __forceinline__ void zou_he(const Dom &d, float *ft, bool inlet,
-                                       int k, int c, const uint32_t *E,
-                                       float m, float &rr, float &rb) {
-  const int a = d.c.axis;
-  const int in_dir = inlet ? -1 : 1;
-  float K0 = 0.f, Kin = 0.f, K0d = 0.f, Kind = 0.f, N[3] = {0.f, 0.f, 0.f};
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const int ea = Lattice<Q>::e(i, a);
-    const float dv = ft[i] - __fmul_rn(Lattice<Q>::w(i), d.c.rho0);
-    if (ea == 0) {
-      K0 += ft[i];
-      K0d += dv;
-#pragma unroll
-      for (int t = 0; t < 3; ++t)
-        if (t != a) N[t] += 0.5f * (float)Lattice<Q>::e(i, t) * dv;
-    } else if (ea == in_dir) {
-      Kin += ft[i];
-      Kind += dv;
-    }
-  }
-  float jt;
-  if (inlet) {
-    jt = (d.c.rho_in_r + d.c.rho_in_b - d.c.rho0) - (K0d + 2.f * Kind);
-    rr = d.c.rho_in_r;
-    rb = d.c.rho_in_b;
-  } else {
-    jt = (K0d + 2.f * Kind) - (d.c.rho_out - d.c.rho0);
-    const float4 Sown = __ldg(d.S_src + k);
-    float K0r = 0.f, Kinr = 0.f;
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-      const int ea = Lattice<Q>::e(i, a);
-      if (ea < 0) continue;
-      float fr, fb;
-      if (i == 0) {
-        rebuild<Q>(ft[0], Sown, 0, fr, fb);
-      } else {
-        const uint32_t es = E[c + R::off(Lattice<Q>::opp(i))];
-        const bool fl = e_link(es);
-        const float4 S =
-            fl ? __ldg(d.S_src + guard(d, e_idx(es), d.NF, GUARD_ZOU_HE)) : Sown;
-        const float ev = (float)Lattice<Q>::ex(i) * S.y +
-                         (float)Lattice<Q>::ey(i) * S.z +
-                         (float)Lattice<Q>::ez(i) * S.w;
-        rebuild_ev<Q>(ft[i], S.x, fl ? ev : -ev, i, fr, fb);
-      }
-      if (ea == 0) K0r += fr;
-      else Kinr += fr;
-    }
-    const float chi_r = 0.5f * (1.f + m_phi(m));
-    rr = K0r + 2.f * Kinr - jt * chi_r;
-    rb = (K0 - K0r) + 2.f * (Kin - Kinr) - jt * (1.f - chi_r);
-    jt = -jt;
-  }
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    if (Lattice<Q>::e(i, a) != -in_dir) continue;
-    float corr = 0.f;
-#pragma unroll
-    for (int t = 0; t < 3; ++t)
-      if (t != a) corr += (float)Lattice<Q>::e(i, t) * N[t];
-    ft[i] = ft[Lattice<Q>::opp(i)] + 6.f * Lattice<Q>::w(i) * jt - corr;
-  }
-}
-
 // The pull of f^t again, App. B on the Zou-He planes, Eq. (5) F = 1/2
 // gamma kappa C + rho g (Eq. 36), the collision (Eq. 2) and the store of the
 // recoloured state (f''_i; q and v = beta rho^r rho^b / rho n of Eqs.
@@ -505,11 +509,12 @@ __global__ void __launch_bounds__(TB, MRT ? 3 : 4) kt_collide(Dom d) {
   using R = Reg<Q, 1, Tile<Q>::TZ>;
   using IO = TIO<Q, ST>;
   __shared__ uint32_t E[R::NC];
+  __shared__ uint4 W[R::NROW];
   __shared__ uint16_t list[R::NOWN];
   int X0, Y0, Z0, base, n;
   slab_of<R>(d, blockIdx.x, X0, Y0, Z0, base, n);
   if (n == 0) return;
-  stage<Q, 1, Tile<Q>::TZ>(d, X0, Y0, Z0, E);
+  stage<Q, 1, Tile<Q>::TZ>(d, X0, Y0, Z0, E, W);
   __syncthreads();
   own_list<Q, 1, Tile<Q>::TZ>(d, X0, Y0, Z0, base, E, list);
   __syncthreads();
@@ -531,7 +536,13 @@ __global__ void __launch_bounds__(TB, MRT ? 3 : 4) kt_collide(Dom d) {
     const int ac = axis_pos<R>(X0, Y0, Z0, lp, a);
     if (d.c.zou_he && (ac == 0 || ac == ext - 1)) {
       m = __ldg(d.mf + k);
-      zou_he<Q, R>(d, ft, ac == 0, k, c, E, m, rr, rb);
+      const float4 Sown = __ldg(d.S_src + k);
+      auto srcS = [&](int i, bool &fl) {
+        const uint32_t es = E[c + R::off(Lattice<Q>::opp(i))];
+        fl = e_link(es);
+        return fl ? __ldg(d.S_src + guard(d, e_idx(es), d.NF, GUARD_ZOU_HE)) : Sown;
+      };
+      zou_he_totals<Q>(d.c, ft, ac == 0, m, Sown, srcS, rr, rb);
     } else {
       const float2 Rk = __ldg(d.R + k);
       rr = Rk.x;
@@ -540,22 +551,18 @@ __global__ void __launch_bounds__(TB, MRT ? 3 : 4) kt_collide(Dom d) {
     }
     const float kappa = __ldg(d.kap + k);
     const float4 c4 = __ldg(d.ncf + k);
-    const float rho = rr + rb;
-    const float hk = 0.5f * d.c.gamma * kappa * c4.w;
-    const float F[3] = {hk * c4.x + rho * d.c.g[0], hk * c4.y + rho * d.c.g[1],
-                        hk * c4.z + rho * d.c.g[2]};
-    float u[3];
+    float F[3], u[3];
+    const float rho = force(d.c, rr, rb, kappa, c4, F);
     collide<Q, MRT>(d.c, ft, rho, F, m_phi(m), u);
 #pragma unroll
     for (int i = 0; i < Q; ++i) IO::store(d, d.T_dst, i, k, ft[i]);
-    const float seg = d.c.beta * rr * rb / rho;
-    d.S_dst[k] = make_float4(m_of(rr, rb), seg * c4.x, seg * c4.y, seg * c4.z);
+    d.S_dst[k] = recoloured_split(d.c, rr, rb, rho, c4);
     if (MACROS) d.macro[k] = make_float4(u[0], u[1], u[2], rho);
   }
 }
 
 // ------------------------------------------------------------- launches
-constexpr int SZ_GRAD = 8;  // slab depth of the stencil passes (D3Q19)
+constexpr int SZ_GRAD = 4;  // slab depth of the stencil passes (D3Q19)
 constexpr int SZ_CURV = 4;
 
 template <int Q, int ST>

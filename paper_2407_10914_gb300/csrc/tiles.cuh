@@ -114,13 +114,11 @@ __device__ __forceinline__ void pull_sums(const Dom &d, int k, int gp,
       const int src = guard(d, fl ? entry_idx(e) : k, d.NF, GUARD_PULL);
       ft[i] = IO::load_dyn(d, fl ? i : Lattice<Q>::opp(i), src);
       const float4 S = fl ? ldv<COH>(d.S_src + src) : Sown;
-      const float ev = (float)Lattice<Q>::ex(i) * S.y +
-                       (float)Lattice<Q>::ey(i) * S.z +
-                       (float)Lattice<Q>::ez(i) * S.w;
+      const float ev = edot<Q>(i, S.y, S.z, S.w);
       rebuild_ev<Q>(ft[i], S.x, fl ? ev : -ev, i, fr, fb);
     }
-    rr += fr;
-    rb += fb;
+    rr = __fadd_rn(rr, fr);
+    rb = __fadd_rn(rb, fb);
   }
 }
 

@@ -52,6 +52,12 @@ def fields(s):
             m["rho"].cpu().numpy(), m["u"].cpu().numpy())
 
 
+def where(x, y):
+    """Index and values of the largest difference (for the failure message)."""
+    k = np.unravel_index(np.argmax(np.abs(x - y)), x.shape)
+    return k, float(x[k]), float(y[k])
+
+
 @pytest.mark.parametrize("name,case,dev", CASES, ids=[c[0] for c in CASES])
 def test_schedules_bit_identical_fp32(torch, name, case, dev):
     a, b = pair(case)
@@ -59,8 +65,7 @@ def test_schedules_bit_identical_fp32(torch, name, case, dev):
         a.step(n)
         b.step(n)
         for x, y, what in zip(fields(a), fields(b), ("pops", "phi", "rho", "u")):
-            assert np.array_equal(x, y), (name, n, what,
-                                          float(np.abs(x - y).max()))
+            assert np.array_equal(x, y), (name, n, what, where(x, y))
 
 
 MRT_CASES = [c for c in CASES if c[1].lattice == 19][:4]
@@ -73,7 +78,7 @@ def test_schedules_bit_identical_mrt(torch, name, case, dev):
     a.step(4)
     b.step(4)
     for x, y, what in zip(fields(a), fields(b), ("pops", "phi", "rho", "u")):
-        assert np.array_equal(x, y), (name, what, float(np.abs(x - y).max()))
+        assert np.array_equal(x, y), (name, what, where(x, y))
 
 
 @pytest.mark.parametrize("storage,tol", [("fp16", 1e-4), ("bf16", 1e-3)])
