@@ -17,7 +17,6 @@ One JSON line on rank 0:
   passes     every kernel of the step: CUDA-event time, its own
              algorithmic bytes (pass_bytes below) and ncu DRAM bytes;
              dominant_pass the longest of them;
-  node_schedule  the same rock stepped by the node schedule, for comparison;
   cpu_baseline  the FP64 oracle on a bounded slab of the same rock, on all
              host cores and on one;
   tube       the capillary-tube workload (256 x 20 x 20, r = 8, Type-I,
@@ -64,36 +63,16 @@ METRIC = "MLUPS & % HBM roofline: plain FP32 vs FP16-storage/batched at stated e
 BYTES_POP = {"fp32": 4, "fp16": 2, "bf16": 2}
 
 
-def pass_bytes(Q: int, bpp: int, sched: str = "tiles",
-               cells_per_node: float = 3.66) -> dict:
-    """Algorithmic DRAM bytes per processed node of each pass of a schedule:
-    what the pass must read and write once (a gathered field counts once per
-    node, since every element is read by a fixed number of neighbours that
-    L2 serves). cells_per_node = box cells per fluid node (3.66 on the 256^3
-    rock). The tile passes find their neighbours through the row words
-    (16 B per 32 box cells, 0.5 B per cell); the node passes through the
-    dense entry box (4 B per cell of the padded box), the Eq. 35 pass
-    through its CSR links (4.2 per node on the rock, taken as 5 x 4 B and
-    two offsets), the Eq. 34 pass through a 4 B direction mask."""
-    rw = round(0.5 * cells_per_node, 2)
+def pass_bytes(Q: int, bpp: int, cells_per_node: float = 3.66) -> dict:
+    """Algorithmic DRAM bytes per processed node of each pass: what the pass
+    must read and write once (a gathered field counts once per node, since
+    every element is read by a fixed number of neighbours that L2 serves).
+    Fluid passes find their neighbours in the dense entry box, 4 B per cell
+    of the padded box, read once per pass: cells_per_node = box cells per
+    fluid node (3.66 on the 256^3 rock, 15 B of entries per node); the
+    Eq. 35 pass reads its CSR links (4.2 per node on the rock, taken as
+    5 x 4 B) and two offsets; the Eq. 34 pass a 4 B direction mask."""
     ent = round(4.0 * cells_per_node, 1)
-    if sched == "tiles":
-        return {
-            # T_i of the sources (Q planes), (q, v) 16 B, row words; writes
-            # (rho^r, rho^b) 8 B and the phase field 4 B
-            "pull": Q * bpp + 16 + rw + 8 + 4,
-            # per plane node: flags 1 B, padded index 4 B, the entry of
-            # x - a 4 B, its phase 4 B, (rho^r, rho^b) 8 B; writes the phase
-            "planes": 1 + 4 + 4 + 4 + 8 + 4,
-            # row words, the phase field 4 B, wall normal 16 B at the
-            # fluid-boundary nodes (about 45 %: 7 B); writes (n_c, |C|) 16 B
-            "gradient": rw + 4 + 7 + 16,
-            # row words, (n_c, |C|) 16 B; writes the curvature 4 B
-            "curvature": rw + 16 + 4,
-            # row words, T_i of the sources, (rho^r, rho^b) 8 B, curvature
-            # 4 B, (n_c, |C|) 16 B; writes f'' (Q planes) and (q, v) 16 B
-            "collide": rw + Q * bpp + 8 + 4 + 16 + Q * bpp + 16,
-        }
     return {
         # T_i of the sources (each once), (q, v) 16 B, the entries, flags
         # 1 B, padded index 4 B; writes f^t (Q planes), (rho^r, rho^b) 8 B,
@@ -123,16 +102,11 @@ def pass_bytes(Q: int, bpp: int, sched: str = "tiles",
     }
 
 
-# the kernel of each pass, by schedule (names as ncu lists them)
-PASS_KERNEL = {
-    "tiles": {"pull": "kt_pull", "planes": "kt_planes",
-              "gradient": "kt_gradient", "curvature": "kt_curvature",
-              "collide": "kt_collide"},
-    "nodes": {"stream": "k_stream", "zh_fix": "k_zh_fix",
-              "phi_solid": "k_phi_solid", "gradient": "k_gradient",
-              "nc_solid": "k_nc_solid", "curvature": "k_curvature",
-              "collide": "k_collide"},
-}
+# the kernel of each pass (names as ncu lists them)
+PASS_KERNEL = {"stream": "k_stream", "zh_fix": "k_zh_fix",
+               "phi_solid": "k_phi_solid", "gradient": "k_gradient",
+               "nc_solid": "k_nc_solid", "curvature": "k_curvature",
+               "collide": "k_collide"}
 
 
 def parse():
@@ -164,8 +138,6 @@ def parse():
                     help="skip the gradient (adjoint) object")
     ap.add_argument("--repeats", type=int, default=5,
                     help="repeats of the timed region (median reported)")
-    ap.add_argument("--no-node-schedule", action="store_true",
-                    help="skip timing the node schedule beside the tiles")
     ap.add_argument("--oracle-sample", nargs=3, type=int, default=None,
                     metavar=("PLANES", "STEPS", "SIZE"),
                     help=argparse.SUPPRESS)
@@ -280,7 +252,7 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha1()
-    for f in ("step.cu", "step_tiles.cu", "passes.cuh", "tiles.cuh",
+    for f in ("step.cu", "passes.cuh", "tiles.cuh",
               "stencil.cuh", "lattice.cuh", "context.hpp", "geometry.cu"):
         h.update(open(os.path.join(ROOT, "paper_2407_10914_gb300", "csrc", f),
                       "rb").read())
@@ -358,45 +330,6 @@ def run_oracle_sample(args):
                                           "sample")}), flush=True)
 
 
-def node_schedule(args, torch, lbm, s, Q, bpp, cells, nf, n_sbnd, n_zh,
-                  peak, name):
-    """The same session stepped by the node schedule (seven passes, the
-    streamed populations stored): its step time and per-pass times, for
-    comparison. The session's state advances; its schedule is put back."""
-    stream = torch.cuda.current_stream()
-    s.set_schedule("nodes")
-    steps = min(args.steps, 200)
-    s.step(3)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    s.step(steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    k2 = min(steps, 100)
-    pm = s.step_timed(k2)
-    pb = pass_bytes(Q, bpp, "nodes", cells)
-    n_of = {"stream": nf, "zh_fix": n_zh, "phi_solid": n_sbnd, "gradient": nf,
-            "nc_solid": n_sbnd, "curvature": nf, "collide": nf}
-    out = {"ms_per_step": round(ms, 5),
-           "value": round(nf / (ms * 1e-3) / 1e6, 2), "unit": "MLUPS",
-           "frac": round((2 * 2 * Q * bpp + 4) * nf / (ms * 1e-3) / 1e9 / peak, 4),
-           "passes": {}}
-    for p, t in pm.items():
-        if t <= 0 or n_of[p] == 0:
-            continue
-        t1 = t / k2
-        b = pb[p] * n_of[p]
-        kern = PASS_KERNEL["nodes"][p]
-        out["passes"][p] = {"kernel": kern, "ms": round(t1, 5),
-                            "GBps": round(b / (t1 * 1e-3) / 1e9, 1),
-                            "dram_bytes_per_launch": recorded_traffic(kern, name)}
-    s.set_schedule("tiles")
-    return out
-
-
 def run_reference(args):
     ws, rank, _ = dist_init(args)
     if rank != 0:
@@ -466,15 +399,14 @@ def run_ours(args):
 
     # per-pass times (events inside the library, on the same stream)
     k2 = max(1, min(args.steps, 200))
-    sched = s.schedule
     pass_ms = s.step_timed(k2)
     bpp = BYTES_POP[args.storage]
-    cells = float(case.n_nodes) / nf
-    pb = pass_bytes(Q, bpp, sched, cells)
+    cells = float((case.solid.shape[0] + 2) * (case.solid.shape[1] + 2)
+                  * (case.solid.shape[2] + 2)) / nf
+    pb = pass_bytes(Q, bpp, cells)
     n_zh = s.n_zou_he
-    n_of = {"pull": nf, "planes": n_zh, "stream": nf, "zh_fix": n_zh,
-            "phi_solid": n_sbnd, "gradient": nf, "nc_solid": n_sbnd,
-            "curvature": nf, "collide": nf}
+    n_of = {"stream": nf, "zh_fix": n_zh, "phi_solid": n_sbnd, "gradient": nf,
+            "nc_solid": n_sbnd, "curvature": nf, "collide": nf}
     peak, peak_src = measured_peaks()
     passes_out = {}
     for p, t in pass_ms.items():
@@ -482,7 +414,7 @@ def run_ours(args):
             continue
         t1 = t / k2
         b = pb[p] * n_of[p]
-        kern = PASS_KERNEL[sched][p]
+        kern = PASS_KERNEL[p]
         tr = recorded_traffic(kern, name)
         passes_out[p] = {"kernel": kern, "ms": round(t1, 5),
                          "bytes_per_node": pb[p], "nodes": n_of[p],
@@ -501,10 +433,6 @@ def run_ours(args):
     if passes_out and all(v["dram_bytes_per_launch"] for v in passes_out.values()):
         step_traffic = sum(v["dram_bytes_per_launch"] for v in passes_out.values())
     launches_per_step = len(passes_out)
-    nodes_sched = None
-    if not args.no_node_schedule and rank == 0:
-        nodes_sched = node_schedule(args, torch, lbm, s, Q, bpp, cells, nf,
-                                    n_sbnd, n_zh, peak, name)
 
     e2e = None
     if not args.no_e2e:
@@ -563,7 +491,7 @@ def run_ours(args):
             },
             "roofline": {"bound": "hbm",
                          "kernel": "the whole step (" + ", ".join(
-                             PASS_KERNEL[sched][p] for p in passes_out) + ")",
+                             PASS_KERNEL[p] for p in passes_out) + ")",
                          "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": step_traffic, "peak_source": peak_src,
@@ -579,7 +507,6 @@ def run_ours(args):
                                          "(profiles/dram_traffic.txt, current "
                                          "kernel source only)"},
             "dominant_pass": dict(passes_out[dom], name=dom),
-            "schedule": sched,
             "passes": passes_out,
             "repeats_ms_per_step": [round(x / args.steps, 5) for x in rep_ms],
             "spread_pct": round(100 * (max(rep_ms) - min(rep_ms)) / ms, 2),
@@ -591,8 +518,6 @@ def run_ours(args):
         }
         if clk and clk.get("sm_mhz"):
             line["time_x_sm_mhz"] = round(step_ms * clk["sm_mhz"], 3)
-        if nodes_sched:
-            line["node_schedule"] = nodes_sched
         if e2e:
             line["e2e"] = e2e
         if tube:

@@ -145,40 +145,14 @@ lbm_status lbm_init_state(lbm_handle h, const float *phi0_dev, void *stream);
  * by one. */
 lbm_status lbm_step(lbm_handle h, int nsteps, void *stream);
 
-/* Kernel schedules of a step (lbm_set_schedule). Both compute the same
- * float32 numbers bit for bit (float32 storage; with 16-bit storage the node
- * schedule also rounds the streamed populations to the storage type before
- * the collision, the tile schedule keeps them in float32):
- *   LBM_SCHED_TILES (default): four passes over tiles of the box, each block
- *     staging its tile and a halo of one or two nodes in shared memory;
- *     Eqs. (34)-(35) are evaluated inside the stencil passes and the pull of
- *     Eq. (1) runs twice (for the phase field, then for the collision), so
- *     no streamed copy of the populations is stored;
- *   LBM_SCHED_NODES: seven passes with one thread per node of the compact
- *     fluid or solid-boundary list; the streamed populations are stored
- *     once and read by the collision. */
-enum { LBM_SCHED_TILES = 0, LBM_SCHED_NODES = 1 };
-
-/* Choose the kernel schedule of lbm_step()/lbm_step_timed() for this
- * handle; LBM_ERR_ARG for an unknown value. The next lbm_step() records
- * its graph again. lbm_get_schedule() returns the current one (-1 for a
- * null handle). Batches and the adjoint keep their own kernels. */
-lbm_status lbm_set_schedule(lbm_handle h, int schedule);
-int lbm_get_schedule(lbm_handle h);
-
 /* Kernels of a step, in launch order, as lbm_step_timed() reports them. */
 #define LBM_N_PASSES 7
 /* Profiling form of lbm_step(): the same nsteps steps, with CUDA events
- * recorded on `stream` around each kernel of a step. Node schedule: [0]
- * streaming and the phase field (Eq. 1, Eqs. 7-9); [1] App. B on the
- * Zou-He planes; [2] Eq. (34); [3] colour gradient and wetting (Eqs. 6,
- * 27-33); [4] Eq. (35); [5] curvature (Eq. 12); [6] force, collision and
- * recolouring (Eqs. 5, 2, 20-21). Tile schedule: [0] the pull for the
- * colour densities and phase field; [1] the Zou-He planes' phase field
- * (inlet zeta^r - zeta^b, Eq. 39 at the outlet); [2] 0 (Eq. 34 is part of
- * [3]); [3] Eq. (34), colour gradient and wetting; [4] 0 (Eq. 35 is part of
- * [5]); [5] Eq. (35) and the curvature; [6] the pull again, App. B on the
- * Zou-He planes, force, collision and recolouring.
+ * recorded on `stream` around each kernel of a step: [0] streaming and the
+ * phase field (Eq. 1, Eqs. 7-9); [1] App. B on the Zou-He planes; [2]
+ * Eq. (34); [3] colour gradient and wetting (Eqs. 6, 27-33); [4] Eq. (35);
+ * [5] curvature (Eq. 12); [6] force, collision and recolouring (Eqs. 5, 2,
+ * 20-21).
  * Adds the elapsed milliseconds of each, summed over the steps, to
  * pass_ms[0..LBM_N_PASSES-1] (host array) and synchronises the stream; a
  * kernel that does not run adds about 0. The results equal lbm_step()'s. */

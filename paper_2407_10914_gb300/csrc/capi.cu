@@ -48,7 +48,7 @@ struct Layout {
   size_t ms, ncs, sg, sgp, sflag, sdir;           // S-space
   size_t phib, fgp;                               // dense phase field
   size_t nbd, soff, slink, fflag, zh;             // neighbour lookup
-  size_t map, cls, mask, fbase, sbase, cntf, cnts, g0, g1, rows;
+  size_t map, cls, mask, fbase, sbase, cntf, cnts, g0, g1;
   size_t red, out, cnt, total;
   long long NF, NFp, NS, ntiles;
   int ntx, nty, ntz;
@@ -109,7 +109,6 @@ Layout make_layout(int Q, int nx, int ny, int nz, int storage, long long NF,
   L.map = take((size_t)N * 2);
   L.cls = take((size_t)N);
   L.mask = take((size_t)N);
-  L.rows = take((size_t)L.ntiles * TY * TZ * 16);
   L.fbase = take((size_t)(L.ntiles + 1) * 4);
   L.sbase = take((size_t)(L.ntiles + 1) * 4);
   L.cntf = take((size_t)L.ntiles * 4);
@@ -237,8 +236,6 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
   d.sdir = (const uint32_t *)(base + L.sdir);
   d.px = nx + 2;
   d.py = ny + 2;
-  d.rows = (const uint4 *)(base + L.rows);
-  d.sched = LBM_SCHED_TILES;
   d.err = (unsigned *)(c->counters + 3);  // zeroed with the counters at set-up
   cudaError_t e = cudaMemcpyAsync(c->mask, solid_host, (size_t)N,
                                   cudaMemcpyHostToDevice, s);
@@ -287,6 +284,8 @@ lbm_status lbm_set_params(lbm_handle c, const lbm_params *p) {
   lbm::StepConst &k = c->d.c;
   k.nu_r = (float)((p->tau_r - 0.5) / 3.0);
   k.nu_b = (float)((p->tau_b - 0.5) / 3.0);
+  k.h_r = (float)(1.5 / (p->tau_r - 0.5));
+  k.h_b = (float)(1.5 / (p->tau_b - 0.5));
   k.gamma = (float)p->gamma;
   k.beta = (float)p->beta;
   k.rho0 = (float)p->rho0;
@@ -391,19 +390,6 @@ lbm_status lbm_step(lbm_handle c, int nsteps, void *stream) {
   return LBM_OK;
 }
 
-lbm_status lbm_set_schedule(lbm_handle c, int schedule) {
-  if (!c) return LBM_ERR_ARG;
-  if (schedule != LBM_SCHED_TILES && schedule != LBM_SCHED_NODES)
-    return fail(c, LBM_ERR_ARG, "schedule must be LBM_SCHED_TILES or LBM_SCHED_NODES");
-  if (c->d.sched != schedule) {
-    c->d.sched = schedule;
-    ++c->pgen;  // the recorded step graphs hold the other kernels
-  }
-  return LBM_OK;
-}
-
-int lbm_get_schedule(lbm_handle c) { return c ? c->d.sched : -1; }
-
 lbm_status lbm_step_timed(lbm_handle c, int nsteps, void *stream,
                           double *pass_ms) {
   if (!c || nsteps < 0 || !pass_ms) return LBM_ERR_ARG;
@@ -439,7 +425,7 @@ lbm_status lbm_macros(lbm_handle c, float *rho, float *phi, float *u,
                       void *stream) {
   if (!c) return LBM_ERR_ARG;
   if (!c->state_set) return fail(c, LBM_ERR_STATE, "init the state first");
-  lbm::launch_export_macros(c->Q, c->d, rho, phi, u, (cudaStream_t)stream);
+  lbm::launch_export_macros(c->d, rho, phi, u, (cudaStream_t)stream);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "macros");
   return LBM_OK;

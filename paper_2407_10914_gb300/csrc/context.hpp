@@ -36,6 +36,7 @@ enum : uint8_t {
 // Constants of the step as the kernels use them (float, precomputed).
 struct StepConst {
   float nu_r, nu_b;  // kinematic viscosities
+  float h_r, h_b;    // 1 / (2 nu^r), 1 / (2 nu^b) (Eq. 14's halves)
   float gamma, beta, rho0;
   float cos_t, sin_t;
   int wetting, zou_he, axis;
@@ -100,13 +101,6 @@ struct Dom {
   // the directions of its links, so that Eq. 34 reads the dense box
   const uint32_t *sdir;
   int px, py;
-  // per row of a tile (TX = 32 cells at fixed y, z; tiles.cuh): the fluid
-  // bits, the boundary bits (solid-boundary for a solid cell,
-  // fluid-boundary for a fluid one; bit x of the row is cell X0 + x) and the
-  // F-index of the row's first fluid node. The tile passes of step_tiles.cu
-  // find every neighbour's F-index from these, 0.5 B per box cell.
-  const uint4 *rows;    // [ntiles * rows per tile]
-  int sched;            // LBM_SCHED_TILES or LBM_SCHED_NODES (lbm_step)
   unsigned *err;        // error word of the bounds-checked build (guard())
   StepConst c;
 };

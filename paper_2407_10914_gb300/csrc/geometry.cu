@@ -165,8 +165,13 @@ static void scan_exclusive(const int *in, int *out, long long n, int *bsum,
 }
 
 // One block per tile: rank of each node among the nodes of its kind in the
-// tile, in (z, y, x) order; map = (class << 14) | rank; the F and S lists
-// hold box indices.
+// tile; map = (class << 14) | rank; the F and S lists hold box indices.
+// Fluid nodes on the two x faces of the box (x = 0, x = nx - 1) come first
+// in their tile, then the tile's other fluid nodes in (z, y, x) order;
+// solid-boundary nodes in (z, y, x) order. With the x faces leading, the
+// Zou-He planes of an x-axis flow are runs of consecutive F indices (the
+// fix-up pass reads and writes them coalesced) instead of nodes a tile row
+// apart; for every other node the order is the plain tile order.
 template <int Q>
 __global__ void k_tile_map(Dom d, uint16_t *__restrict__ map,
                            int *__restrict__ fg, int *__restrict__ sg) {
@@ -184,82 +189,53 @@ __global__ void k_tile_map(Dom d, uint16_t *__restrict__ map,
     carry_s = 0;
   }
   __syncthreads();
-  for (int c0 = 0; c0 < G::TN; c0 += GBLOCK) {
-    const int lp = c0 + threadIdx.x;
-    int x, y, z;
-    local_node<Q>(lp, X0, Y0, Z0, x, y, z);
-    const bool valid = x < d.nx && y < d.ny && z < d.nz;
-    const int g = valid ? x + d.nx * (y + d.ny * z) : 0;
-    const int c = valid ? d.cls[g] : CLS_SOLID;
-    const bool isf = valid && (c & 2);
-    const bool iss = valid && c == CLS_SOLID_BND;
-    const unsigned bf = __ballot_sync(0xffffffffu, isf);
-    const unsigned bs = __ballot_sync(0xffffffffu, iss);
-    if (lane == 0) {
-      wf[warp] = __popc(bf);
-      ws[warp] = __popc(bs);
-    }
-    __syncthreads();
-    int of = carry_f, os = carry_s;
-    for (int w = 0; w < warp; ++w) {
-      of += wf[w];
-      os += ws[w];
-    }
-    if (valid) {
-      int rank = 0;
-      if (isf) {
-        rank = of + __popc(bf & lt);
-        fg[d.fbase[t] + rank] = g;
-      } else if (iss) {
-        rank = os + __popc(bs & lt);
-        sg[d.sbase[t] + rank] = g;
+  // pass 0: the x-face fluid nodes (tiles on an x face only); pass 1: the rest
+  const bool face_tile = X0 == 0 || X0 + G::TX >= d.nx;
+  for (int pass = face_tile ? 0 : 1; pass < 2; ++pass) {
+    for (int c0 = 0; c0 < G::TN; c0 += GBLOCK) {
+      const int lp = c0 + threadIdx.x;
+      int x, y, z;
+      local_node<Q>(lp, X0, Y0, Z0, x, y, z);
+      const bool valid = x < d.nx && y < d.ny && z < d.nz;
+      const int g = valid ? x + d.nx * (y + d.ny * z) : 0;
+      const int c = valid ? d.cls[g] : CLS_SOLID;
+      const bool face = x == 0 || x == d.nx - 1;
+      const bool fluid = valid && (c & 2);
+      const bool isf = fluid && (pass == 0 ? face : !(face && face_tile));
+      const bool iss = pass == 1 && valid && c == CLS_SOLID_BND;
+      const unsigned bf = __ballot_sync(0xffffffffu, isf);
+      const unsigned bs = __ballot_sync(0xffffffffu, iss);
+      if (lane == 0) {
+        wf[warp] = __popc(bf);
+        ws[warp] = __popc(bs);
       }
-      map[g] = (uint16_t)((c << 14) | rank);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      for (int w = 0; w < GBLOCK / 32; ++w) {
-        carry_f += wf[w];
-        carry_s += ws[w];
+      __syncthreads();
+      int of = carry_f, os = carry_s;
+      for (int w = 0; w < warp; ++w) {
+        of += wf[w];
+        os += ws[w];
       }
-    }
-    __syncthreads();
-  }
-}
-
-// One block per tile: the row words of the tile (Dom::rows). Row r = ly +
-// TY lz holds the cells X0 .. X0 + 31 at (Y0 + ly, Z0 + lz): x = fluid bits,
-// y = boundary bits (class bit 0: solid-boundary or fluid-boundary), z =
-// F-index of the row's first fluid node (fluid nodes are ranked in (z, y,
-// x) order within the tile, so a fluid cell's F-index is z plus the fluid
-// bits below it). Cells past the box's end are solid.
-template <int Q>
-__global__ void k_tile_rows(Dom d, uint4 *__restrict__ rows) {
-  using G = TileGeo<Q>;
-  constexpr int RPT = G::TY * G::TZ;
-  __shared__ unsigned fb[RPT];
-  const int t = blockIdx.x;
-  const int X0 = (t % d.ntx) * G::TX;
-  const int q = t / d.ntx;
-  const int Y0 = (q % d.nty) * G::TY, Z0 = (q / d.nty) * G::TZ;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int r = warp; r < RPT; r += GBLOCK / 32) {
-    const int x = X0 + lane, y = Y0 + r % G::TY, z = Z0 + r / G::TY;
-    const bool valid = x < d.nx && y < d.ny && z < d.nz;
-    const int c = valid ? d.cls[x + d.nx * (y + d.ny * z)] : CLS_SOLID;
-    const unsigned f = __ballot_sync(0xffffffffu, (c & 2) != 0);
-    const unsigned b = __ballot_sync(0xffffffffu, (c & 1) != 0);
-    if (lane == 0) {
-      fb[r] = f;
-      rows[(size_t)t * RPT + r] = make_uint4(f, b, 0u, 0u);
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned base = (unsigned)d.fbase[t];
-    for (int r = 0; r < RPT; ++r) {
-      rows[(size_t)t * RPT + r].z = base;
-      base += __popc(fb[r]);
+      // the node's map entry is written in the pass that ranks it (every
+      // node that is not fluid in pass 1)
+      if (valid && (isf || (pass == 1 && !fluid))) {
+        int rank = 0;
+        if (isf) {
+          rank = of + __popc(bf & lt);
+          fg[d.fbase[t] + rank] = g;
+        } else if (iss) {
+          rank = os + __popc(bs & lt);
+          sg[d.sbase[t] + rank] = g;
+        }
+        map[g] = (uint16_t)((c << 14) | rank);
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        for (int w = 0; w < GBLOCK / 32; ++w) {
+          carry_f += wf[w];
+          carry_s += ws[w];
+        }
+      }
+      __syncthreads();
     }
   }
 }
@@ -490,11 +466,6 @@ cudaError_t build_geometry(lbm_ctx *c, cudaStream_t s) {
     k_tile_map<19><<<nt, GBLOCK, 0, s>>>(d, map, fg, sg);
   else
     k_tile_map<9><<<nt, GBLOCK, 0, s>>>(d, map, fg, sg);
-  uint4 *rows = const_cast<uint4 *>(d.rows);
-  if (c->Q == 19)
-    k_tile_rows<19><<<nt, GBLOCK, 0, s>>>(d, rows);
-  else
-    k_tile_rows<9><<<nt, GBLOCK, 0, s>>>(d, rows);
   int tot[2] = {0, 0};
   cudaError_t e = cudaMemcpyAsync(&tot[0], d.fbase + c->ntiles, sizeof(int),
                                   cudaMemcpyDeviceToHost, s);
@@ -753,34 +724,11 @@ __global__ void k_export_macros(Dom d, float *__restrict__ rho,
   if (k < d.NS && phi) phi[d.sg[k]] = m_phi(d.ms[k]);
 }
 
-// Eq. (34) at solid-boundary node j from the fluid nodes' encoded phase
-// field, over its links (the in-box fluid neighbours in direction order, as
-// phi_solid_node sums them): the value the step's stencils used.
-template <int Q>
-__global__ void k_phi_solid_links(Dom d) {
-  const int j = blockIdx.x * GBLOCK + threadIdx.x;
-  if (j >= d.NS) return;
-  Eq34 acc;
-  const int e = d.soff[j + 1];
-  for (int p = d.soff[j]; p < e; ++p) {
-    const uint32_t l = d.slink[p];
-    acc.add((l >> 31) ? Lattice<Q>::w(Q - 1) : Lattice<Q>::w(1),
-            d.mf[l & 0x7FFFFFFFu]);
-  }
-  d.ms[j] = acc.finish();
-}
-
-void launch_export_macros(int Q, const Dom &d, float *rho, float *phi,
-                          float *u, cudaStream_t s) {
+void launch_export_macros(const Dom &d, float *rho, float *phi, float *u,
+                          cudaStream_t s) {
   if (rho) cudaMemsetAsync(rho, 0, sizeof(float) * (size_t)d.N, s);
   if (phi) cudaMemsetAsync(phi, 0, sizeof(float) * (size_t)d.N, s);
   if (u) cudaMemsetAsync(u, 0, sizeof(float) * 3 * (size_t)d.N, s);
-  if (phi && d.NS > 0) {
-    if (Q == 19)
-      k_phi_solid_links<19><<<gblocks(d.NS), GBLOCK, 0, s>>>(d);
-    else
-      k_phi_solid_links<9><<<gblocks(d.NS), GBLOCK, 0, s>>>(d);
-  }
   const long long n = d.NF > d.NS ? d.NF : d.NS;
   k_export_macros<<<gblocks(n), GBLOCK, 0, s>>>(d, rho, phi, u);
 }

@@ -46,6 +46,11 @@ struct Lattice<19> {
                            7, 14, 13, 12, 11, 18, 17, 16, 15};
     return O[i];
   }
+  // the first member of the p-th opposite pair (the other is opp(pair(p)))
+  __host__ __device__ static constexpr int pair(int p) {
+    constexpr int P[9] = {1, 3, 5, 7, 8, 11, 12, 15, 16};
+    return P[p];
+  }
 };
 
 template <>
@@ -73,6 +78,10 @@ struct Lattice<9> {
   __host__ __device__ static constexpr int opp(int i) {
     constexpr int O[9] = {0, 2, 1, 4, 3, 8, 7, 6, 5};
     return O[i];
+  }
+  __host__ __device__ static constexpr int pair(int p) {
+    constexpr int P[4] = {1, 3, 5, 6};
+    return P[p];
   }
 };
 

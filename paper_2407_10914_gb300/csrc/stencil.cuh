@@ -486,10 +486,12 @@ __device__ __forceinline__ float4 recoloured_split(const StepConst &c, float rr,
 // Eqs. (13)-(14): S_nu from the harmonic-mean viscosity (phi clamped).
 __device__ __forceinline__ float relaxation_rate(const StepConst &c,
                                                  float phi) {
+  // 1/nu = (1 + phi)/(2 nu^r) + (1 - phi)/(2 nu^b); 1/S = 3 nu + 1/2, so
+  // S = (1/nu) / (3 + (1/nu)/2): one division
   const float pc = fminf(1.f, fmaxf(-1.f, phi));
-  const float inv_nu = __fadd_rn(__fadd_rn(1.f, pc) / (2.f * c.nu_r),
-                                 __fsub_rn(1.f, pc) / (2.f * c.nu_b));
-  return 1.f / __fadd_rn(3.f / inv_nu, 0.5f);
+  const float inv_nu =
+      __fmaf_rn(__fadd_rn(1.f, pc), c.h_r, __fmul_rn(__fsub_rn(1.f, pc), c.h_b));
+  return inv_nu / __fmaf_rn(0.5f, inv_nu, 3.f);
 }
 
 // Eq. (2) with one rate S for all non-conserved moments and rate 0 for rho
@@ -517,17 +519,30 @@ __device__ __forceinline__ void collide(const StepConst &c, float *ft,
   // an FMA), so every kernel that inlines this function computes the same
   // d_i bit for bit.
   (void)rho;
-  float d[Q], drho = 0.f;
-  float j[3] = {0.f, 0.f, 0.f};
+  // Directions come in opposite pairs (i, opp(i)) with e_opp = -e_i and equal
+  // weights: per pair, e.u, e.F and e.b change sign, the rest is shared, and
+  // the two populations are updated with packed two-lane float32 operations
+  // (FFMA2 / FADD2 / FMUL2; each lane rounds as its scalar op).
+  constexpr int NP = (Q - 1) / 2;
+  float d[Q], drho, j[3] = {0.f, 0.f, 0.f};
+  {
+    d[0] = __fsub_rn(ft[0], __fmul_rn(Lattice<Q>::w(0), c.rho0));
+    drho = d[0];
 #pragma unroll
-  for (int i = 0; i < Q; ++i) {
-    const float di = __fsub_rn(ft[i], __fmul_rn(Lattice<Q>::w(i), c.rho0));
-    d[i] = di;
-    drho = __fadd_rn(drho, di);
-    const int e[3] = {Lattice<Q>::ex(i), Lattice<Q>::ey(i), Lattice<Q>::ez(i)};
+    for (int p = 0; p < NP; ++p) {
+      const int i = Lattice<Q>::pair(p), o = Lattice<Q>::opp(i);
+      const float wr = __fmul_rn(Lattice<Q>::w(i), c.rho0);
+      const float2 dd = __fadd2_rn(make_float2(ft[i], ft[o]), make_float2(-wr, -wr));
+      d[i] = dd.x;
+      d[o] = dd.y;
+      // s = d_i + d_o (mass), t = d_i - d_o (momentum along e_i)
+      const float2 st = __fadd2_rn(make_float2(dd.x, dd.x), make_float2(dd.y, -dd.y));
+      drho = __fadd_rn(drho, st.x);
+      const int e[3] = {Lattice<Q>::ex(i), Lattice<Q>::ey(i), Lattice<Q>::ez(i)};
 #pragma unroll
-    for (int a = 0; a < 3; ++a)
-      if (e[a]) j[a] = __fadd_rn(j[a], e[a] > 0 ? di : -di);
+      for (int a = 0; a < 3; ++a)
+        if (e[a]) j[a] = __fadd_rn(j[a], e[a] > 0 ? st.y : -st.y);
+    }
   }
   rho = __fadd_rn(c.rho0, drho);
   const float irho = 1.f / rho;
@@ -581,26 +596,51 @@ __device__ __forceinline__ void collide(const StepConst &c, float *ft,
       }
     }
   }
-#pragma unroll
-  for (int i = 0; i < Q; ++i) {
+  // f''_i = f_i + upd_i + e_i.b with, in deviations,
+  //   f - feq = d_i - w_i (drho + rho0 P_i),  P_i = 3 e.u + 4.5 (e.u)^2 - 1.5 u.u,
+  //   upd_i = -S (f - feq) + (1 - S/2) w_i (3 (e.F - u.F) + 9 (e.u)(e.F));
+  // the update is summed apart from f_i and added last (it keeps the
+  // precision of the deviations: the full droplet and tube runs stay within
+  // 1e-4 of the FP64 oracle in phi this way, and not when f_i is updated
+  // term by term)
+  const float m15uu = __fmul_rn(-1.5f, uu), m3uF = __fmul_rn(-3.f, uF);
+  auto pair_update = [&](int i, int o) {
     const float w = Lattice<Q>::w(i);
     const float eu = edot<Q>(i, u[0], u[1], u[2]);
     const float eF = edot<Q>(i, F[0], F[1], F[2]);
-    // f - feq in deviations: d_i - w_i (drho + rho0 (3 e.u + ...))
-    const float P = __fmaf_rn(-1.5f, uu, __fmaf_rn(__fmul_rn(4.5f, eu), eu,
-                                                   __fmul_rn(3.f, eu)));
-    const float dneq =
-        __fsub_rn(d[i], __fmul_rn(w, __fmaf_rn(c.rho0, P, drho)));
-    const float guo = __fmul_rn(
-        w, __fmaf_rn(__fmul_rn(9.f, eu), eF, __fmul_rn(3.f, __fsub_rn(eF, uF))));
-    // the update is summed apart from f_i and added last: it keeps the
-    // precision of the deviations (the full droplet and tube runs stay
-    // within 1e-4 of the FP64 oracle in phi this way, and not when f_i is
-    // updated term by term)
-    const float upd = __fmaf_rn(-S, dneq, __fmul_rn(kf, guo));
-    ft[i] = __fadd_rn(ft[i], __fadd_rn(upd, edot<Q>(i, b[0], b[1], b[2])));
-    if constexpr (Q == 19 && MRT != 0) {
-      if (mrt && i > 0) {
+    const float eb = edot<Q>(i, b[0], b[1], b[2]);
+    const float A = __fmaf_rn(__fmul_rn(4.5f, eu), eu, m15uu);  // shared part of P
+    const float t3 = __fmul_rn(3.f, eu);
+    const float G0 = __fmaf_rn(__fmul_rn(9.f, eu), eF, m3uF);  // shared part of G/w
+    const float t4 = __fmul_rn(3.f, eF);
+    const float2 P = __fadd2_rn(make_float2(A, A), make_float2(t3, -t3));
+    const float2 X = __ffma2_rn(make_float2(c.rho0, c.rho0), P, make_float2(drho, drho));
+    const float2 dneq = __ffma2_rn(make_float2(-w, -w), X, make_float2(d[i], d[o]));
+    const float2 g = __fmul2_rn(make_float2(w, w),
+                                __fadd2_rn(make_float2(G0, G0), make_float2(t4, -t4)));
+    const float2 upd = __ffma2_rn(make_float2(-S, -S), dneq,
+                                  __fmul2_rn(make_float2(kf, kf), g));
+    const float2 nf = __fadd2_rn(make_float2(ft[i], ft[o]),
+                                 __fadd2_rn(upd, make_float2(eb, -eb)));
+    ft[i] = nf.x;
+    ft[o] = nf.y;
+  };
+  {
+    // rest population: e_0 = 0
+    const float X0 = __fmaf_rn(c.rho0, m15uu, drho);
+    const float dneq0 = __fmaf_rn(-Lattice<Q>::w(0), X0, d[0]);
+    const float g0 = __fmul_rn(Lattice<Q>::w(0), m3uF);
+    ft[0] = __fadd_rn(ft[0], __fmaf_rn(-S, dneq0, __fmul_rn(kf, g0)));
+  }
+#pragma unroll
+  for (int p = 0; p < NP; ++p) {
+    const int i = Lattice<Q>::pair(p);
+    pair_update(i, Lattice<Q>::opp(i));
+  }
+  if constexpr (Q == 19 && MRT != 0) {
+    if (mrt) {
+#pragma unroll
+      for (int i = 1; i < Q; ++i) {
         const int ix = Lattice<Q>::ex(i), iy = Lattice<Q>::ey(i),
                   iz = Lattice<Q>::ez(i);
         const float c5 = (float)(5 * (ix * ix + iy * iy + iz * iz) - 9);

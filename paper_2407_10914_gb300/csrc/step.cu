@@ -1,6 +1,5 @@
-// The time step as seven node passes (schedule LBM_SCHED_NODES; the default
-// schedule is the tile passes of step_tiles.cu). Each pass needs the
-// previous one's values at lattice neighbours:
+// The time step as seven dependent passes. Each pass needs the previous
+// one's values at lattice neighbours:
 //   1 k_stream     (fluid)  pull of Eq. (1), Eqs. (7)-(9): stores f^t,
 //                  (rho^r, rho^b) and the phase field; k_zh_fix then applies
 //                  App. B on the Zou-He planes
@@ -171,18 +170,12 @@ static void dispatch(int Q, int storage, const Dom &d, cudaStream_t s,
 
 void launch_step(int Q, int storage, const Dom &d, cudaStream_t s,
                  bool macros) {
-  if (d.sched == LBM_SCHED_TILES)
-    launch_step_tiles(Q, storage, d, s, macros, nullptr);
-  else
-    dispatch(Q, storage, d, s, macros, nullptr);
+  dispatch(Q, storage, d, s, macros, nullptr);
 }
 
 void launch_step_events(int Q, int storage, const Dom &d, cudaStream_t s,
                         bool macros, cudaEvent_t *ev) {
-  if (d.sched == LBM_SCHED_TILES)
-    launch_step_tiles(Q, storage, d, s, macros, ev);
-  else
-    dispatch(Q, storage, d, s, macros, ev);
+  dispatch(Q, storage, d, s, macros, ev);
 }
 
 }  // namespace lbm

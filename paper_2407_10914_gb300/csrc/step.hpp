@@ -7,17 +7,10 @@
 
 namespace lbm {
 
-// One time step on stream s, in the domain's schedule (d.sched): the tile
-// passes of step_tiles.cu or the node passes of step.cu. `macros` also
+// One time step: the seven passes of step.cu on stream s. `macros` also
 // stores rho and u of this step.
 void launch_step(int Q, int storage, const Dom &d, cudaStream_t s,
                  bool macros);
-
-// The tile passes (step_tiles.cu); ev: null, or eight events recorded as
-// launch_step_events describes (the slots of the node passes that the tile
-// passes fold into their neighbours get back-to-back events).
-void launch_step_tiles(int Q, int storage, const Dom &d, cudaStream_t s,
-                       bool macros, cudaEvent_t *ev);
 
 // The same step with an event recorded before each of its kernels and after
 // the last (ev[0..7], the slots of lbm_step_timed); kernels that do not run
@@ -53,11 +46,9 @@ void launch_import_pops(int Q, int storage, const Dom &d, const float *src,
 void launch_export_nw(const Dom &d, float *out, cudaStream_t s);
 
 // Dense rho [N], phi [N], u [3][N] of the last macro step (geometry.cu);
-// any pointer may be null. Eq. (34) at the solid-boundary nodes is
-// evaluated here from the fluid nodes' phase field (the tile passes never
-// store it).
-void launch_export_macros(int Q, const Dom &d, float *rho, float *phi,
-                          float *u, cudaStream_t s);
+// any pointer may be null.
+void launch_export_macros(const Dom &d, float *rho, float *phi, float *u,
+                          cudaStream_t s);
 
 // FP64 reductions (reduce.cu): the result lands in *out_dev.
 void launch_reduce(int Q, int storage, const Dom &d, int kind, double *partials,

@@ -2,9 +2,10 @@
 // pull of Eq. (1).
 //
 // The box is cut into tiles of TX x TY x TZ nodes (32 x 8 x 8 for D3Q19,
-// 32 x 32 x 1 for D2Q9; TX = 32 always, so that one row of a tile is one
-// 32-bit mask). Fluid nodes are numbered tile by tile (F-space), and within
-// a tile in (z, y, x) order; so are the solid-boundary nodes (S-space). The uint16 map over the box holds a node's class (bits 14-15)
+// 64 x 32 x 1 for D2Q9). Fluid nodes are numbered tile by tile (F-space),
+// and within a tile the fluid nodes on the box's x faces first, then the
+// others in (z, y, x) order; solid-boundary nodes in (z, y, x) order
+// (S-space). The uint16 map over the box holds a node's class (bits 14-15)
 // and its rank among the nodes of its kind in its tile (bits 0-13); with the
 // per-tile bases fbase/sbase this gives its F- or S-index.
 //
@@ -29,7 +30,7 @@ struct Tile<19> {
 
 template <>
 struct Tile<9> {
-  static constexpr int TX = 32, TY = 32, TZ = 1, LX = 5, LY = 5, LZ = 0;
+  static constexpr int TX = 64, TY = 32, TZ = 1, LX = 6, LY = 5, LZ = 0;
 };
 
 template <int Q>
@@ -110,10 +111,12 @@ __device__ __forceinline__ void pull_sums(const Dom &d, int k, int gp,
       rebuild<Q>(ft[0], Sown, 0, fr, fb);
     } else {
       const uint32_t e = nb_entry<Q>(d, gp, Lattice<Q>::opp(i));
-      const bool fl = (entry_cls(e) & 2) && !entry_out(e);
+      // a fluid class (bit 31) not clamped off the box (OUT)
+      const bool fl = (e & (0x80000000u | OUT_BIT)) == 0x80000000u;
       const int src = guard(d, fl ? entry_idx(e) : k, d.NF, GUARD_PULL);
       ft[i] = IO::load_dyn(d, fl ? i : Lattice<Q>::opp(i), src);
-      const float4 S = fl ? ldv<COH>(d.S_src + src) : Sown;
+      // bounce-back reads the node's own (q, v): src = k
+      const float4 S = ldv<COH>(d.S_src + src);
       const float ev = edot<Q>(i, S.y, S.z, S.w);
       rebuild_ev<Q>(ft[i], S.x, fl ? ev : -ev, i, fr, fb);
     }

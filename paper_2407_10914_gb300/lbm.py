@@ -25,13 +25,10 @@ STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA",
           -3: "LBM_ERR_STATE", -4: "LBM_ERR_NONFINITE", -5: "LBM_ERR_TIMEOUT",
           -6: "LBM_ERR_NOMEM"}
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
-# kernel schedules of lbm_step (LBM_SCHED_TILES, LBM_SCHED_NODES)
-SCHEDULE = {"tiles": 0, "nodes": 1}
 (LBM_MASS_R, LBM_MASS_B, LBM_SW_COUNT, LBM_SW_SMOOTH, LBM_DP, LBM_CA_R,
  LBM_CA_B) = range(7)
 EXPORTS = ("lbm_workspace_bytes", "lbm_init_geometry", "lbm_set_params",
-           "lbm_init_state", "lbm_step", "lbm_step_timed",
-           "lbm_set_schedule", "lbm_get_schedule", "lbm_macros",
+           "lbm_init_state", "lbm_step", "lbm_step_timed", "lbm_macros",
            "lbm_reduce",
            "lbm_get_populations", "lbm_set_populations", "lbm_swap_inlet",
            "lbm_debug_flags",
@@ -92,10 +89,6 @@ def load_library(path: str = LIB_PATH):
     L.lbm_step.argtypes = [vp, C.c_int, vp]
     L.lbm_step_timed.restype = C.c_int
     L.lbm_step_timed.argtypes = [vp, C.c_int, vp, C.POINTER(C.c_double)]
-    L.lbm_set_schedule.restype = C.c_int
-    L.lbm_set_schedule.argtypes = [vp, C.c_int]
-    L.lbm_get_schedule.restype = C.c_int
-    L.lbm_get_schedule.argtypes = [vp]
     L.lbm_macros.restype = C.c_int
     L.lbm_macros.argtypes = [vp, vp, vp, vp, vp]
     L.lbm_reduce.restype = C.c_int
@@ -237,35 +230,15 @@ def lbm_step(h, nsteps, stream):
     _check(load_library().lbm_step(h, int(nsteps), stream), h, "lbm_step")
 
 
-# the slots of lbm_step_timed per schedule (None: a slot the schedule
-# leaves empty because the work is part of the next kernel)
-PASSES = {
-    "nodes": ("stream", "zh_fix", "phi_solid", "gradient", "nc_solid",
-              "curvature", "collide"),
-    "tiles": ("pull", "planes", None, "gradient", None, "curvature",
-              "collide"),
-}
-
-
-def lbm_set_schedule(h, schedule: str):
-    _check(load_library().lbm_set_schedule(h, SCHEDULE[schedule]), h,
-           "lbm_set_schedule")
-
-
-def lbm_get_schedule(h) -> str:
-    v = load_library().lbm_get_schedule(h)
-    for k, x in SCHEDULE.items():
-        if x == v:
-            return k
-    raise LbmError(f"lbm_get_schedule: {v}")
+PASSES = ("stream", "zh_fix", "phi_solid", "gradient", "nc_solid",
+          "curvature", "collide")
 
 
 def lbm_step_timed(h, nsteps, stream) -> dict:
-    names = PASSES[lbm_get_schedule(h)]
-    ms = (C.c_double * len(names))()
+    ms = (C.c_double * len(PASSES))()
     _check(load_library().lbm_step_timed(h, int(nsteps), stream, ms), h,
            "lbm_step_timed")
-    return {n: v for n, v in zip(names, ms[:]) if n is not None}
+    return dict(zip(PASSES, ms[:]))
 
 
 def lbm_macros(h, rho, phi, u, stream):
@@ -418,13 +391,6 @@ class Session:
         """Per-pass milliseconds summed over n steps (CUDA events)."""
         return lbm_step_timed(self.h, n, self.stream())
 
-    def set_schedule(self, schedule: str):
-        """Kernel schedule of step(): "tiles" (default) or "nodes"."""
-        lbm_set_schedule(self.h, schedule)
-
-    @property
-    def schedule(self) -> str:
-        return lbm_get_schedule(self.h)
 
     def macros(self):
         t = self.torch

@@ -92,27 +92,21 @@ def test_batch_entry_points_host_only(lib):
 
 
 def test_pass_list_matches_header_and_byte_model():
-    """lbm_step_timed reports LBM_N_PASSES slots in either schedule; the
-    binding names them and bench.py's byte model has an entry for each
-    named pass."""
+    """lbm_step_timed reports LBM_N_PASSES kernels; the binding names them
+    and bench.py's byte model has an entry for each."""
     import importlib.util
     from paper_2407_10914_gb300 import lbm
     src = open(os.path.join(ROOT, "include", "lbmgb.h")).read()
     n = int(re.search(r"#define LBM_N_PASSES (\d+)", src).group(1))
-    assert set(lbm.PASSES) == set(lbm.SCHEDULE)
-    for sched, v in lbm.SCHEDULE.items():
-        m = re.search(r"LBM_SCHED_%s = (\d+)" % sched.upper(), src)
-        assert m and int(m.group(1)) == v
-        assert len(lbm.PASSES[sched]) == n
+    assert len(lbm.PASSES) == n
     spec = importlib.util.spec_from_file_location(
         "bench_module", os.path.join(ROOT, "bench.py"))
     bench = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(bench)
     for q in (9, 19):
-        for sched in lbm.SCHEDULE:
-            pb = bench.pass_bytes(q, 4, sched)
-            assert set(pb) == {p for p in lbm.PASSES[sched] if p}
-            assert all(v > 0 for v in pb.values())
+        pb = bench.pass_bytes(q, 4)
+        assert set(pb) == set(lbm.PASSES) == set(bench.PASS_KERNEL)
+        assert all(v > 0 for v in pb.values())
 
 
 def test_noalloc_refuses_host_tensor_before_any_launch():
