@@ -23,15 +23,16 @@ namespace lbm {
 constexpr int BLOCK = 256;
 
 // Blocks per SM, measured on the 256^3 rock: the gather passes are bound by
-// load latency, so the stream and gradient passes run with 32 registers
-// (7-8 resident blocks of 256 threads; the gradient pass gains 14 % over its
-// unbounded 34 registers, the stream pass 4 % over 40); so does the
-// curvature, a gather of the neighbours' n_c split off the collision. The
-// single-rate collision then runs 4 blocks (64 registers, 28 B of spills),
-// 4 % faster than 3 blocks with 80; the MRT collision keeps 3 blocks (it
-// would spill 84 B at 64 registers).
+// load latency. The stream pass runs 6 blocks of 256 threads (40 registers:
+// 0.205 against 0.223 ms at 7 blocks and 32 registers, with the pull's
+// unconditional (q, v) load); the gradient and curvature passes 8 blocks at
+// 32 registers (the gradient gains 14 % over its unbounded 34 registers; the
+// curvature, a gather of the neighbours' n_c split off the collision, is 7 %
+// slower at 6 blocks). The single-rate collision runs 4 blocks (64
+// registers; 3 and 5 blocks are 1 % and 11 % slower); the MRT collision
+// keeps 3 blocks (it would spill at 64 registers).
 template <int Q, int ST>
-__global__ void __launch_bounds__(BLOCK, 7) k_stream(Dom d) {
+__global__ void __launch_bounds__(BLOCK, 6) k_stream(Dom d) {
   const int k = blockIdx.x * BLOCK + threadIdx.x;
   if (k < d.NF) stream_node<Q, ST, false>(d, k);
 }
