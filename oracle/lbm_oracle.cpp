@@ -747,6 +747,12 @@ struct OracleT {
   }
 
  public:
+  // Eqs. (34) and (35) on the current phi and n_c (for tests).
+  void extrapolations_only() {
+    extrapolate_phi();
+    extrapolate_nc();
+  }
+
   // Single-node collision: Eq. (2) with one rate S for every non-conserved
   // moment and rate 0 for the conserved ones (rho, j), i.e. the relaxation
   // matrix of Eq. (4) with S_e = S_eps = S_q = S_nu = S_pi = S_m = S.
@@ -1076,6 +1082,22 @@ void orc_stream_only(void *h, double *dst) {
   Oracle *o = static_cast<Oracle *>(h);
   o->stream_part();
   std::memcpy(dst, o->ftmp.data(), sizeof(double) * o->ftmp.size());
+}
+
+// Test hook: the extrapolations of Eqs. (34)-(35) alone on a prescribed
+// field. phi_in (N) and nc_in (3N) give the fluid nodes' phase field and
+// n_c (other entries are ignored); phi_out and nc_out receive the fields
+// after Eq. (34) and Eq. (35) set the solid-boundary nodes. The stored
+// state is not changed.
+void orc_extrapolate(void *h, const double *phi_in, const double *nc_in,
+                     double *phi_out, double *nc_out) {
+  Oracle *o = static_cast<Oracle *>(h);
+  const long N = o->N;
+  std::memcpy(o->phi.data(), phi_in, sizeof(double) * N);
+  std::memcpy(o->nc.data(), nc_in, sizeof(double) * 3 * N);
+  o->extrapolations_only();
+  std::memcpy(phi_out, o->phi.data(), sizeof(double) * N);
+  std::memcpy(nc_out, o->nc.data(), sizeof(double) * 3 * N);
 }
 
 // Classes (0 solid, 1 solid-boundary, 2 fluid, 3 fluid-boundary), the

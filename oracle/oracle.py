@@ -70,6 +70,7 @@ def lib():
         L.orc_swap_inlet.argtypes = [C.c_void_p, C.c_int]
         L.orc_swap_inlet.restype = C.c_long
         L.orc_stream_only.argtypes = [C.c_void_p, C.c_void_p]
+        L.orc_extrapolate.argtypes = [C.c_void_p] + [C.c_void_p] * 4
         L.orc_geometry.argtypes = [C.c_void_p] + [C.c_void_p] * 3
         L.orc_fields.argtypes = [C.c_void_p] + [C.c_void_p] * 6
         L.orc_reduce.restype = C.c_double
@@ -242,6 +243,17 @@ class Oracle:
         out = np.zeros((2, self.q) + self.shape)
         lib().orc_stream_only(self._h, _ptr(out))
         return out
+
+    def extrapolate(self, phi: np.ndarray, nc: np.ndarray):
+        """Eqs. (34)-(35) alone on a prescribed phase field (nz, ny, nx) and
+        n_c (3, nz, ny, nx) of the fluid nodes: returns both fields with the
+        solid-boundary nodes filled. The stored state is not changed."""
+        pi = np.ascontiguousarray(phi, np.float64)
+        ni = np.ascontiguousarray(nc, np.float64)
+        po = np.zeros(self.shape)
+        no = np.zeros((3,) + self.shape)
+        lib().orc_extrapolate(self._h, _ptr(pi), _ptr(ni), _ptr(po), _ptr(no))
+        return po, no
 
     def geometry(self):
         cls = np.zeros(self.shape, np.uint8)

@@ -109,6 +109,44 @@ def test_poiseuille_closed_form(tau):
     np.testing.assert_allclose(u[1:-1], expect, rtol=0, atol=1e-12)
 
 
+@pytest.mark.parametrize("phi0", [0.3, -0.55])
+def test_mixture_channel_viscosity(phi0):
+    """Eqs. (13)-(14) pinned by a single-phase flow: a uniform mixture phi0
+    of fluids with tau^r = 1.0 and tau^b = 0.6 has no colour gradient (C = 0,
+    so neither recolouring nor surface tension acts) and flows as one fluid
+    of the harmonic-mean viscosity 1/nu = (1 + phi0)/(2 nu^r) +
+    (1 - phi0)/(2 nu^b). The body-forced channel then reaches the closed
+    form of test_poiseuille_closed_form with tau = 3 nu + 1/2. Swapping
+    nu^r and nu^b or taking the arithmetic mean of the viscosities moves
+    the centre-line speed by 30-120 %."""
+    g, ny = 1e-6, 19
+    case = W.channel_2d(nx=4, ny=ny, g=g, tau=1.0)
+    phi = np.full(case.solid.shape, float(phi0))
+    phi[case.solid == 1] = 0.0
+    o = O.Oracle(9, case.solid, case.periodic)
+    o.set_params(**dict(case.params, tau_r=1.0, tau_b=0.6))
+    o.init_state(phi)
+    o.step(30000)
+    f = o.fields()
+    u = f["u"][0, 0, :, 0]
+    fluid = case.solid[0, :, 0] == 0
+    assert np.abs(f["phi"][0, :, 0][fluid] - phi0).max() < 1e-12
+    nur, nub = 0.5 / 3, 0.1 / 3
+    nu = 1.0 / ((1 + phi0) / (2 * nur) + (1 - phi0) / (2 * nub))
+    tau = 3 * nu + 0.5
+    y = np.arange(ny, dtype=float)[1:-1]
+
+    def profile(nu, tau):
+        us = g * (16 * (tau - 0.5) ** 2 - 3) / (24 * nu)
+        return g / (2 * nu) * (y - 0.5) * (ny - 1.5 - y) + us
+
+    np.testing.assert_allclose(u[1:-1], profile(nu, tau), rtol=0, atol=1e-12)
+    for wrong in (1.0 / ((1 + phi0) / (2 * nub) + (1 - phi0) / (2 * nur)),
+                  0.5 * ((1 + phi0) * nur + (1 - phi0) * nub)):
+        other = profile(wrong, 3 * wrong + 0.5)
+        assert np.abs(other - u[1:-1]).max() > 0.3 * np.abs(u[1:-1]).max()
+
+
 @pytest.mark.parametrize("wetting,theta,tol", [(2, 60.0, 1.5), (1, 60.0, 1.5),
                                                (2, 120.0, 3.0)])
 def test_static_contact_angle(wetting, theta, tol):
