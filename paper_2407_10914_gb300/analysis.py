@@ -64,6 +64,25 @@ def droplet_contact_angle(phi_slice, wall_row, axis_col):
     return 180.0 - contact_angle_from_cap(b, h)
 
 
+def sessile_angle_3d(phi: np.ndarray, cx: float, cy: float,
+                     wall_layer: int = 0):
+    """Contact angle (degrees, through fluid b) of a red sessile drop on the
+    wall z = ``wall_layer`` of a 3-D phase field phi[z, y, x], with Eqs.
+    (45)-(46) applied to the two central sections through the drop's axis
+    (x, y) = (cx, cy): the x-z section (interpolated between the two rows
+    nearest cy) and the y-z section (between the two columns nearest cx).
+    Returns (mean, x-z angle, y-z angle)."""
+    y0 = int(math.floor(cy))
+    ty = cy - y0
+    sxz = (1 - ty) * phi[:, y0, :] + ty * phi[:, min(y0 + 1, phi.shape[1] - 1), :]
+    x0 = int(math.floor(cx))
+    tx = cx - x0
+    syz = (1 - tx) * phi[:, :, x0] + tx * phi[:, :, min(x0 + 1, phi.shape[2] - 1)]
+    ax = droplet_contact_angle(sxz, wall_layer, cx)
+    ay = droplet_contact_angle(syz, wall_layer, cy)
+    return 0.5 * (ax + ay), ax, ay
+
+
 def interface_position(phi: np.ndarray, axis: int = 0, solid=None) -> float:
     """Volume-equivalent position of a red slug entering along ``axis`` from
     coordinate 0: the number of red-filled cross-sections, i.e. the red

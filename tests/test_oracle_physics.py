@@ -159,6 +159,23 @@ def test_static_contact_angle(wetting, theta, tol):
     assert abs(th - theta) < tol, th
 
 
+@pytest.mark.parametrize("wetting,theta", [(2, 60.0), (1, 120.0)])
+def test_static_contact_angle_d3q19(wetting, theta):
+    """Sec. III.B in 3-D: a D3Q19 sessile drop (R = 8 on the wall z = 0 of a
+    32 x 32 x 20 box) relaxes to the prescribed angle through fluid b,
+    measured with the 3-D form of Eqs. (45)-(46) (central sections through
+    the drop's axis). At this drop size the diffuse interface biases the
+    base measure by 1-4.5 deg (the paper's R = 30 drops: +3.6/-2.2 deg for
+    Scheme-I), so the bound is 5 deg; the angle is settled by 4500 steps
+    (it moves by less than 0.1 deg from there to 9000)."""
+    case = W.droplet_3d(side=32, radius=8.0, theta_deg=theta, wetting=wetting,
+                        shape=(20, 32, 32))
+    o = run(case, 4500)
+    th, ax, ay = A.sessile_angle_3d(o.fields()["phi"], *case.info["centre"][:2])
+    assert abs(ax - ay) < 1e-3  # x <-> y symmetric up to summation order
+    assert abs(th - theta) < 5.0, th
+
+
 def test_washburn_equal_viscosity():
     """Sec. IV.A, pressure-driven case with theta = 90 deg (Scheme-I) and
     equal viscosities: Eq. (47) reduces to z(t) = z0 + r^2 dP t/(8 mu L).
