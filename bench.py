@@ -34,7 +34,8 @@ One JSON line on rank 0:
   storage_16bit the same rock with FP16 / BF16 population storage, each
              with its error against the FP64 oracle on a slab;
   batched    the 96-drop contact-angle sweep stepped as one batch
-             (autotuned schedule);
+             (autotuned schedule), FP32 and FP16-offset storage, each with
+             its error against the FP64 oracle;
   adjoint    the gradient of the smooth saturation after 2000 steps of the
              128^3 imbibition pack w.r.t. theta and g_x, beside central
              finite differences.
@@ -459,8 +460,10 @@ def run_ours(args):
         sixteen = run_16bit(args, torch, lbm, case, min(args.steps, 500))
 
     batched = None
+    batched16 = None
     if not args.no_batched:
-        batched = run_batched(args, torch, lbm)
+        batched = run_batched(args, torch, lbm, "fp32")
+        batched16 = run_batched(args, torch, lbm, "fp16")
     adjoint = None
     if not args.no_adjoint:
         adjoint = run_adjoint(args, torch, lbm)
@@ -532,6 +535,8 @@ def run_ours(args):
             line["storage_16bit"] = sixteen
         if batched:
             line["batched"] = batched
+        if batched16:
+            line["batched_fp16"] = batched16
         if adjoint:
             line["adjoint"] = adjoint
         if cpu:
@@ -762,12 +767,30 @@ def run_mrt(args, torch, lbm, case, steps: int):
     return out
 
 
+def field_errors(o, s, fluid):
+    """Largest |difference| over fluid nodes of phi, rho and |u| between the
+    oracle and a session, after the same steps."""
+    fo = o.fields()
+    m = s.macros()
+    out = {}
+    for k in ("phi", "rho"):
+        got = m[k].cpu().numpy().astype(np.float64)
+        out[k] = float(np.abs(got - fo[k])[fluid].max())
+    gu = m["u"].cpu().numpy().astype(np.float64)
+    out["u"] = float(np.sqrt(((gu - fo["u"]) ** 2).sum(0))[fluid].max())
+    out["u_max"] = float(np.sqrt((fo["u"] ** 2).sum(0))[fluid].max())
+    return out
+
+
 def run_16bit(args, torch, lbm, case, steps: int):
     """The same rock with the f''_i planes stored as 16-bit offsets (FP16,
-    BF16): throughput over `steps` steps, per-pass times, and the error
-    against the FP64 oracle after 10 steps from the initial state on the
-    32-plane slab (max |f_gpu - f_oracle| / max |f_oracle| per colour), with
-    the FP32 storage's error on the same slab beside it."""
+    BF16): throughput over `steps` steps, per-pass times, the fraction of
+    the HBM roofline with their own 156 B per fluid-node update (2 x 2Q
+    populations of 2 B and a 4 B link mask), and the error against the FP64
+    oracle after 10 steps from the initial state: the populations on the
+    32-plane slab (max |f_gpu - f_oracle| / max |f_oracle| per colour) and
+    phi, rho, u on the full rock, with the FP32 storage's errors beside
+    them."""
     from oracle import oracle as O
     out = {}
     slab = oracle_sample(case, 32)
@@ -777,18 +800,35 @@ def run_16bit(args, torch, lbm, case, steps: int):
     o.step(10)
     ref = o.pops
     fl = slab.solid == 0
+    del o
+    full = O.Oracle(case.lattice, case.solid, case.periodic)
+    full.set_params(**case.params)
+    full.init_state(case.phi0)
+    full.step(10)
+    fluid = case.solid == 0
 
-    def slab_err(storage):
+    def errors(storage):
         t = lbm.Session(slab.lattice, slab.solid, slab.periodic, storage)
         t.set_params(**slab.params)
         t.init_state(slab.phi0.astype(np.float32))
         t.step(10)
         got = t.get_populations().cpu().numpy().astype(np.float64)
-        return max(float(np.abs(got[c][:, fl] - ref[c][:, fl]).max()
-                         / np.abs(ref[c][:, fl]).max()) for c in range(2))
+        pop = max(float(np.abs(got[c][:, fl] - ref[c][:, fl]).max()
+                        / np.abs(ref[c][:, fl]).max()) for c in range(2))
+        del t
+        r = lbm.Session(case.lattice, case.solid, case.periodic, storage)
+        r.set_params(**case.params)
+        r.init_state(case.phi0.astype(np.float32))
+        r.step(10)
+        fe = field_errors(full, r, fluid)
+        del r
+        return pop, fe
 
-    out["fp32_slab_error"] = slab_err("fp32")
+    pop32, fe32 = errors("fp32")
+    out["fp32_slab_error"] = pop32
+    out["fp32_full_rock_field_errors"] = fe32
     stream = torch.cuda.current_stream()
+    peak, _ = measured_peaks()
     for storage in ("fp16", "bf16"):
         s = lbm.Session(case.lattice, case.solid, case.periodic, storage)
         s.set_params(**case.params)
@@ -804,32 +844,78 @@ def run_16bit(args, torch, lbm, case, steps: int):
         ms = e0.elapsed_time(e1) / steps
         k2 = min(steps, 100)
         pm = s.step_timed(k2)
+        upd = 2 * 2 * case.lattice * 2 + 4
+        del s
+        pop, fe = errors(storage)
         out[storage] = {
-            "value": round(s.n_fluid / (ms * 1e-3) / 1e6, 2), "unit": "MLUPS",
-            "ms_per_step": round(ms, 4),
+            "value": round(case_fluid(case) / (ms * 1e-3) / 1e6, 2),
+            "unit": "MLUPS", "ms_per_step": round(ms, 4),
             "pass_ms_per_step": {k: round(v / k2, 5) for k, v in pm.items()},
-            "bytes_per_update_2q_pops": 2 * 2 * case.lattice * 2 + 4,
-            "error_vs_fp64_oracle": slab_err(storage),
+            "bytes_per_update_2q_pops": upd,
+            "roofline_frac": round(upd * case_fluid(case) / (ms * 1e-3) / 1e9
+                                   / peak, 4),
+            "error_vs_fp64_oracle": pop,
             "error_sample": "32-plane slab of the rock, 10 steps from the "
                             "initial state, max relative population error",
+            "full_rock_field_errors": fe,
+            "full_rock_sample": "the whole 256^3 rock, 10 steps from the "
+                                "initial state: max |difference| over fluid "
+                                "nodes of phi, rho and |u|",
         }
-        del s
     return out
 
 
-def run_batched(args, torch, lbm):
+def case_fluid(case) -> int:
+    return int((case.solid == 0).sum())
+
+
+def batch_error(args, torch, lbm, storage: str, steps: int = 20):
+    """Error of a batch against the FP64 oracle: the two smallest drops of
+    the sweep stepped together in one batch (the same kernels), `steps`
+    steps from the initial state, max |f_gpu - f_oracle| / max |f_oracle|
+    per colour over both cases."""
+    from oracle import oracle as O
+    from paper_2407_10914_gb300 import workloads as W
+    cases = sorted(W.batched_droplets(count=args.batched_cases),
+                   key=lambda c: c.n_nodes)[:2]
+    sess = []
+    for c in cases:
+        s = lbm.Session(c.lattice, c.solid, c.periodic, storage)
+        s.set_params(**c.params)
+        s.init_state(c.phi0.astype(np.float32))
+        sess.append(s)
+    b = lbm.Batch(sess)
+    b.step(steps)
+    torch.cuda.synchronize()
+    err = 0.0
+    for c, s in zip(cases, sess):
+        o = O.Oracle(c.lattice, c.solid, c.periodic)
+        o.set_params(**c.params)
+        o.init_state(c.phi0)
+        o.step(steps)
+        got = s.get_populations().cpu().numpy().astype(np.float64)
+        fl = c.solid == 0
+        for k in range(2):
+            err = max(err, float(np.abs(got[k][:, fl] - o.pops[k][:, fl]).max()
+                                 / np.abs(o.pops[k][:, fl]).max()))
+    del b, sess
+    return err, [c.name for c in cases]
+
+
+def run_batched(args, torch, lbm, storage: str = "fp32"):
     """The contact-angle sweep: 96 D3Q19 sessile drops in boxes of 48^3 to
     128^3 (Scheme-I and Scheme-II, theta 30-150 deg), stepped together by
     one batch. The schedule is chosen by the autotuner (its trials are
     reported too); the value is fluid-node updates per second over all
-    cases, CUDA events around `batched-steps` steps."""
+    cases, CUDA events around `batched-steps` steps; the error against the
+    FP64 oracle comes from batch_error."""
     from paper_2407_10914_gb300 import autotune
     from paper_2407_10914_gb300 import workloads as W
     t0 = time.time()
     cases = W.batched_droplets(count=args.batched_cases)
     sess = []
     for c in cases:
-        s = lbm.Session(c.lattice, c.solid, c.periodic, args.storage)
+        s = lbm.Session(c.lattice, c.solid, c.periodic, storage)
         s.set_params(**c.params)
         s.init_state(c.phi0.astype(np.float32))
         sess.append(s)
@@ -850,21 +936,29 @@ def run_batched(args, torch, lbm):
         raise SystemExit("batched sweep: a persistent-kernel wait ran out")
     nf = b.n_fluid
     sides = sorted(int(c.solid.shape[0]) for c in cases)
+    peak, _ = measured_peaks()
+    upd = 2 * 2 * 19 * BYTES_POP[storage] + 4
     out = {
-        "workload": f"batch{len(cases)}_sessile_drops_{args.storage}",
+        "workload": f"batch{len(cases)}_sessile_drops_{storage}",
         "cases": len(cases), "box_sides": [sides[0], sides[-1]],
         "fluid_nodes": nf,
         "nodes": int(sum(c.n_nodes for c in cases)),
         "value": round(nf / (ms * 1e-3) / 1e6, 2), "unit": "MLUPS",
         "ms_per_step": round(ms, 4), "steps": args.batched_steps,
+        "roofline_frac": round(upd * nf / (ms * 1e-3) / 1e9 / peak, 4),
+        "bytes_per_update": upd,
         "schedule": {"mode": ["level launches", "persistent"][tune["config"][0]],
                      "threads": tune["config"][1], "chunk": tune["config"][2]},
         "tuning_ms_per_step": tune.get("trials"),
         "setup_s": round(setup_s, 1),
-        "parity": "bit-identical to stepping each case alone (tests/test_gpu_batch.py)",
     }
     del b, sess
     torch.cuda.empty_cache()
+    err, names = batch_error(args, torch, lbm, storage)
+    out["error_vs_fp64_oracle"] = err
+    out["error_sample"] = (f"cases {names[0]} and {names[1]} stepped together "
+                           "in one batch, 20 steps from the initial state, max "
+                           "relative population error")
     return out
 
 

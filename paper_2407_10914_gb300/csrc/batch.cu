@@ -116,9 +116,21 @@ __device__ __forceinline__ int case_of(const int *__restrict__ start, int n,
   return lo;
 }
 
+// Resident 256-thread blocks per SM each pass is compiled for, as in the
+// single-domain kernels (step.cu): the gather passes with few registers
+// (stream 6 blocks, the stencils 8), the collision (with the curvature of
+// Eq. 12 computed in it) 3 blocks; twice as many blocks of 128 threads.
+template <int P, int BT>
+struct PassBlocks {
+  static constexpr int k256 =
+      P == P_STREAM ? 6 : (P == P_COLLIDE ? 3 : 8);
+  static constexpr int value = BT == 256 ? k256 : 2 * k256;
+};
+
 // Mode 0: pass P of step s for every case; start = that pass's block prefix.
 template <int Q, int ST, int P, bool MACROS, int BT>
-__global__ void __launch_bounds__(BT) k_batch_pass(const Dom *__restrict__ table,
+__global__ void __launch_bounds__(BT, (PassBlocks<P, BT>::value))
+    k_batch_pass(const Dom *__restrict__ table,
                                                    const int *__restrict__ start,
                                                    int ncase,
                                                    const BatchCtl *__restrict__ ctl,
@@ -171,8 +183,10 @@ __device__ bool wait_count(const unsigned long long *cnt,
   }
 }
 
+// All passes in one kernel: the registers of the heaviest (the collision
+// with the curvature), bounded to 3 resident blocks of 256 threads.
 template <int Q, int ST, int BT>
-__global__ void __launch_bounds__(BT) k_batch_persistent(
+__global__ void __launch_bounds__(BT, BT == 256 ? 3 : 6) k_batch_persistent(
     const Dom *__restrict__ table, Plan pl, BatchCtl *ctl,
     unsigned long long *done, int nsteps, unsigned long long limit_ns) {
   __shared__ __align__(16) Dom sd;
