@@ -752,6 +752,10 @@ struct OracleT {
     extrapolate_phi();
     extrapolate_nc();
   }
+  // Eq. (6)/(11) on the current phi, and Eq. (12) on the current n_c
+  // (for tests; C, n_c and kappa are overwritten in that order).
+  void gradient_only() { colour_gradient(); }
+  void curvature_only() { curvature_force(); }
 
   // Single-node collision: Eq. (2) with one rate S for every non-conserved
   // moment and rate 0 for the conserved ones (rho, j), i.e. the relaxation
@@ -1098,6 +1102,23 @@ void orc_extrapolate(void *h, const double *phi_in, const double *nc_in,
   o->extrapolations_only();
   std::memcpy(phi_out, o->phi.data(), sizeof(double) * N);
   std::memcpy(nc_out, o->nc.data(), sizeof(double) * 3 * N);
+}
+
+// Test hook: the stencils alone on prescribed fields. phi_in (N): Eq. (6)
+// and Eq. (11) give C and n_c (3N each, into C_out, nc_out); nc_in (3N):
+// Eq. (12) gives kappa (N, into kappa_out). The stored state is not
+// changed; the colour densities are taken as they are (they enter F only).
+void orc_stencils(void *h, const double *phi_in, const double *nc_in,
+                  double *C_out, double *nc_out, double *kappa_out) {
+  Oracle *o = static_cast<Oracle *>(h);
+  const long N = o->N;
+  std::memcpy(o->phi.data(), phi_in, sizeof(double) * N);
+  o->gradient_only();
+  std::memcpy(C_out, o->C.data(), sizeof(double) * 3 * N);
+  std::memcpy(nc_out, o->nc.data(), sizeof(double) * 3 * N);
+  std::memcpy(o->nc.data(), nc_in, sizeof(double) * 3 * N);
+  o->curvature_only();
+  std::memcpy(kappa_out, o->kappa.data(), sizeof(double) * N);
 }
 
 // Classes (0 solid, 1 solid-boundary, 2 fluid, 3 fluid-boundary), the

@@ -71,6 +71,7 @@ def lib():
         L.orc_swap_inlet.restype = C.c_long
         L.orc_stream_only.argtypes = [C.c_void_p, C.c_void_p]
         L.orc_extrapolate.argtypes = [C.c_void_p] + [C.c_void_p] * 4
+        L.orc_stencils.argtypes = [C.c_void_p] + [C.c_void_p] * 5
         L.orc_geometry.argtypes = [C.c_void_p] + [C.c_void_p] * 3
         L.orc_fields.argtypes = [C.c_void_p] + [C.c_void_p] * 6
         L.orc_reduce.restype = C.c_double
@@ -254,6 +255,19 @@ class Oracle:
         no = np.zeros((3,) + self.shape)
         lib().orc_extrapolate(self._h, _ptr(pi), _ptr(ni), _ptr(po), _ptr(no))
         return po, no
+
+    def stencils(self, phi: np.ndarray, nc: np.ndarray):
+        """Eqs. (6), (11) on a prescribed phase field (nz, ny, nx) and Eq.
+        (12) on a prescribed n_c (3, nz, ny, nx): returns C, n_c and kappa.
+        The stored state is not changed."""
+        pi = np.ascontiguousarray(phi, np.float64)
+        ni = np.ascontiguousarray(nc, np.float64)
+        Co = np.zeros((3,) + self.shape)
+        no = np.zeros((3,) + self.shape)
+        ko = np.zeros(self.shape)
+        lib().orc_stencils(self._h, _ptr(pi), _ptr(ni), _ptr(Co), _ptr(no),
+                           _ptr(ko))
+        return Co, no, ko
 
     def geometry(self):
         cls = np.zeros(self.shape, np.uint8)
