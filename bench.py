@@ -48,6 +48,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import shutil
 import subprocess
@@ -142,6 +143,18 @@ def parse():
     ap.add_argument("--oracle-sample", nargs=3, type=int, default=None,
                     metavar=("PLANES", "STEPS", "SIZE"),
                     help=argparse.SUPPRESS)
+    ap.add_argument("--adjoint-fd64", nargs="?", const="all", default=None,
+                    choices=["all", "gx"],
+                    help="also central differences of the FP64 oracle at the "
+                         "gradient workload's full size (about 15 min of "
+                         "host CPU)")
+    ap.add_argument("--adjoint-tlm64", action="store_true",
+                    help="also the FP64 oracle's tangent-linear run at the "
+                         "gradient workload's full size")
+    ap.add_argument("--tile", default="auto",
+                    help="tile shape of the fluid-node numbering: 'auto' "
+                         "(the autotuner's search on the workload), "
+                         "'default', or XxYxZ")
     ap.add_argument("--adjoint-size", type=int, default=128)
     ap.add_argument("--adjoint-steps", type=int, default=2000)
     return ap.parse_args()
@@ -356,6 +369,25 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------- our arm
+def pick_tile(args, make, q):
+    """Tile shape for the run: --tile auto runs the autotuner's tile search
+    (each candidate a domain or batch of its own, 1 untimed + 8 timed
+    steps); returns (tile or None for the default, the trials or None)."""
+    if args.tile == "default":
+        return None, None
+    if args.tile != "auto":
+        return tuple(int(v) for v in args.tile.split("x")), None
+    from paper_2407_10914_gb300 import autotune
+    r = autotune.tune_tile(make, q, trial_steps=8, use_cache=False)
+    return r["tile"], r["trials"]
+
+
+def tile_name(tile, q):
+    if tile is None:
+        tile = (32, 8, 8) if q == 19 else (64, 32, 1)
+    return "x".join(str(v) for v in tile)
+
+
 def run_ours(args):
     import torch
     from paper_2407_10914_gb300 import build, lbm
@@ -367,9 +399,16 @@ def run_ours(args):
     build.build()
     case, name = workload(args)
     Q = case.lattice
-    s = lbm.Session(Q, case.solid, case.periodic, args.storage)
-    s.set_params(**case.params)
-    s.init_state(case.phi0.astype(np.float32))
+
+    def make(tile):
+        s = lbm.Session(Q, case.solid, case.periodic, args.storage, tile=tile)
+        s.set_params(**case.params)
+        s.init_state(case.phi0.astype(np.float32))
+        return s
+
+    tile, tile_trials = pick_tile(args, make, Q)
+    torch.cuda.empty_cache()
+    s = make(tile)
     nf = s.n_fluid
     n_sbnd = s.counts[2]
     stream = torch.cuda.current_stream()
@@ -437,7 +476,7 @@ def run_ours(args):
 
     e2e = None
     if not args.no_e2e:
-        e2e = end_to_end(args, case, torch, lbm)
+        e2e = end_to_end(args, case, torch, lbm, tile)
 
     tube = None
     if not args.no_tube and rank == 0:
@@ -457,7 +496,7 @@ def run_ours(args):
 
     sixteen = None
     if not args.no_16bit and rank == 0:
-        sixteen = run_16bit(args, torch, lbm, case, min(args.steps, 500))
+        sixteen = run_16bit(args, torch, lbm, case, min(args.steps, 500), tile)
 
     batched = None
     batched16 = None
@@ -488,6 +527,8 @@ def run_ours(args):
                 "fluid_nodes": nf, "nodes": case.n_nodes,
                 "rock_porosity": round(case.info.get("rock_porosity", 0), 4),
                 "storage": args.storage, "lattice": "D3Q19",
+                "tile": tile_name(tile, Q),
+                "tile_search_ms_per_step": tile_trials,
                 "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                 "l2": "inputs larger than L2 (two population buffers of "
                       f"{2 * Q * bpp * case.n_nodes / 1e9:.2f} GB)",
@@ -547,12 +588,12 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def end_to_end(args, case, torch, lbm):
+def end_to_end(args, case, torch, lbm, tile=None):
     """The user's call sequence from host memory: workspace allocated
-    beforehand; timed: lbm_init_geometry (solid image H2D from pinned host
-    memory), phi0 H2D (pinned), K x (step + S_w read-back), final phi D2H."""
-    from paper_2407_10914_gb300.lbm import (STORAGE, lbm_init_geometry,
-                                            lbm_workspace_bytes)
+    beforehand; timed: lbm_init_geometry_tiled (solid image H2D from pinned
+    host memory; the run's tile shape), phi0 H2D (pinned), K x (step + S_w
+    read-back), final phi D2H."""
+    from paper_2407_10914_gb300.lbm import STORAGE, lbm_workspace_bytes_tiled
     import ctypes as C
     nz, ny, nx = case.solid.shape
     Q = case.lattice
@@ -560,7 +601,9 @@ def end_to_end(args, case, torch, lbm):
     phi_pin = torch.from_numpy(case.phi0.astype(np.float32).reshape(-1)).pin_memory()
     out_pin = torch.empty(case.n_nodes, dtype=torch.float32).pin_memory()
     mask = sum((1 << a) for a in range(3) if case.periodic[a])
-    wsb = lbm_workspace_bytes(Q, nx, ny, nz, case.solid, STORAGE[args.storage])
+    wsb = lbm_workspace_bytes_tiled(Q, nx, ny, nz, case.solid,
+                                    STORAGE[args.storage], tile)
+    tile_c = None if tile is None else (C.c_int * 3)(*tile)
     work = torch.empty(wsb, dtype=torch.uint8, device="cuda")
     phi_dev = torch.empty(case.n_nodes, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -570,10 +613,10 @@ def end_to_end(args, case, torch, lbm):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     h = C.c_void_p()
-    st = L.lbm_init_geometry(C.byref(h), Q, nx, ny, nz,
-                             C.c_void_p(solid_pin.data_ptr()), mask,
-                             STORAGE[args.storage], C.c_void_p(work.data_ptr()),
-                             wsb, sp)
+    st = L.lbm_init_geometry_tiled(C.byref(h), Q, nx, ny, nz,
+                                   C.c_void_p(solid_pin.data_ptr()), mask,
+                                   STORAGE[args.storage], tile_c,
+                                   C.c_void_p(work.data_ptr()), wsb, sp)
     assert st == 0, st
     lbm.lbm_set_params(h, lbm.make_params(**case.params))
     phi_dev.copy_(phi_pin, non_blocking=True)
@@ -782,7 +825,7 @@ def field_errors(o, s, fluid):
     return out
 
 
-def run_16bit(args, torch, lbm, case, steps: int):
+def run_16bit(args, torch, lbm, case, steps: int, tile=None):
     """The same rock with the f''_i planes stored as 16-bit offsets (FP16,
     BF16): throughput over `steps` steps, per-pass times, the fraction of
     the HBM roofline with their own 156 B per fluid-node update (2 x 2Q
@@ -829,8 +872,10 @@ def run_16bit(args, torch, lbm, case, steps: int):
     out["fp32_full_rock_field_errors"] = fe32
     stream = torch.cuda.current_stream()
     peak, _ = measured_peaks()
+    out["tile"] = tile_name(tile, case.lattice)
     for storage in ("fp16", "bf16"):
-        s = lbm.Session(case.lattice, case.solid, case.periodic, storage)
+        s = lbm.Session(case.lattice, case.solid, case.periodic, storage,
+                        tile=tile)
         s.set_params(**case.params)
         s.init_state(case.phi0.astype(np.float32))
         s.step(args.warmup)
@@ -911,15 +956,22 @@ def run_batched(args, torch, lbm, storage: str = "fp32"):
     FP64 oracle comes from batch_error."""
     from paper_2407_10914_gb300 import autotune
     from paper_2407_10914_gb300 import workloads as W
-    t0 = time.time()
     cases = W.batched_droplets(count=args.batched_cases)
-    sess = []
-    for c in cases:
-        s = lbm.Session(c.lattice, c.solid, c.periodic, storage)
-        s.set_params(**c.params)
-        s.init_state(c.phi0.astype(np.float32))
-        sess.append(s)
-    b = lbm.Batch(sess)
+
+    def make(tile):
+        sess = []
+        for c in cases:
+            s = lbm.Session(c.lattice, c.solid, c.periodic, storage, tile=tile)
+            s.set_params(**c.params)
+            s.init_state(c.phi0.astype(np.float32))
+            sess.append(s)
+        return lbm.Batch(sess)
+
+    tile, tile_trials = pick_tile(args, make, 19)
+    torch.cuda.empty_cache()
+    t0 = time.time()
+    b = make(tile)
+    sess = b.sessions
     setup_s = time.time() - t0
     tune = autotune.tune(b, trial_steps=4, use_cache=False)
     stream = torch.cuda.current_stream()
@@ -950,6 +1002,8 @@ def run_batched(args, torch, lbm, storage: str = "fp32"):
         "schedule": {"mode": ["level launches", "persistent"][tune["config"][0]],
                      "threads": tune["config"][1], "chunk": tune["config"][2]},
         "tuning_ms_per_step": tune.get("trials"),
+        "tile": tile_name(tile, 19),
+        "tile_search_ms_per_step": tile_trials,
         "setup_s": round(setup_s, 1),
     }
     del b, sess
@@ -968,7 +1022,6 @@ def run_adjoint(args, torch, lbm):
     respect to theta and g_x: checkpointed forward run plus hand-written
     reverse sweep (K = 45 for T = 2000), timed with CUDA events, and the
     same derivatives by central differences of the FP32 forward run."""
-    import math
     from paper_2407_10914_gb300 import workloads as W
     from paper_2407_10914_gb300.adjoint import Run
     n, T = args.adjoint_size, args.adjoint_steps
@@ -994,23 +1047,45 @@ def run_adjoint(args, torch, lbm):
         s.step(T)
         return s.reduce(lbm.LBM_SW_SMOOTH)
 
-    hth = 1.0  # degrees
-    fd_th = (sw(theta_deg=case.params["theta_deg"] + hth)
-             - sw(theta_deg=case.params["theta_deg"] - hth)) / (2 * hth)
+    th0 = case.params["theta_deg"]
     g0 = case.params["g"][0]
-    hg = 0.1 * g0
-    fd_g = (sw(g=(g0 + hg, 0.0, 0.0)) - sw(g=(g0 - hg, 0.0, 0.0))) / (2 * hg)
+    # central differences of the FP32 forward run over a range of steps
+    sweep_th, sweep_g = {}, {}
+    for hth in (0.25, 0.5, 1.0, 2.0):
+        sweep_th[str(hth)] = (sw(theta_deg=th0 + hth)
+                              - sw(theta_deg=th0 - hth)) / (2 * hth)
+    for frac in (0.05, 0.1, 0.2, 0.4):
+        hg = frac * g0
+        sweep_g[str(frac)] = (sw(g=(g0 + hg, 0.0, 0.0))
+                              - sw(g=(g0 - hg, 0.0, 0.0))) / (2 * hg)
+    fd_th, hth = sweep_th["1.0"], 1.0
+    fd_g, hg = sweep_g["0.1"], 0.1 * g0
     ad_th = dth * math.pi / 180.0  # per degree
+    # the regularisation of the linearisation: (freeze_sin, c_min)
+    s.set_params(**case.params)
+    regs = {}
+    for fz, cm in ((0.05, 1e-3), (0.02, 1e-3), (0.1, 1e-3), (0.05, 1e-4),
+                   (0.05, 1e-2), (0.01, 1e-4), (0.005, 1e-5), (0.002, 1e-6),
+                   (0.0, 1e-3), (0.05, 0.0), (0.0, 0.0)):
+        r2 = Run(s, case.phi0, T, every=45 if T == 2000 else None,
+                 freeze_sin=fz, c_min=cm)
+        r2.forward()
+        a_th, a_g = r2.backward()
+        regs[f"{fz}/{cm}"] = {"dJ_dtheta_per_deg": a_th * math.pi / 180.0,
+                              "dJ_dgx": float(a_g[0])}
     nf = s.n_fluid
-    return {
+    out = {
         "workload": f"adjoint_pack{n}_scheme2_T{T}",
         "fluid_nodes": nf, "steps": T, "checkpoint_every": run.K,
         "J_sw_smooth": J,
         "dJ_dtheta_per_deg": {"adjoint": ad_th, "central_fd_fp32": fd_th,
                               "h_deg": hth,
-                              "rel_diff": abs(ad_th - fd_th) / abs(fd_th)},
+                              "rel_diff": abs(ad_th - fd_th) / abs(fd_th),
+                              "fd_fp32_by_h_deg": sweep_th},
         "dJ_dgx": {"adjoint": float(dg[0]), "central_fd_fp32": fd_g,
-                   "h": hg, "rel_diff": abs(dg[0] - fd_g) / abs(fd_g)},
+                   "h": hg, "rel_diff": abs(dg[0] - fd_g) / abs(fd_g),
+                   "fd_fp32_by_h_frac": sweep_g},
+        "adjoint_by_freeze_sin_c_min": regs,
         "forward_ms": round(fwd_ms, 1), "backward_ms": round(bwd_ms, 1),
         "gradient_MLUPS": round(nf * T / ((fwd_ms + bwd_ms) * 1e-3) / 1e6, 1),
         "freeze_sin": run.freeze_sin, "c_min": run.c_min,
@@ -1020,6 +1095,63 @@ def run_adjoint(args, torch, lbm):
                 "long runs); the FP64 tangent-linear oracle checks the same "
                 "code to 1e-3 (tests/test_gpu_adjoint.py)",
     }
+    if args.adjoint_fd64:
+        out["fd_fp64_oracle"] = adjoint_fd64(case, T, args.adjoint_fd64)
+    if args.adjoint_tlm64:
+        out["tlm_fp64_oracle"] = adjoint_tlm64(case, T, run.freeze_sin,
+                                               run.c_min)
+    return out
+
+
+def adjoint_tlm64(case, T: int, freeze_sin: float, c_min: float) -> dict:
+    """The FP64 oracle's tangent-linear run at the full size of the
+    gradient workload with the adjoint's regularisation: the same
+    derivative of the same regularised linearisation, from the forward
+    mode and in FP64."""
+    from oracle import oracle as O
+    t0 = time.time()
+    t = O.TangentLinear(case.lattice, case.solid, case.periodic)
+    t.set_params(**case.params)
+    t.set_freeze(freeze_sin)
+    t.set_cmin(c_min)
+    t.init_state(case.phi0)
+    t.step(T)
+    J, dth, dg = t.sw()
+    return {"J": J, "dJ_dtheta_per_deg": dth * math.pi / 180.0,
+            "dJ_dgx": dg, "freeze_sin": freeze_sin, "c_min": c_min,
+            "seconds": round(time.time() - t0, 1)}
+
+
+def adjoint_fd64(case, T: int, which: str = "all") -> dict:
+    """Central differences of the FP64 oracle's forward run at the full size
+    of the gradient workload (about 150 s per run on 16 host cores): theta
+    at h = 0.5 and 1 deg, g_x at h = 10 % of g_x ("all"); or g_x alone at
+    h = 5, 10 and 20 % ("gx")."""
+    from oracle import oracle as O
+
+    def sw64(**over):
+        p = dict(case.params)
+        p.update(over)
+        o = O.Oracle(case.lattice, case.solid, case.periodic)
+        o.set_params(**p)
+        o.init_state(case.phi0)
+        o.step(T)
+        return o.reduce(O.SW_SMOOTH)
+
+    t0 = time.time()
+    th0, g0 = case.params["theta_deg"], case.params["g"][0]
+    out = {"J": sw64()}
+    if which == "all":
+        out["dJ_dtheta_per_deg"] = {
+            str(h): (sw64(theta_deg=th0 + h) - sw64(theta_deg=th0 - h))
+            / (2 * h) for h in (0.5, 1.0)}
+    out["dJ_dgx"] = {}
+    for frac in ((0.1,) if which == "all" else (0.05, 0.1, 0.2)):
+        hg = frac * g0
+        out["dJ_dgx"][str(frac)] = (sw64(g=(g0 + hg, 0.0, 0.0))
+                                    - sw64(g=(g0 - hg, 0.0, 0.0))) / (2 * hg)
+    out["seconds"] = round(time.time() - t0, 1)
+    return out
 
 
 def main():

@@ -128,6 +128,28 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
                              void *dev_workspace, size_t ws_bytes,
                              void *stream);
 
+/* The two calls above with a chosen tile shape. The fluid nodes are
+ * numbered tile by tile, tiles of tile[0] x tile[1] x tile[2] nodes (x, y,
+ * z; host array of 3 ints). NULL gives the default the calls above use:
+ * 32 x 8 x 8 (D3Q19), 64 x 32 x 1 (D2Q9). Each extent a power of two,
+ * tile[0] from 32 to 1024, at most 16384 nodes, tile[2] = 1 for D2Q9;
+ * otherwise the size call returns 0 and the init call LBM_ERR_ARG. A
+ * workspace must be sized with the same tile shape it is built with. The
+ * shape sets only where each node's values sit in memory (so how well the
+ * step's neighbour reads share cache lines): every per-node result
+ * (lbm_macros, lbm_get_populations) is the same bit for bit for every
+ * shape; sums over nodes (lbm_reduce) may differ in rounding order, and a
+ * state saved by lbm_save_state loads only into a domain of the same
+ * shape. */
+size_t lbm_workspace_bytes_tiled(int lattice, int nx, int ny, int nz,
+                                 const uint8_t *solid_host, int storage,
+                                 const int *tile);
+lbm_status lbm_init_geometry_tiled(lbm_handle *out, int lattice, int nx,
+                                   int ny, int nz, const uint8_t *solid_host,
+                                   unsigned periodic_mask, int storage,
+                                   const int *tile, void *dev_workspace,
+                                   size_t ws_bytes, void *stream);
+
 /* Set the parameters (host struct, copied). Validates them. */
 lbm_status lbm_set_params(lbm_handle h, const lbm_params *p);
 

@@ -1,12 +1,15 @@
-"""Choice of a batch's schedule (mode, threads per block, chunk) by timing.
+"""Choice by timing of a batch's schedule (mode, threads per block, chunk)
+and of a domain's tile shape (the blocks in which its fluid nodes are
+numbered in memory).
 
-Every schedule gives the same results bit for bit, so the trials are real
-steps of the run: each candidate takes one untimed step (which records its
-CUDA graph) and ``trial_steps`` steps timed with CUDA events on the
-batch's stream; the fastest wins. The winner is cached per shape class, the
-lattice, storage, case count and the total fluid and solid-boundary node
-counts to two significant digits, in a JSON file, so a batch of the same
-class later skips the search.
+Every schedule gives the same results bit for bit, so the schedule trials
+are real steps of the run: each candidate takes one untimed step (which
+records its CUDA graph) and ``trial_steps`` steps timed with CUDA events on
+the batch's stream; the fastest wins. The tile shape is fixed when a
+domain's geometry is built, so its trials build one domain (or batch) per
+candidate from a caller's factory and time it the same way; per-node
+results do not depend on the shape. Winners are cached per shape class in
+a JSON file, so a batch or domain of the same class later skips the search.
 """
 from __future__ import annotations
 
@@ -20,6 +23,15 @@ from typing import Dict, Optional, Tuple
 # mode 1 = one persistent launch per call with chunk blocks per work item
 CANDIDATES = ((0, 256, 1), (0, 128, 1), (1, 256, 1), (1, 256, 4),
               (1, 256, 16), (1, 128, 4), (1, 128, 16))
+
+
+# tile shapes (x, y, z) tried per lattice; the first is the library default
+TILE_CANDIDATES = {
+    19: ((32, 8, 8), (32, 4, 4), (64, 4, 4), (32, 4, 8), (64, 8, 8),
+         (32, 16, 16), (128, 2, 2), (128, 8, 4)),
+    9: ((64, 32, 1), (32, 32, 1), (32, 64, 1), (128, 16, 1), (64, 64, 1),
+        (256, 8, 1)),
+}
 
 
 def default_cache_path() -> str:
@@ -111,3 +123,63 @@ def tune(batch, trial_steps: int = 8, cache_path: Optional[str] = None,
         store_cache(path, key, entry)
     return {"config": best, "key": key, "cached": False, "steps_used": used,
             "ms_per_step": timings[best], "trials": entry["trials"]}
+
+
+def _time_steps(obj, torch, trial_steps: int) -> float:
+    stream = torch.cuda.current_stream()
+    obj.step(1)  # records the graph
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    obj.step(trial_steps)
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / trial_steps
+
+
+def tile_class(q: int, storage: str, shape, counts) -> str:
+    """Key of a domain for the tile choice: lattice, storage, box shape
+    (nz, ny, nx) and (n_fluid, n_solid_boundary) to two significant digits
+    (summed over the cases of a batch)."""
+    nf = sum(int(c[0]) for c in counts)
+    ns = sum(int(c[1]) for c in counts)
+    dims = "x".join(str(int(v)) for v in shape)
+    return f"tile-Q{q}-{storage}-{dims}-n{len(counts)}-F{_sig2(nf)}-S{_sig2(ns)}"
+
+
+def tune_tile(make, q: int, key: Optional[str] = None,
+              candidates=None, trial_steps: int = 8,
+              cache_path: Optional[str] = None,
+              use_cache: bool = True) -> dict:
+    """Pick the fastest tile shape. make(tile) builds a ready-to-step
+    object (a lbm.Session with parameters and state set, or a lbm.Batch of
+    such sessions) whose fluid nodes are numbered in tiles of that shape;
+    each candidate's object takes one untimed and ``trial_steps`` timed
+    steps and is then dropped. Returns {"tile", "key", "cached",
+    "ms_per_step", "trials"}; build the run's own object with the returned
+    tile. With a key and use_cache, the winner is read from and stored in
+    the cache."""
+    cands = tuple(candidates or TILE_CANDIDATES[q])
+    path = cache_path or default_cache_path()
+    if use_cache and key:
+        hit = load_cache(path).get(key)
+        if hit and tuple(hit.get("tile", ())) in cands:
+            return {"tile": tuple(hit["tile"]), "key": key, "cached": True,
+                    "ms_per_step": hit.get("ms_per_step"),
+                    "trials": hit.get("trials")}
+    timings = {}
+    torch = None
+    for tile in cands:
+        obj = make(tile)
+        torch = obj.torch
+        timings[tuple(tile)] = _time_steps(obj, torch, trial_steps)
+        del obj
+    order = {tuple(c): i for i, c in enumerate(cands)}
+    best = min(timings, key=lambda t: (timings[t], order[t]))
+    trials = {"x".join(map(str, t)): v for t, v in timings.items()}
+    if use_cache and key:
+        store_cache(path, key, {"tile": list(best),
+                                "ms_per_step": timings[best],
+                                "trials": trials})
+    return {"tile": best, "key": key, "cached": False,
+            "ms_per_step": timings[best], "trials": trials}

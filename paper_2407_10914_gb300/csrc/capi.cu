@@ -56,16 +56,35 @@ struct Layout {
 
 // NF is the number of fluid nodes; NS an upper bound of the solid-boundary
 // nodes (the number of solid nodes).
+// Tile extents as log2 (lx, ly, lz): the caller's tile[3] (powers of two,
+// x extent 32..1024, at most 2^14 nodes, z extent 1 for D2Q9) or, for a
+// null tile, 32 x 8 x 8 (D3Q19) / 64 x 32 x 1 (D2Q9). False if invalid.
+bool tile_shape(int Q, const int *tile, int lg[3]) {
+  if (!tile) {
+    lg[0] = Q == 19 ? 5 : 6;
+    lg[1] = Q == 19 ? 3 : 5;
+    lg[2] = Q == 19 ? 3 : 0;
+    return true;
+  }
+  for (int a = 0; a < 3; ++a) {
+    const int t = tile[a];
+    if (t < 1 || t > 1024 || (t & (t - 1))) return false;
+    lg[a] = 0;
+    while ((1 << lg[a]) < t) ++lg[a];
+  }
+  if (lg[0] < lbm::TILE_MIN_LX || lg[0] > lbm::TILE_MAX_LX) return false;
+  if (lg[0] + lg[1] + lg[2] > lbm::TILE_MAX_LN) return false;
+  return Q == 19 || lg[2] == 0;
+}
+
 Layout make_layout(int Q, int nx, int ny, int nz, int storage, long long NF,
-                   long long NS) {
+                   long long NS, const int lg[3]) {
   Layout L{};
   const long long N = (long long)nx * ny * nz;
   L.NF = NF;
   L.NFp = pad64(NF > 0 ? NF : 1);
   L.NS = NS;
-  const int TX = Q == 19 ? lbm::Tile<19>::TX : lbm::Tile<9>::TX;
-  const int TY = Q == 19 ? lbm::Tile<19>::TY : lbm::Tile<9>::TY;
-  const int TZ = Q == 19 ? lbm::Tile<19>::TZ : lbm::Tile<9>::TZ;
+  const int TX = 1 << lg[0], TY = 1 << lg[1], TZ = 1 << lg[2];
   L.ntx = (nx + TX - 1) / TX;
   L.nty = (ny + TY - 1) / TY;
   L.ntz = (nz + TZ - 1) / TZ;
@@ -137,24 +156,44 @@ void swap_buffers(lbm_ctx *c) { lbm::swap_state(c); }
 
 extern "C" {
 
-size_t lbm_workspace_bytes(int lattice, int nx, int ny, int nz,
-                           const uint8_t *solid_host, int storage) {
+size_t lbm_workspace_bytes_tiled(int lattice, int nx, int ny, int nz,
+                                 const uint8_t *solid_host, int storage,
+                                 const int *tile) {
+  int lg[3];
   if (!valid_shape(lattice, nx, ny, nz)) return 0;
-  if (storage < 0 || storage > 2) return 0;
+  if (storage < 0 || storage > 2 || !tile_shape(lattice, tile, lg)) return 0;
   const long long N = (long long)nx * ny * nz;
   const long long ns = solid_host ? count_solid(solid_host, N) : N;
   const long long nf = solid_host ? N - ns : N;
-  return make_layout(lattice, nx, ny, nz, storage, nf, ns).total;
+  return make_layout(lattice, nx, ny, nz, storage, nf, ns, lg).total;
+}
+
+size_t lbm_workspace_bytes(int lattice, int nx, int ny, int nz,
+                           const uint8_t *solid_host, int storage) {
+  return lbm_workspace_bytes_tiled(lattice, nx, ny, nz, solid_host, storage,
+                                   nullptr);
 }
 
 lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
                              int nz, const uint8_t *solid_host,
                              unsigned periodic_mask, int storage,
                              void *ws, size_t ws_bytes, void *stream) {
+  return lbm_init_geometry_tiled(out, lattice, nx, ny, nz, solid_host,
+                                 periodic_mask, storage, nullptr, ws,
+                                 ws_bytes, stream);
+}
+
+lbm_status lbm_init_geometry_tiled(lbm_handle *out, int lattice, int nx,
+                                   int ny, int nz, const uint8_t *solid_host,
+                                   unsigned periodic_mask, int storage,
+                                   const int *tile, void *ws, size_t ws_bytes,
+                                   void *stream) {
   if (!out) return LBM_ERR_ARG;
   *out = nullptr;
+  int lg[3];
   if (!valid_shape(lattice, nx, ny, nz) || !solid_host || !ws ||
-      storage < 0 || storage > 2 || periodic_mask > 7u)
+      storage < 0 || storage > 2 || periodic_mask > 7u ||
+      !tile_shape(lattice, tile, lg))
     return LBM_ERR_ARG;
   if (((uintptr_t)ws) % ALIGN) return LBM_ERR_ARG;
   const long long N = (long long)nx * ny * nz;
@@ -163,7 +202,7 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
   // node indices travel in 29 bits of a neighbour entry
   if (N - n_solid >= (1LL << 29) || n_solid >= (1LL << 29)) return LBM_ERR_ARG;
   const Layout L = make_layout(lattice, nx, ny, nz, storage, N - n_solid,
-                               n_solid);
+                               n_solid, lg);
   if (ws_bytes < L.total) return LBM_ERR_NOMEM;
   lbm_ctx *c = new (std::nothrow) lbm_ctx();
   if (!c) return LBM_ERR_NOMEM;
@@ -199,6 +238,9 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
   d.ntx = L.ntx;
   d.nty = L.nty;
   d.ntz = L.ntz;
+  d.tlx = lg[0];
+  d.tly = lg[1];
+  d.tlz = lg[2];
   d.ntiles = (int)L.ntiles;
   d.NF = (int)L.NF;
   d.NS = (int)L.NS;  // upper bound until the lists are built

@@ -52,6 +52,7 @@ struct Dom {
   long long N;      // nodes of the box
   unsigned periodic;
   int ntx, nty, ntz;  // tiles per axis
+  int tlx, tly, tlz;  // log2 of the tile extents
   int ntiles;
   int NF, NS;       // fluid nodes, solid-boundary nodes
   long long NFp;    // stride of one population plane (NF rounded up)

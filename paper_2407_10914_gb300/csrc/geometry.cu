@@ -42,9 +42,7 @@ __global__ void k_classify(Dom d, const uint8_t *__restrict__ mask,
 }
 
 // One block per tile: fluid and solid-boundary counts of the tile.
-template <int Q>
 __global__ void k_tile_count(Dom d, int *__restrict__ cf, int *__restrict__ cs) {
-  using G = TileGeo<Q>;
   __shared__ int sf, ss;
   if (threadIdx.x == 0) {
     sf = 0;
@@ -52,13 +50,13 @@ __global__ void k_tile_count(Dom d, int *__restrict__ cf, int *__restrict__ cs) 
   }
   __syncthreads();
   const int t = blockIdx.x;
-  const int X0 = (t % d.ntx) * G::TX;
-  const int q = t / d.ntx;
-  const int Y0 = (q % d.nty) * G::TY, Z0 = (q / d.nty) * G::TZ;
+  int X0, Y0, Z0;
+  tile_origin(d, t, X0, Y0, Z0);
+  const int TN = 1 << (d.tlx + d.tly + d.tlz);
   int nf = 0, ns = 0;
-  for (int lp = threadIdx.x; lp < G::TN; lp += GBLOCK) {
+  for (int lp = threadIdx.x; lp < TN; lp += GBLOCK) {
     int x, y, z;
-    local_node<Q>(lp, X0, Y0, Z0, x, y, z);
+    local_node(d, lp, X0, Y0, Z0, x, y, z);
     if (x >= d.nx || y >= d.ny || z >= d.nz) continue;
     const int c = d.cls[x + d.nx * (y + d.ny * z)];
     nf += (c & 2) ? 1 : 0;
@@ -172,16 +170,14 @@ static void scan_exclusive(const int *in, int *out, long long n, int *bsum,
 // Zou-He planes of an x-axis flow are runs of consecutive F indices (the
 // fix-up pass reads and writes them coalesced) instead of nodes a tile row
 // apart; for every other node the order is the plain tile order.
-template <int Q>
 __global__ void k_tile_map(Dom d, uint16_t *__restrict__ map,
                            int *__restrict__ fg, int *__restrict__ sg) {
-  using G = TileGeo<Q>;
   __shared__ int wf[GBLOCK / 32], ws[GBLOCK / 32];
   __shared__ int carry_f, carry_s;
   const int t = blockIdx.x;
-  const int X0 = (t % d.ntx) * G::TX;
-  const int q = t / d.ntx;
-  const int Y0 = (q % d.nty) * G::TY, Z0 = (q / d.nty) * G::TZ;
+  int X0, Y0, Z0;
+  tile_origin(d, t, X0, Y0, Z0);
+  const int TN = 1 << (d.tlx + d.tly + d.tlz);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   if (threadIdx.x == 0) {
@@ -190,13 +186,14 @@ __global__ void k_tile_map(Dom d, uint16_t *__restrict__ map,
   }
   __syncthreads();
   // pass 0: the x-face fluid nodes (tiles on an x face only); pass 1: the rest
-  const bool face_tile = X0 == 0 || X0 + G::TX >= d.nx;
+  const bool face_tile = X0 == 0 || X0 + (1 << d.tlx) >= d.nx;
   for (int pass = face_tile ? 0 : 1; pass < 2; ++pass) {
-    for (int c0 = 0; c0 < G::TN; c0 += GBLOCK) {
+    for (int c0 = 0; c0 < TN; c0 += GBLOCK) {
       const int lp = c0 + threadIdx.x;
       int x, y, z;
-      local_node<Q>(lp, X0, Y0, Z0, x, y, z);
-      const bool valid = x < d.nx && y < d.ny && z < d.nz;
+      local_node(d, lp, X0, Y0, Z0, x, y, z);
+      // a tile smaller than the block leaves the block's last threads idle
+      const bool valid = lp < TN && x < d.nx && y < d.ny && z < d.nz;
       const int g = valid ? x + d.nx * (y + d.ny * z) : 0;
       const int c = valid ? d.cls[g] : CLS_SOLID;
       const bool face = x == 0 || x == d.nx - 1;
@@ -284,7 +281,7 @@ __global__ void k_dense_entries(Dom d, uint32_t *__restrict__ nbd) {
       out = true;
     }
   }
-  const uint32_t e = box_entry<Q>(d, c[0], c[1], c[2]);
+  const uint32_t e = box_entry(d, c[0], c[1], c[2]);
   nbd[p] = out ? (e | OUT_BIT) : e;
 }
 
@@ -309,7 +306,7 @@ __global__ void k_s_links(Dom d, const int *__restrict__ off,
     const int Y = axis_step(y + Lattice<Q>::ey(i), d.ny, d.periodic & 2u, false, out);
     const int Z = axis_step(z + Lattice<Q>::ez(i), d.nz, d.periodic & 4u, false, out);
     if (out) continue;
-    const uint32_t e = box_entry<Q>(d, X, Y, Z);
+    const uint32_t e = box_entry(d, X, Y, Z);
     if (!(entry_cls(e) & 2)) continue;
     if (links)
       links[at + n] = (uint32_t)entry_idx(e) |
@@ -454,18 +451,12 @@ cudaError_t build_geometry(lbm_ctx *c, cudaStream_t s) {
   else
     k_classify<9><<<gN, GBLOCK, 0, s>>>(d, c->mask, cls);
   const unsigned nt = (unsigned)c->ntiles;
-  if (c->Q == 19)
-    k_tile_count<19><<<nt, GBLOCK, 0, s>>>(d, c->cnt_f, c->cnt_s);
-  else
-    k_tile_count<9><<<nt, GBLOCK, 0, s>>>(d, c->cnt_f, c->cnt_s);
+  k_tile_count<<<nt, GBLOCK, 0, s>>>(d, c->cnt_f, c->cnt_s);
   k_scan<<<1, 1024, 0, s>>>(c->cnt_f, c->ntiles, const_cast<int *>(d.fbase));
   k_scan<<<1, 1024, 0, s>>>(c->cnt_s, c->ntiles, const_cast<int *>(d.sbase));
   uint16_t *map = const_cast<uint16_t *>(d.map);
   int *fg = const_cast<int *>(d.fg), *sg = const_cast<int *>(d.sg);
-  if (c->Q == 19)
-    k_tile_map<19><<<nt, GBLOCK, 0, s>>>(d, map, fg, sg);
-  else
-    k_tile_map<9><<<nt, GBLOCK, 0, s>>>(d, map, fg, sg);
+  k_tile_map<<<nt, GBLOCK, 0, s>>>(d, map, fg, sg);
   int tot[2] = {0, 0};
   cudaError_t e = cudaMemcpyAsync(&tot[0], d.fbase + c->ntiles, sizeof(int),
                                   cudaMemcpyDeviceToHost, s);

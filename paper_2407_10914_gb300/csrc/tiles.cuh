@@ -1,11 +1,13 @@
 // Tiles of the box, the entries that name a box position's node, and the
 // pull of Eq. (1).
 //
-// The box is cut into tiles of TX x TY x TZ nodes (32 x 8 x 8 for D3Q19,
-// 64 x 32 x 1 for D2Q9). Fluid nodes are numbered tile by tile (F-space),
-// and within a tile the fluid nodes on the box's x faces first, then the
-// others in (z, y, x) order; solid-boundary nodes in (z, y, x) order
-// (S-space). The uint16 map over the box holds a node's class (bits 14-15)
+// The box is cut into tiles of TX x TY x TZ nodes (by default 32 x 8 x 8
+// for D3Q19, 64 x 32 x 1 for D2Q9; the shape is chosen when the geometry is
+// built: powers of two, TX from 32 to 1024, at most 16384 nodes). Fluid
+// nodes are numbered tile by tile (F-space), and within a tile the fluid
+// nodes on the box's x faces first, then the others in (z, y, x) order;
+// solid-boundary nodes in (z, y, x) order (S-space). The shape changes
+// only where a node's values sit in memory, never what is computed. The uint16 map over the box holds a node's class (bits 14-15)
 // and its rank among the nodes of its kind in its tile (bits 0-13); with the
 // per-tile bases fbase/sbase this gives its F- or S-index.
 //
@@ -20,24 +22,9 @@
 
 namespace lbm {
 
-template <int Q>
-struct Tile;
-
-template <>
-struct Tile<19> {
-  static constexpr int TX = 32, TY = 8, TZ = 8, LX = 5, LY = 3, LZ = 3;
-};
-
-template <>
-struct Tile<9> {
-  static constexpr int TX = 64, TY = 32, TZ = 1, LX = 6, LY = 5, LZ = 0;
-};
-
-template <int Q>
-struct TileGeo {
-  static constexpr int TX = Tile<Q>::TX, TY = Tile<Q>::TY, TZ = Tile<Q>::TZ;
-  static constexpr int TN = TX * TY * TZ;
-};
+// Limits of a tile shape (log2 of the extents): the x extent from a warp's
+// run of nodes to 1024, at most 2^14 nodes (the rank field of the map).
+constexpr int TILE_MIN_LX = 5, TILE_MAX_LX = 10, TILE_MAX_LN = 14;
 
 // Entries: class << 30 | index (index < 2^29). In the dense entry box a halo
 // cell off a non-periodic axis holds the entry of the clamped position (the
@@ -51,34 +38,36 @@ __device__ __forceinline__ int entry_idx(uint32_t e) {
 __device__ __forceinline__ bool entry_out(uint32_t e) { return e & OUT_BIT; }
 
 // Tile number of box node (X, Y, Z).
-template <int Q>
 __device__ __forceinline__ int tile_of(const Dom &d, int X, int Y, int Z) {
-  return (X >> Tile<Q>::LX) +
-         d.ntx * ((Y >> Tile<Q>::LY) + d.nty * (Z >> Tile<Q>::LZ));
+  return (X >> d.tlx) + d.ntx * ((Y >> d.tly) + d.nty * (Z >> d.tlz));
 }
 
 // Entry of box node (X, Y, Z) (inside the box).
-template <int Q>
 __device__ __forceinline__ uint32_t box_entry(const Dom &d, int X, int Y,
                                               int Z) {
   const uint16_t m = __ldg(d.map + (X + d.nx * (Y + d.ny * Z)));
   const int cls = m >> 14;
-  const int t = tile_of<Q>(d, X, Y, Z);
+  const int t = tile_of(d, X, Y, Z);
   const int base = __ldg(((cls & 2) ? d.fbase : d.sbase) + t);
   return ((uint32_t)cls << 30) | (uint32_t)(base + (m & 0x3FFF));
 }
 
-// Box coordinates of the tile-local node lp.
-template <int Q>
-__device__ __forceinline__ void local_node(int lp, int X0, int Y0, int Z0,
-                                           int &x, int &y, int &z) {
-  using G = TileGeo<Q>;
-  const int lx = lp & (G::TX - 1);
-  const int ly = (lp >> Tile<Q>::LX) & (G::TY - 1);
-  const int lz = lp >> (Tile<Q>::LX + Tile<Q>::LY);
-  x = X0 + lx;
-  y = Y0 + ly;
-  z = Z0 + lz;
+// Origin of tile t.
+__device__ __forceinline__ void tile_origin(const Dom &d, int t, int &X0,
+                                            int &Y0, int &Z0) {
+  const int q = t / d.ntx;
+  X0 = (t % d.ntx) << d.tlx;
+  Y0 = (q % d.nty) << d.tly;
+  Z0 = (q / d.nty) << d.tlz;
+}
+
+// Box coordinates of the tile-local node lp of the tile at (X0, Y0, Z0).
+__device__ __forceinline__ void local_node(const Dom &d, int lp, int X0,
+                                           int Y0, int Z0, int &x, int &y,
+                                           int &z) {
+  x = X0 + (lp & ((1 << d.tlx) - 1));
+  y = Y0 + ((lp >> d.tlx) & ((1 << d.tly) - 1));
+  z = Z0 + (lp >> (d.tlx + d.tly));
 }
 
 // Entry of the lattice neighbour x + e_dir of the fluid node at padded box

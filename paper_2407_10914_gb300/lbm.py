@@ -27,7 +27,9 @@ STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_CUDA",
 STORAGE = {"fp32": 0, "fp16": 1, "bf16": 2}
 (LBM_MASS_R, LBM_MASS_B, LBM_SW_COUNT, LBM_SW_SMOOTH, LBM_DP, LBM_CA_R,
  LBM_CA_B) = range(7)
-EXPORTS = ("lbm_workspace_bytes", "lbm_init_geometry", "lbm_set_params",
+EXPORTS = ("lbm_workspace_bytes", "lbm_init_geometry",
+           "lbm_workspace_bytes_tiled", "lbm_init_geometry_tiled",
+           "lbm_set_params",
            "lbm_init_state", "lbm_step", "lbm_step_timed", "lbm_macros",
            "lbm_reduce",
            "lbm_get_populations", "lbm_set_populations", "lbm_swap_inlet",
@@ -81,6 +83,12 @@ def load_library(path: str = LIB_PATH):
     L.lbm_init_geometry.restype = C.c_int
     L.lbm_init_geometry.argtypes = [C.POINTER(vp)] + [C.c_int] * 4 + [
         vp, C.c_uint, C.c_int, vp, sz, vp]
+    L.lbm_workspace_bytes_tiled.restype = sz
+    L.lbm_workspace_bytes_tiled.argtypes = [C.c_int] * 4 + [
+        vp, C.c_int, C.POINTER(C.c_int)]
+    L.lbm_init_geometry_tiled.restype = C.c_int
+    L.lbm_init_geometry_tiled.argtypes = [C.POINTER(vp)] + [C.c_int] * 4 + [
+        vp, C.c_uint, C.c_int, C.POINTER(C.c_int), vp, sz, vp]
     L.lbm_set_params.restype = C.c_int
     L.lbm_set_params.argtypes = [vp, C.POINTER(lbm_params)]
     L.lbm_init_state.restype = C.c_int
@@ -204,6 +212,20 @@ def lbm_workspace_bytes(lattice, nx, ny, nz, solid: Optional[np.ndarray],
     return int(L.lbm_workspace_bytes(lattice, nx, ny, nz, sp, storage))
 
 
+def _tile_arg(tile):
+    return None if tile is None else (C.c_int * 3)(*[int(t) for t in tile])
+
+
+def lbm_workspace_bytes_tiled(lattice, nx, ny, nz,
+                              solid: Optional[np.ndarray], storage=0,
+                              tile=None) -> int:
+    """tile: None (the default shape) or (tx, ty, tz)."""
+    L = load_library()
+    sp = None if solid is None else solid.ctypes.data_as(C.c_void_p)
+    return int(L.lbm_workspace_bytes_tiled(lattice, nx, ny, nz, sp, storage,
+                                           _tile_arg(tile)))
+
+
 def lbm_init_geometry(lattice, nx, ny, nz, solid: np.ndarray, periodic_mask,
                       storage, workspace, stream) -> C.c_void_p:
     L = load_library()
@@ -214,6 +236,21 @@ def lbm_init_geometry(lattice, nx, ny, nz, solid: np.ndarray, periodic_mask,
                              storage, _dptr(workspace), workspace.numel(),
                              stream)
     _check(st, None, "lbm_init_geometry")
+    return h
+
+
+def lbm_init_geometry_tiled(lattice, nx, ny, nz, solid: np.ndarray,
+                            periodic_mask, storage, tile, workspace,
+                            stream) -> C.c_void_p:
+    L = load_library()
+    h = C.c_void_p()
+    solid = np.ascontiguousarray(solid, np.uint8)
+    st = L.lbm_init_geometry_tiled(C.byref(h), lattice, nx, ny, nz,
+                                   solid.ctypes.data_as(C.c_void_p),
+                                   periodic_mask, storage, _tile_arg(tile),
+                                   _dptr(workspace), workspace.numel(),
+                                   stream)
+    _check(st, None, "lbm_init_geometry_tiled")
     return h
 
 
@@ -331,7 +368,7 @@ class Session:
     out as torch tensors of shape (nz, ny, nx) (x fastest)."""
 
     def __init__(self, lattice: int, solid: np.ndarray, periodic=(True,) * 3,
-                 storage: str = "fp32", device: str = "cuda"):
+                 storage: str = "fp32", device: str = "cuda", tile=None):
         torch = _torch()
         self.torch = torch
         solid = np.ascontiguousarray(solid, np.uint8)
@@ -344,13 +381,15 @@ class Session:
         self.storage = storage
         self.device = torch.device(device)
         mask = sum((1 << a) for a in range(3) if periodic[a])
-        ws = lbm_workspace_bytes(lattice, nx, ny, nz, solid, STORAGE[storage])
+        self.tile = None if tile is None else tuple(int(t) for t in tile)
+        ws = lbm_workspace_bytes_tiled(lattice, nx, ny, nz, solid,
+                                       STORAGE[storage], self.tile)
         if ws == 0:
-            raise LbmError("bad domain")
+            raise LbmError("bad domain or tile shape")
         self.workspace = torch.empty(ws, dtype=torch.uint8, device=self.device)
-        self.h = lbm_init_geometry(lattice, nx, ny, nz, solid, mask,
-                                   STORAGE[storage], self.workspace,
-                                   self.stream())
+        self.h = lbm_init_geometry_tiled(lattice, nx, ny, nz, solid, mask,
+                                         STORAGE[storage], self.tile,
+                                         self.workspace, self.stream())
         self.counts = lbm_counts(self.h)
         self._solid = solid
         self.n_zou_he = 0

@@ -51,6 +51,39 @@ def test_workspace_bytes_host_only(lib):
     assert lbm.lbm_workspace_bytes(19, 6, 5, 4, solid, 5) == 0
 
 
+def test_tile_shapes_host_only(lib):
+    """Tile shapes: powers of two, x extent 32..1024, at most 16384 nodes,
+    z extent 1 on D2Q9; the default shape is what a null tile gives; the
+    per-tile arrays grow with the number of tiles."""
+    from paper_2407_10914_gb300 import autotune, lbm
+    solid = np.zeros((20, 30, 70), np.uint8)
+    args = (19, 70, 30, 20, solid, 0)
+    base = lbm.lbm_workspace_bytes(*args)
+    assert lbm.lbm_workspace_bytes_tiled(*args, None) == base
+    assert lbm.lbm_workspace_bytes_tiled(*args, (32, 8, 8)) == base
+    assert lbm.lbm_workspace_bytes_tiled(*args, (32, 1, 1)) > base
+    for bad in ((16, 8, 8), (48, 8, 8), (32, 32, 32), (2048, 1, 1),
+                (32, 0, 8), (32, 8, -8), (32, 3, 8)):
+        assert lbm.lbm_workspace_bytes_tiled(*args, bad) == 0, bad
+    s2 = np.zeros((1, 30, 70), np.uint8)
+    assert lbm.lbm_workspace_bytes_tiled(9, 70, 30, 1, s2, 0, (64, 32, 1)) \
+        == lbm.lbm_workspace_bytes(9, 70, 30, 1, s2, 0)
+    assert lbm.lbm_workspace_bytes_tiled(9, 70, 30, 1, s2, 0, (64, 16, 2)) == 0
+    h = C.c_void_p()
+    sp = solid.ctypes.data_as(C.c_void_p)
+    bad = (C.c_int * 3)(16, 8, 8)
+    assert lib.lbm_init_geometry_tiled(C.byref(h), 19, 70, 30, 20, sp, 7, 0,
+                                       bad, C.c_void_p(256), 1 << 30,
+                                       None) == -1
+    assert not h.value
+    for q, cands in autotune.TILE_CANDIDATES.items():
+        assert cands[0] == ((32, 8, 8) if q == 19 else (64, 32, 1))
+        for t in cands:
+            sh = (20, 30, 70) if q == 19 else (1, 30, 70)
+            assert lbm.lbm_workspace_bytes_tiled(
+                q, 70, 30, sh[0], np.zeros(sh, np.uint8), 0, t) > 0, t
+
+
 def test_init_geometry_rejects_bad_arguments(lib):
     h = C.c_void_p()
     solid = np.zeros(8, np.uint8)
