@@ -52,7 +52,6 @@ struct Dom {
   long long N;      // nodes of the box
   unsigned periodic;
   int ntx, nty, ntz;  // tiles per axis
-  int tlx, tly, tlz;  // log2 of the tile extents
   int ntiles;
   int NF, NS;       // fluid nodes, solid-boundary nodes
   long long NFp;    // stride of one population plane (NF rounded up)
@@ -104,6 +103,7 @@ struct Dom {
   int px, py;
   unsigned *err;        // error word of the bounds-checked build (guard())
   StepConst c;
+  int tlx, tly, tlz;    // log2 of the tile extents (set-up kernels only)
 };
 
 }  // namespace lbm

@@ -22,6 +22,21 @@ namespace lbm {
 
 constexpr int BLOCK = 256;
 
+// Programmatic dependent launch. The passes of a step are launched with
+// programmatic stream serialisation: a pass's blocks may be scheduled while
+// the previous pass drains its last wave, and each waits
+// (griddepcontrol.wait: the previous grid complete, its writes visible)
+// before it touches global memory. A pass lets its successor launch once
+// all its own blocks have started (launch_dependents), so waiting blocks
+// never take the place of a block that has yet to start: no pass waits on
+// one that cannot finish. Launched without the attribute (the adjoint's
+// recomputation, the timed per-pass launches) both instructions do
+// nothing.
+__device__ __forceinline__ void pass_entry() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // Blocks per SM, measured on the 256^3 rock: the gather passes are bound by
 // load latency. The stream pass runs 6 blocks of 256 threads (40 registers:
 // 0.205 against 0.223 ms at 7 blocks and 32 registers, with the pull's
@@ -33,36 +48,42 @@ constexpr int BLOCK = 256;
 // keeps 3 blocks (it would spill at 64 registers).
 template <int Q, int ST>
 __global__ void __launch_bounds__(BLOCK, 6) k_stream(Dom d) {
+  pass_entry();
   const int k = blockIdx.x * BLOCK + threadIdx.x;
   if (k < d.NF) stream_node<Q, ST, false>(d, k);
 }
 
 template <int Q, int ST>
 __global__ void __launch_bounds__(BLOCK) k_zh_fix(Dom d) {
+  pass_entry();
   const int j = blockIdx.x * BLOCK + threadIdx.x;
   if (j < d.n_zh) zh_fix_node<Q, ST, false>(d, j);
 }
 
 template <int Q>
 __global__ void __launch_bounds__(BLOCK) k_phi_solid(Dom d) {
+  pass_entry();
   const int j = blockIdx.x * BLOCK + threadIdx.x;
   if (j < d.NS) phi_solid_node<Q, false>(d, j);
 }
 
 template <int Q>
 __global__ void __launch_bounds__(BLOCK, 8) k_gradient(Dom d) {
+  pass_entry();
   const int k = blockIdx.x * BLOCK + threadIdx.x;
   if (k < d.NF) gradient_node<Q, false>(d, k);
 }
 
 template <int Q>
 __global__ void __launch_bounds__(BLOCK) k_nc_solid(Dom d) {
+  pass_entry();
   const int j = blockIdx.x * BLOCK + threadIdx.x;
   if (j < d.NS) nc_solid_node<Q, false>(d, j);
 }
 
 template <int Q>
 __global__ void __launch_bounds__(BLOCK, 8) k_curvature(Dom d) {
+  pass_entry();
   const int k = blockIdx.x * BLOCK + threadIdx.x;
   if (k < d.NF) curvature_node<Q, false>(d, k);
 }
@@ -70,6 +91,7 @@ __global__ void __launch_bounds__(BLOCK, 8) k_curvature(Dom d) {
 // MRT: the collision compiled for the single rate (0) or the MRT rates (1)
 template <int Q, int ST, bool MACROS, int MRT>
 __global__ void __launch_bounds__(BLOCK, MRT ? 3 : 4) k_collide(Dom d) {
+  pass_entry();
   const int k = blockIdx.x * BLOCK + threadIdx.x;
   if (k < d.NF) collide_node<Q, ST, MACROS, false, MRT, true>(d, k);
 }
@@ -82,6 +104,23 @@ struct PassRange {
   ~PassRange() { nvtxRangePop(); }
 };
 
+// Launch of one pass: programmatic serialisation on the stream, unless the
+// per-pass events sit between the launches.
+static void launch_pass(void (*kern)(Dom), unsigned grid, cudaStream_t s,
+                        const Dom &d, bool pdl) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(BLOCK);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, kern, d);
+}
+
 template <int Q, int ST>
 static void launch_step_t(const Dom &d, cudaStream_t s, bool macros,
                           cudaEvent_t *ev) {
@@ -89,45 +128,46 @@ static void launch_step_t(const Dom &d, cudaStream_t s, bool macros,
   const unsigned g = (unsigned)((d.NF + BLOCK - 1) / BLOCK);
   const unsigned gs = (unsigned)((d.NS + BLOCK - 1) / BLOCK);
   const unsigned gz = (unsigned)((d.n_zh + BLOCK - 1) / BLOCK);
+  const bool pdl = ev == nullptr;
   if (ev) cudaEventRecord(ev[0], s);
   {
     PassRange r("stream (Eq. 1, 7-9)");
-    k_stream<Q, ST><<<g, BLOCK, 0, s>>>(d);
+    launch_pass(k_stream<Q, ST>, g, s, d, pdl);
   }
   if (ev) cudaEventRecord(ev[1], s);
   if (d.n_zh > 0) {
     PassRange r("Zou-He planes (App. B)");
-    k_zh_fix<Q, ST><<<gz, BLOCK, 0, s>>>(d);
+    launch_pass(k_zh_fix<Q, ST>, gz, s, d, pdl);
   }
   if (ev) cudaEventRecord(ev[2], s);
   if (d.NS > 0) {
     PassRange r("phi at solid boundary (Eq. 34)");
-    k_phi_solid<Q><<<gs, BLOCK, 0, s>>>(d);
+    launch_pass(k_phi_solid<Q>, gs, s, d, pdl);
   }
   if (ev) cudaEventRecord(ev[3], s);
   {
     PassRange r("gradient, wetting (Eq. 6, 27-33)");
-    k_gradient<Q><<<g, BLOCK, 0, s>>>(d);
+    launch_pass(k_gradient<Q>, g, s, d, pdl);
   }
   if (ev) cudaEventRecord(ev[4], s);
   if (d.NS > 0) {
     PassRange r("n_c at solid boundary (Eq. 35)");
-    k_nc_solid<Q><<<gs, BLOCK, 0, s>>>(d);
+    launch_pass(k_nc_solid<Q>, gs, s, d, pdl);
   }
   if (ev) cudaEventRecord(ev[5], s);
   const bool mrt = Q == 19 && d.c.mrt;
   {
     PassRange r("curvature (Eq. 12)");
-    k_curvature<Q><<<g, BLOCK, 0, s>>>(d);
+    launch_pass(k_curvature<Q>, g, s, d, pdl);
   }
   if (ev) cudaEventRecord(ev[6], s);
   PassRange r("force, collision, recolouring (Eq. 5, 2, 20-21)");
   if (macros) {
-    if (mrt) k_collide<Q, ST, true, 1><<<g, BLOCK, 0, s>>>(d);
-    else k_collide<Q, ST, true, 0><<<g, BLOCK, 0, s>>>(d);
+    launch_pass(mrt ? k_collide<Q, ST, true, 1> : k_collide<Q, ST, true, 0>, g, s,
+                d, pdl);
   } else {
-    if (mrt) k_collide<Q, ST, false, 1><<<g, BLOCK, 0, s>>>(d);
-    else k_collide<Q, ST, false, 0><<<g, BLOCK, 0, s>>>(d);
+    launch_pass(mrt ? k_collide<Q, ST, false, 1> : k_collide<Q, ST, false, 0>,
+                g, s, d, pdl);
   }
   if (ev) cudaEventRecord(ev[7], s);
 }

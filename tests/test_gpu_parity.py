@@ -251,9 +251,14 @@ def test_mass_conservation_gpu(torch):
 
 
 def test_step_timed_equals_step(torch):
-    """lbm_step_timed runs the same kernels as lbm_step (events only): the
-    states after 5 steps are bit-identical, and every kernel that runs on
-    the Type-I pack (all seven) reports a positive time."""
+    """lbm_step_timed runs the same kernels as lbm_step, with events
+    between the passes instead of programmatic dependent launches (where a
+    pass's blocks start while its predecessor drains and wait for it on the
+    device): the states after 5 steps are bit-identical, on a case small
+    enough that every pass's blocks are resident at once (so each pass
+    really does wait on the device for the one before it), and every
+    kernel that runs on the Type-I pack (all seven) reports a positive
+    time."""
     from paper_2407_10914_gb300 import lbm
     case = CASES[2][1]  # porous_typeI_schemeI: Zou-He planes and solids
     a = gpu_session(torch, case)
