@@ -242,8 +242,8 @@ lbm_status lbm_counts(lbm_handle h, int64_t *n_nodes, int64_t *n_fluid,
  * its scratch is a fixed array of the library's own in device memory
  * (about 16 KB, present on every GPU that loads the library until exit).
  * The first call on a device looks up that array's address with the
- * device current; make it before any stream capture. Every call shares the
- * array; calls that overlap on the GPU race on it. Synchronises the stream.
+ * device current. Every call shares the array; calls that overlap on the
+ * GPU race on it. Synchronises the stream.
  * LBM_ERR_ARG for lattice not 9/19, null pointers, n_nodes outside
  * [1, LBM_NOALLOC_MAX_NODES], or a pops_dev that is not device (or
  * managed) memory of the current device; nothing is enqueued then. */

@@ -18,8 +18,7 @@
 // race on the array and may return wrong sums.
 //
 // The first call on a device looks up the device address of the scratch
-// array (cudaGetSymbolAddress) with that device current and caches it; make
-// that first call before any stream capture.
+// array (cudaGetSymbolAddress) with that device current and caches it.
 #include <cuda_runtime.h>
 
 #include <cstdint>
