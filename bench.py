@@ -531,7 +531,8 @@ def run_ours(args):
                 "tile_search_ms_per_step": tile_trials,
                 "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                 "l2": "inputs larger than L2 (two population buffers of "
-                      f"{2 * Q * bpp * case.n_nodes / 1e9:.2f} GB)",
+                      f"{Q * bpp * nf / 1e9:.2f} GB each over the fluid "
+                      "nodes, against 0.13 GB of L2)",
             },
             "roofline": {"bound": "hbm",
                          "kernel": "the whole step (" + ", ".join(
@@ -1095,12 +1096,40 @@ def run_adjoint(args, torch, lbm):
                 "long runs); the FP64 tangent-linear oracle checks the same "
                 "code to 1e-3 (tests/test_gpu_adjoint.py)",
     }
+    ref = stored_fd64(n, T)
+    if ref:
+        th_ref, g_ref = ref["dJ_dtheta_per_deg"]["0.5"], ref["dJ_dgx"]["0.1"]
+        ref["rel_diff_theta"] = abs(ad_th - th_ref) / abs(th_ref)
+        ref["rel_diff_gx"] = abs(float(dg[0]) - g_ref) / abs(g_ref)
+        out["fd_fp64_stored"] = ref
     if args.adjoint_fd64:
         out["fd_fp64_oracle"] = adjoint_fd64(case, T, args.adjoint_fd64)
     if args.adjoint_tlm64:
         out["tlm_fp64_oracle"] = adjoint_tlm64(case, T, run.freeze_sin,
                                                run.c_min)
     return out
+
+
+def stored_fd64(n: int, T: int):
+    """The FP64 oracle's central differences of the gradient workload
+    (tests/golden/adjoint_pack128_T2000_fd64.txt, written by
+    make_adjoint_fd64.py beside it), for the 128^3, T = 2000 case only:
+    {"J", "dJ_dtheta_per_deg": {h: value}, "dJ_dgx": {h: value}}."""
+    p = os.path.join(ROOT, "tests", "golden", "adjoint_pack128_T2000_fd64.txt")
+    if n != 128 or T != 2000 or not os.path.exists(p):
+        return None
+    out = {"dJ_dtheta_per_deg": {}, "dJ_dgx": {},
+           "source": "tests/golden/adjoint_pack128_T2000_fd64.txt"}
+    for line in open(p):
+        parts = line.split()
+        if len(parts) != 3 or line.startswith("#"):
+            continue
+        if parts[0] == "J":
+            out["J"] = float(parts[2])
+        elif parts[0] in ("dJ_dtheta_per_deg", "dJ_dgx"):
+            out[parts[0]][parts[1]] = float(parts[2])
+    ok = "0.5" in out["dJ_dtheta_per_deg"] and "0.1" in out["dJ_dgx"]
+    return out if ok else None
 
 
 def adjoint_tlm64(case, T: int, freeze_sin: float, c_min: float) -> dict:
