@@ -756,6 +756,10 @@ struct OracleT {
   // (for tests; C, n_c and kappa are overwritten in that order).
   void gradient_only() { colour_gradient(); }
   void curvature_only() { curvature_force(); }
+  // Collision and recolouring, Eqs. (2) and (20)-(21), on the current
+  // streamed populations, colour densities, phase field, n_c and F (for
+  // tests).
+  void collide_recolour_only() { collide_recolour(); }
 
   // Single-node collision: Eq. (2) with one rate S for every non-conserved
   // moment and rate 0 for the conserved ones (rho, j), i.e. the relaxation
@@ -1119,6 +1123,32 @@ void orc_stencils(void *h, const double *phi_in, const double *nc_in,
   std::memcpy(o->nc.data(), nc_in, sizeof(double) * 3 * N);
   o->curvature_only();
   std::memcpy(kappa_out, o->kappa.data(), sizeof(double) * N);
+}
+
+// Test hook: collision and recolouring alone on a prescribed node state.
+// ft_in (2QN) holds the streamed populations f^r, f^b (only their sum
+// f^t enters the collision); rho_r, rho_b (N) the colour densities; phi
+// (N) the phase field (it sets the relaxation rate, Eq. 14); nc_in and
+// F_in (3N) the interface normal and the force density. f_out (2QN)
+// receives the post-recolouring populations f^r', f^b' of Eqs. (20)-(21).
+// The stored state is not changed apart from these inputs.
+void orc_collide_recolour(void *h, const double *ft_in, const double *rho_r,
+                          const double *rho_b, const double *phi_in,
+                          const double *nc_in, const double *F_in,
+                          double *f_out) {
+  Oracle *o = static_cast<Oracle *>(h);
+  const long N = o->N;
+  const long QN = (long)o->L.Q * N;
+  std::vector<double> keep(o->f);
+  std::memcpy(o->ftmp.data(), ft_in, sizeof(double) * 2 * QN);
+  std::memcpy(o->rho_r.data(), rho_r, sizeof(double) * N);
+  std::memcpy(o->rho_b.data(), rho_b, sizeof(double) * N);
+  std::memcpy(o->phi.data(), phi_in, sizeof(double) * N);
+  std::memcpy(o->nc.data(), nc_in, sizeof(double) * 3 * N);
+  std::memcpy(o->F.data(), F_in, sizeof(double) * 3 * N);
+  o->collide_recolour_only();
+  std::memcpy(f_out, o->f.data(), sizeof(double) * 2 * QN);
+  o->f.swap(keep);
 }
 
 // Classes (0 solid, 1 solid-boundary, 2 fluid, 3 fluid-boundary), the

@@ -72,6 +72,7 @@ def lib():
         L.orc_stream_only.argtypes = [C.c_void_p, C.c_void_p]
         L.orc_extrapolate.argtypes = [C.c_void_p] + [C.c_void_p] * 4
         L.orc_stencils.argtypes = [C.c_void_p] + [C.c_void_p] * 5
+        L.orc_collide_recolour.argtypes = [C.c_void_p] + [C.c_void_p] * 7
         L.orc_geometry.argtypes = [C.c_void_p] + [C.c_void_p] * 3
         L.orc_fields.argtypes = [C.c_void_p] + [C.c_void_p] * 6
         L.orc_reduce.restype = C.c_double
@@ -268,6 +269,19 @@ class Oracle:
         lib().orc_stencils(self._h, _ptr(pi), _ptr(ni), _ptr(Co), _ptr(no),
                            _ptr(ko))
         return Co, no, ko
+
+    def collide_recolour(self, ft, rho_r, rho_b, phi, nc, F):
+        """Eq. (2) and Eqs. (20)-(21) alone on a prescribed state: ft
+        (2, Q, nz, ny, nx) the streamed populations, rho_r, rho_b and phi
+        (nz, ny, nx), nc and F (3, nz, ny, nx). Returns the post-recolouring
+        populations (2, Q, nz, ny, nx); the stored populations are not
+        changed."""
+        q = ft.shape[1]
+        a = [np.ascontiguousarray(x, np.float64)
+             for x in (ft, rho_r, rho_b, phi, nc, F)]
+        out = np.zeros((2, q) + self.shape)
+        lib().orc_collide_recolour(self._h, *[_ptr(x) for x in a], _ptr(out))
+        return out
 
     def geometry(self):
         cls = np.zeros(self.shape, np.uint8)
