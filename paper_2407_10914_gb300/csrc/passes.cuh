@@ -253,6 +253,13 @@ __device__ __forceinline__ void nc_solid_node(const Dom &d, int j) {
 // neighbours clamped); returns kappa and the node's (n_c, |C|).
 template <int Q, bool COH>
 __device__ __forceinline__ float curvature(const Dom &d, int k, float4 &c4) {
+  // kappa enters the step only through F = 1/2 gamma kappa |C| n_c (Eq. 5).
+  // A node with no interface (|C| <= EPS_C) stores (n_c, |C|) = 0, so its
+  // surface force is zero whatever kappa is: the stencil is skipped there
+  // and kappa = 0 stored (the force, hence every population, is the same
+  // bit for bit).
+  c4 = ldv<COH>(d.ncf + k);
+  if (c4.w == 0.f) return 0.f;
   Curv<Q> cv;
   // n_c from the compact lists through the dense entry box: a dense copy of
   // n_c (as the phase field has) was measured slower, 0.293 against 0.265 ms
@@ -267,7 +274,6 @@ __device__ __forceinline__ float curvature(const Dom &d, int k, float4 &c4) {
     const float4 v = fl ? ldv<COH>(d.ncf + idx) : ldv<COH>(d.ncs + idx);
     cv.add(i, v.x, v.y, v.z);
   }
-  c4 = ldv<COH>(d.ncf + k);
   return cv.kappa(c4.x, c4.y, c4.z);
 }
 
@@ -275,7 +281,9 @@ __device__ __forceinline__ float curvature(const Dom &d, int k, float4 &c4) {
 template <int Q, bool COH>
 __device__ __forceinline__ void curvature_node(const Dom &d, int k) {
   float4 c4;
-  d.kap[k] = curvature<Q, COH>(d, k, c4);
+  const float kappa = curvature<Q, COH>(d, k, c4);
+  // stored only where the collision reads it back (a node with an interface)
+  if (c4.w != 0.f) d.kap[k] = kappa;
 }
 
 // Eq. (5) F = 1/2 gamma kappa C (C = |C| n_c) plus rho g (Eq. 36), the
@@ -291,8 +299,10 @@ __device__ __forceinline__ void collide_node(const Dom &d, int k) {
   float4 c4;
   float kappa;
   if (KAP) {
-    kappa = ldv<COH>(d.kap + k);
+    // kappa is stored only at nodes with an interface; elsewhere the
+    // surface force is zero (c4 = 0) and kappa = 0 as curvature() gives it
     c4 = ldv<COH>(d.ncf + k);
+    kappa = c4.w == 0.f ? 0.f : ldv<COH>(d.kap + k);
   } else {
     kappa = curvature<Q, COH>(d, k, c4);
   }
