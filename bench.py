@@ -93,10 +93,11 @@ def pass_bytes(Q: int, bpp: int, cells_per_node: float = 3.66) -> dict:
         # wall normal 16 B (fluid-boundary nodes, about 45 %: 7 B); write
         # (n_c, |C|) 16 B
         "gradient": 4 + 4 + 1 + 7 + 16,
+        # links + offsets, neighbour n_c 16 B; write 16 B
+        "nc_solid": 5 * 4 + 8 + 16 + 16,
         # the node's own (n_c, |C|) 16 B: the bytes every node needs (a
         # node with an interface adds its padded index 4 B, the entries, the
-        # neighbours' (n_c, |C|) 16 B, for a solid-boundary neighbour the
-        # links and n_c of Eq. 35, and the curvature write 4 B; a node
+        # neighbours' (n_c, |C|) 16 B and the curvature write 4 B; a node
         # without one stops there, its surface force being zero)
         "curvature": 16,
         # (n_c, |C|) 16 B, f^t, (rho^r, rho^b), phase 4 B; writes f''
@@ -109,7 +110,7 @@ def pass_bytes(Q: int, bpp: int, cells_per_node: float = 3.66) -> dict:
 # the kernel of each pass (names as ncu lists them)
 PASS_KERNEL = {"stream": "k_stream", "zh_fix": "k_zh_fix",
                "phi_solid": "k_phi_solid", "gradient": "k_gradient",
-               "curvature": "k_curvature",
+               "nc_solid": "k_nc_solid", "curvature": "k_curvature",
                "collide": "k_collide"}
 
 
@@ -448,7 +449,7 @@ def run_ours(args):
     pb = pass_bytes(Q, bpp, cells)
     n_zh = s.n_zou_he
     n_of = {"stream": nf, "zh_fix": n_zh, "phi_solid": n_sbnd, "gradient": nf,
-            "curvature": nf, "collide": nf}
+            "nc_solid": n_sbnd, "curvature": nf, "collide": nf}
     peak, peak_src = measured_peaks()
     passes_out = {}
     for p, t in pass_ms.items():
@@ -689,7 +690,7 @@ def run_tube(torch, lbm):
             "speed": U, "speed_eq47": U_ref,
             "speed_error_pct": round(100 * abs(U / U_ref - 1), 2),
             "r_eff": round(float(np.sqrt(8 * mu * L * U / dP)), 3),
-            "note": "launch-bound at this size (six kernels per step)"}
+            "note": "launch-bound at this size (seven kernels per step)"}
 
 
 def run_laplace(lbm):

@@ -168,14 +168,13 @@ lbm_status lbm_init_state(lbm_handle h, const float *phi0_dev, void *stream);
 lbm_status lbm_step(lbm_handle h, int nsteps, void *stream);
 
 /* Kernels of a step, in launch order, as lbm_step_timed() reports them. */
-#define LBM_N_PASSES 6
+#define LBM_N_PASSES 7
 /* Profiling form of lbm_step(): the same nsteps steps, with CUDA events
  * recorded on `stream` around each kernel of a step: [0] streaming and the
  * phase field (Eq. 1, Eqs. 7-9); [1] App. B on the Zou-He planes; [2]
- * Eq. (34); [3] colour gradient and wetting (Eqs. 6, 27-33); [4] curvature
- * (Eq. 12) at the nodes with an interface, with Eq. (35) for their
- * solid-boundary neighbours; [5] force, collision and recolouring (Eqs. 5,
- * 2, 20-21).
+ * Eq. (34); [3] colour gradient and wetting (Eqs. 6, 27-33); [4] Eq. (35);
+ * [5] curvature (Eq. 12); [6] force, collision and recolouring (Eqs. 5, 2,
+ * 20-21).
  * Adds the elapsed milliseconds of each, summed over the steps, to
  * pass_ms[0..LBM_N_PASSES-1] (host array) and synchronises the stream; a
  * kernel that does not run adds about 0. The results equal lbm_step()'s. */

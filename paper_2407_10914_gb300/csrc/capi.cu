@@ -364,7 +364,11 @@ lbm_status lbm_init_state(lbm_handle c, const float *phi0, void *stream) {
   if (!c || !phi0) return LBM_ERR_ARG;
   if (!c->params_set) return fail(c, LBM_ERR_STATE, "set params first");
   lbm::launch_init_state(c->Q, c->storage, c->d, phi0, (cudaStream_t)stream);
-  cudaError_t e = cudaGetLastError();
+  // the stored curvature is read (and discarded) at nodes without an
+  // interface too: keep it defined
+  cudaError_t e = cudaMemsetAsync(c->d.kap, 0, (size_t)c->d.NFp * sizeof(float),
+                                  (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "init_state");
   c->state_set = true;
   ++c->gen;

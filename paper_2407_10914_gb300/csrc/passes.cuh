@@ -256,13 +256,7 @@ __device__ __forceinline__ void nc_solid_node(const Dom &d, int j) {
 
 // Eq. (12) with d_b n_a by the Eq. (6) stencil on each component (off-box
 // neighbours clamped); returns kappa and the node's (n_c, |C|).
-// EQ35: the n_c of a solid-boundary neighbour is Eq. (35) evaluated here
-// from its links (the same helper and order as nc_solid_node, so the same
-// float), instead of read from the n_c that nc_solid_node stored. With the
-// stencil run only at interface nodes, this costs less than the Eq. 35 pass
-// over every solid-boundary node (0.053 against 0.030 + 0.043 ms on the
-// 256^3 rock).
-template <int Q, bool COH, bool EQ35 = false>
+template <int Q, bool COH>
 __device__ __forceinline__ float curvature(const Dom &d, int k, float4 &c4) {
   // kappa enters the step only through F = 1/2 gamma kappa |C| n_c (Eq. 5).
   // A node with no interface (|C| <= EPS_C) stores (n_c, |C|) = 0, so its
@@ -282,21 +276,17 @@ __device__ __forceinline__ float curvature(const Dom &d, int k, float4 &c4) {
     const uint32_t e = nb_entry<Q>(d, gp, i);
     const bool fl = entry_cls(e) & 2;
     const int idx = guard(d, entry_idx(e), fl ? d.NF : d.NS, GUARD_STENCIL);
-    float4 v;
-    if (EQ35)
-      v = fl ? ldv<COH>(d.ncf + idx) : eq35_at<Q, COH>(d, idx);
-    else
-      v = fl ? ldv<COH>(d.ncf + idx) : ldv<COH>(d.ncs + idx);
+    const float4 v = fl ? ldv<COH>(d.ncf + idx) : ldv<COH>(d.ncs + idx);
     cv.add(i, v.x, v.y, v.z);
   }
   return cv.kappa(c4.x, c4.y, c4.z);
 }
 
 // Eq. (12) at fluid node k, stored for the collision pass.
-template <int Q, bool COH, bool EQ35 = false>
+template <int Q, bool COH>
 __device__ __forceinline__ void curvature_node(const Dom &d, int k) {
   float4 c4;
-  const float kappa = curvature<Q, COH, EQ35>(d, k, c4);
+  const float kappa = curvature<Q, COH>(d, k, c4);
   // stored only where the collision reads it back (a node with an interface)
   if (c4.w != 0.f) d.kap[k] = kappa;
 }
@@ -315,9 +305,12 @@ __device__ __forceinline__ void collide_node(const Dom &d, int k) {
   float kappa;
   if (KAP) {
     // kappa is stored only at nodes with an interface; elsewhere the
-    // surface force is zero (c4 = 0) and kappa = 0 as curvature() gives it
+    // surface force is zero (c4 = 0) and kappa = 0 as curvature() gives it.
+    // Both loads are issued together and the select discards the stale
+    // value (a load that waited for c4 made the pass 4 % slower).
     c4 = ldv<COH>(d.ncf + k);
-    kappa = c4.w == 0.f ? 0.f : ldv<COH>(d.kap + k);
+    const float stored = ldv<COH>(d.kap + k);
+    kappa = c4.w == 0.f ? 0.f : stored;
   } else {
     kappa = curvature<Q, COH>(d, k, c4);
   }

@@ -1,19 +1,17 @@
-// The time step as six dependent kernels. Each needs the previous one's
-// values at lattice neighbours:
+// The time step as seven dependent passes. Each pass needs the previous
+// one's values at lattice neighbours:
 //   1 k_stream     (fluid)  pull of Eq. (1), Eqs. (7)-(9): stores f^t,
-//                  (rho^r, rho^b) and the phase field
-//   2 k_zh_fix     (Zou-He plane nodes) App. B
-//   3 k_phi_solid  (solid-boundary) Eq. (34)
-//   4 k_gradient   (fluid)  Eqs. (6), (27) and wetting, Eqs. (28)-(33)
-//   5 k_curvature  (fluid)  Eq. (12) at the nodes with an interface, with
-//                  Eq. (35) evaluated for their solid-boundary neighbours,
-//                  stored per node
+//                  (rho^r, rho^b) and the phase field; k_zh_fix then applies
+//                  App. B on the Zou-He planes
+//   2 k_phi_solid  (solid-boundary) Eq. (34)
+//   3 k_gradient   (fluid)  Eqs. (6), (27) and wetting, Eqs. (28)-(33)
+//   4 k_nc_solid   (solid-boundary) Eq. (35)
+//   5 k_curvature  (fluid)  Eq. (12), stored per node
 //   6 k_collide    (fluid)  Eqs. (5), (36); Eq. (2) single-rate or MRT on
 //                  the stored f^t; store f'' and (q, v), i.e. the
 //                  recoloured state of Eqs. (20)-(21)
 // One thread per node of the compact fluid (F) or solid-boundary (S) list;
-// the work of a node is in passes.cuh. k_nc_solid (Eq. 35 over every
-// solid-boundary node) serves the adjoint's recomputation of the fields.
+// the work of a node is in passes.cuh.
 #include <cuda_runtime.h>
 #include <nvtx3/nvToolsExt.h>
 
@@ -42,9 +40,10 @@ __device__ __forceinline__ void pass_entry() {
 // Blocks per SM, measured on the 256^3 rock: the gather passes are bound by
 // load latency. The stream pass runs 6 blocks of 256 threads (40 registers:
 // 0.205 against 0.223 ms at 7 blocks and 32 registers, with the pull's
-// unconditional (q, v) load); the gradient pass 8 blocks at 32 registers
-// (14 % faster than its unbounded 34 registers); the curvature pass 6
-// (below). The single-rate collision runs 4 blocks (64
+// unconditional (q, v) load); the gradient and curvature passes 8 blocks at
+// 32 registers (the gradient gains 14 % over its unbounded 34 registers; the
+// curvature, a gather of the neighbours' n_c split off the collision, is 7 %
+// slower at 6 blocks). The single-rate collision runs 4 blocks (64
 // registers; 3 and 5 blocks are 1 % and 11 % slower); the MRT collision
 // keeps 3 blocks (it would spill at 64 registers).
 template <int Q, int ST>
@@ -82,13 +81,11 @@ __global__ void __launch_bounds__(BLOCK) k_nc_solid(Dom d) {
   if (j < d.NS) nc_solid_node<Q, false>(d, j);
 }
 
-// 6 blocks per SM (40 registers, no spills): at 8 blocks the inline Eq. 35
-// spills 116 B for the same time.
 template <int Q>
-__global__ void __launch_bounds__(BLOCK, 6) k_curvature(Dom d) {
+__global__ void __launch_bounds__(BLOCK, 8) k_curvature(Dom d) {
   pass_entry();
   const int k = blockIdx.x * BLOCK + threadIdx.x;
-  if (k < d.NF) curvature_node<Q, false, true>(d, k);
+  if (k < d.NF) curvature_node<Q, false>(d, k);
 }
 
 // MRT: the collision compiled for the single rate (0) or the MRT rates (1)
@@ -153,12 +150,17 @@ static void launch_step_t(const Dom &d, cudaStream_t s, bool macros,
     launch_pass(k_gradient<Q>, g, s, d, pdl);
   }
   if (ev) cudaEventRecord(ev[4], s);
-  const bool mrt = Q == 19 && d.c.mrt;
-  {
-    PassRange r("curvature with Eq. 35 (Eq. 12)");
-    launch_pass(k_curvature<Q>, g, s, d, pdl);
+  if (d.NS > 0) {
+    PassRange r("n_c at solid boundary (Eq. 35)");
+    launch_pass(k_nc_solid<Q>, gs, s, d, pdl);
   }
   if (ev) cudaEventRecord(ev[5], s);
+  const bool mrt = Q == 19 && d.c.mrt;
+  {
+    PassRange r("curvature (Eq. 12)");
+    launch_pass(k_curvature<Q>, g, s, d, pdl);
+  }
+  if (ev) cudaEventRecord(ev[6], s);
   PassRange r("force, collision, recolouring (Eq. 5, 2, 20-21)");
   if (macros) {
     launch_pass(mrt ? k_collide<Q, ST, true, 1> : k_collide<Q, ST, true, 0>, g, s,
@@ -167,7 +169,7 @@ static void launch_step_t(const Dom &d, cudaStream_t s, bool macros,
     launch_pass(mrt ? k_collide<Q, ST, false, 1> : k_collide<Q, ST, false, 0>,
                 g, s, d, pdl);
   }
-  if (ev) cudaEventRecord(ev[6], s);
+  if (ev) cudaEventRecord(ev[7], s);
 }
 
 template <int Q, int ST>

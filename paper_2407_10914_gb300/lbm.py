@@ -267,8 +267,8 @@ def lbm_step(h, nsteps, stream):
     _check(load_library().lbm_step(h, int(nsteps), stream), h, "lbm_step")
 
 
-PASSES = ("stream", "zh_fix", "phi_solid", "gradient", "curvature",
-          "collide")
+PASSES = ("stream", "zh_fix", "phi_solid", "gradient", "nc_solid",
+          "curvature", "collide")
 
 
 def lbm_step_timed(h, nsteps, stream) -> dict:

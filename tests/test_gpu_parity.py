@@ -257,7 +257,7 @@ def test_step_timed_equals_step(torch):
     device): the states after 5 steps are bit-identical, on a case small
     enough that every pass's blocks are resident at once (so each pass
     really does wait on the device for the one before it), and every
-    kernel that runs on the Type-I pack (all six) reports a positive
+    kernel that runs on the Type-I pack (all seven) reports a positive
     time."""
     from paper_2407_10914_gb300 import lbm
     case = CASES[2][1]  # porous_typeI_schemeI: Zou-He planes and solids
@@ -279,7 +279,7 @@ def test_step_graph_equals_single_steps(torch):
     state equals that of n single steps bit for bit, for odd and even n,
     across both orientations of the state buffers, and after new
     parameters (the graph is recorded again)."""
-    case = CASES[2][1]  # Zou-He planes and solids: all six kernels
+    case = CASES[2][1]  # Zou-He planes and solids: all seven kernels
     a = gpu_session(torch, case)
     b = gpu_session(torch, case)
     for s in (a, b):
