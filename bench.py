@@ -107,6 +107,10 @@ def pass_bytes(Q: int, bpp: int, cells_per_node: float = 3.66) -> dict:
     }
 
 
+# GB300 HBM3e nominal bandwidth (the measured copy peak is the roofline's
+# denominator; this is reported beside it)
+NOMINAL_HBM_GBS = 7900.0
+
 # the kernel of each pass (names as ncu lists them)
 PASS_KERNEL = {"stream": "k_stream", "zh_fix": "k_zh_fix",
                "phi_solid": "k_phi_solid", "gradient": "k_gradient",
@@ -543,6 +547,11 @@ def run_ours(args):
                          "achieved": round(achieved, 1), "peak": peak,
                          "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": step_traffic, "peak_source": peak_src,
+                         "frac_of_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
+                         "nominal_gbs": NOMINAL_HBM_GBS,
+                         "dram_bytes_per_update": (
+                             None if step_traffic is None
+                             else round(step_traffic / nf, 1)),
                          "bytes_per_update": upd_bytes,
                          "algorithmic_bytes_per_step": step_alg,
                          "ms_per_step": round(step_ms, 5),
