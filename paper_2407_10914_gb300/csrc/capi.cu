@@ -45,7 +45,7 @@ long long count_solid(const uint8_t *solid, long long N) {
 // Byte offsets of every buffer inside the caller's workspace.
 struct Layout {
   size_t TA, TB, U, R, SA, SB, mf, ncf, kap, nw, fg, macro;  // F-space
-  size_t ms, ncs, sg, sgp, sflag, sdir;           // S-space
+  size_t ms, ncs, sg, sgp, sflag, sdir, smark;    // S-space
   size_t phib, fgp;                               // dense phase field
   size_t nbd, soff, slink, fflag, zh;             // neighbour lookup
   size_t map, cls, mask, fbase, sbase, cntf, cnts, g0, g1;
@@ -115,6 +115,7 @@ Layout make_layout(int Q, int nx, int ny, int nz, int storage, long long NF,
   L.sgp = take(nsp * 4);
   L.sflag = take(nsp);
   L.sdir = take(nsp * 4);
+  L.smark = take(nsp);
   L.fgp = take(nfp * 4);
   L.phib = take((size_t)(nx + 2) * (ny + 2) * (nz + 2) * 4);
   L.nbd = take((size_t)(nx + 2) * (ny + 2) * (nz + 2) * 4);
@@ -276,11 +277,13 @@ lbm_status lbm_init_geometry_tiled(lbm_handle *out, int lattice, int nx,
   d.sgp = (const int *)(base + L.sgp);
   d.sflag = (const uint8_t *)(base + L.sflag);
   d.sdir = (const uint32_t *)(base + L.sdir);
+  d.smark = (uint8_t *)(base + L.smark);
   d.px = nx + 2;
   d.py = ny + 2;
   d.err = (unsigned *)(c->counters + 3);  // zeroed with the counters at set-up
   cudaError_t e = cudaMemcpyAsync(c->mask, solid_host, (size_t)N,
                                   cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d.smark, 0, (size_t)(L.NS > 0 ? L.NS : 1), s);
   if (e == cudaSuccess) e = lbm::build_geometry(c, s);
   if (e != cudaSuccess) {
     delete c;

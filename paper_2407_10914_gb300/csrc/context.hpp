@@ -104,6 +104,10 @@ struct Dom {
   unsigned *err;        // error word of the bounds-checked build (guard())
   StepConst c;
   int tlx, tly, tlz;    // log2 of the tile extents (set-up kernels only)
+  // [NS] 1: a fluid neighbour with an interface reads this node's n_c in
+  // the curvature stencil; set by the step's gradient pass, cleared by its
+  // Eq. 35 pass (zero between steps)
+  uint8_t *smark;
 };
 
 }  // namespace lbm

@@ -215,8 +215,10 @@ __device__ __forceinline__ void phi_solid_node(const Dom &d, int j) {
 // s(x) in place of phi(x + e_i) (the same sum since sum_i w_i e_i = 0),
 // off-box neighbours clamped; at fluid-boundary nodes the wetting scheme
 // turns n_c, keeping |C|. Stored: (n_c, |C|), or zero where |C| <= EPS_C
-// (no interface).
-template <int Q, bool COH>
+// (no interface). MARK: a fluid-boundary node with an interface marks its
+// solid-boundary neighbours (smark), whose Eq. (35) n_c its curvature
+// stencil will read.
+template <int Q, bool COH, bool MARK = false>
 __device__ __forceinline__ void gradient_node(const Dom &d, int k) {
   // the neighbours' phase from the dense box at fixed offsets (the nodes the
   // dense entry box names: fluid, solid-boundary, or the halo cell of a
@@ -230,7 +232,18 @@ __device__ __forceinline__ void gradient_node(const Dom &d, int k) {
           ldv<COH>(d.phib + guard(d, gp + dense_off<Q>(d, i),
                                   d.px * d.py * (d.nz + 2), GUARD_STENCIL)),
           own_blue);
-  d.ncf[k] = normal_and_wetting(d.c, g, (__ldg(d.fflag + k) & 1u) != 0, d.nw + k);
+  const bool fbnd = (__ldg(d.fflag + k) & 1u) != 0;
+  const float4 c4 = normal_and_wetting(d.c, g, fbnd, d.nw + k);
+  d.ncf[k] = c4;
+  if (MARK && fbnd && c4.w != 0.f) {
+    // all entry loads issued together (one round trip)
+#pragma unroll
+    for (int i = 1; i < Q; ++i) {
+      const uint32_t e = nb_entry<Q>(d, gp, i);
+      if (entry_cls(e) == CLS_SOLID_BND)
+        d.smark[guard(d, entry_idx(e), d.NS, GUARD_STENCIL)] = 1;
+    }
+  }
 }
 
 // Eq. (35): n_c at solid-boundary node j = w-weighted mean of the fluid
@@ -252,6 +265,18 @@ __device__ __forceinline__ float4 eq35_at(const Dom &d, int j) {
 template <int Q, bool COH>
 __device__ __forceinline__ void nc_solid_node(const Dom &d, int j) {
   d.ncs[j] = eq35_at<Q, COH>(d, j);
+}
+
+// Eq. (35) only where the step's curvature stencil will read it: at the
+// solid-boundary nodes the gradient pass marked (the neighbours of
+// fluid-boundary nodes with an interface; the curvature runs at no other
+// node, and Eq. 35 of a node whose fluid neighbours all lack an interface
+// is zero). The mark is cleared for the next step.
+template <int Q>
+__device__ __forceinline__ void nc_solid_marked_node(const Dom &d, int j) {
+  if (!d.smark[j]) return;
+  d.smark[j] = 0;
+  d.ncs[j] = eq35_at<Q, false>(d, j);
 }
 
 // Eq. (12) with d_b n_a by the Eq. (6) stencil on each component (off-box

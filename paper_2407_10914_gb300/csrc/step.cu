@@ -67,11 +67,14 @@ __global__ void __launch_bounds__(BLOCK) k_phi_solid(Dom d) {
   if (j < d.NS) phi_solid_node<Q, false>(d, j);
 }
 
-template <int Q>
+// MARK: the step's form, which marks the solid-boundary nodes that its
+// Eq. 35 pass must compute (k_nc_solid_marked); the adjoint recomputes the
+// fields with the plain form and the full Eq. 35 pass.
+template <int Q, bool MARK>
 __global__ void __launch_bounds__(BLOCK, 8) k_gradient(Dom d) {
   pass_entry();
   const int k = blockIdx.x * BLOCK + threadIdx.x;
-  if (k < d.NF) gradient_node<Q, false>(d, k);
+  if (k < d.NF) gradient_node<Q, false, MARK>(d, k);
 }
 
 template <int Q>
@@ -79,6 +82,13 @@ __global__ void __launch_bounds__(BLOCK) k_nc_solid(Dom d) {
   pass_entry();
   const int j = blockIdx.x * BLOCK + threadIdx.x;
   if (j < d.NS) nc_solid_node<Q, false>(d, j);
+}
+
+template <int Q>
+__global__ void __launch_bounds__(BLOCK) k_nc_solid_marked(Dom d) {
+  pass_entry();
+  const int j = blockIdx.x * BLOCK + threadIdx.x;
+  if (j < d.NS) nc_solid_marked_node<Q>(d, j);
 }
 
 template <int Q>
@@ -147,12 +157,12 @@ static void launch_step_t(const Dom &d, cudaStream_t s, bool macros,
   if (ev) cudaEventRecord(ev[3], s);
   {
     PassRange r("gradient, wetting (Eq. 6, 27-33)");
-    launch_pass(k_gradient<Q>, g, s, d, pdl);
+    launch_pass(k_gradient<Q, true>, g, s, d, pdl);
   }
   if (ev) cudaEventRecord(ev[4], s);
   if (d.NS > 0) {
     PassRange r("n_c at solid boundary (Eq. 35)");
-    launch_pass(k_nc_solid<Q>, gs, s, d, pdl);
+    launch_pass(k_nc_solid_marked<Q>, gs, s, d, pdl);
   }
   if (ev) cudaEventRecord(ev[5], s);
   const bool mrt = Q == 19 && d.c.mrt;
@@ -180,7 +190,7 @@ static void launch_fields_t(const Dom &d, cudaStream_t s) {
   k_stream<Q, ST><<<g, BLOCK, 0, s>>>(d);
   if (d.n_zh > 0) k_zh_fix<Q, ST><<<gz, BLOCK, 0, s>>>(d);
   if (d.NS > 0) k_phi_solid<Q><<<gs, BLOCK, 0, s>>>(d);
-  k_gradient<Q><<<g, BLOCK, 0, s>>>(d);
+  k_gradient<Q, false><<<g, BLOCK, 0, s>>>(d);
   if (d.NS > 0) k_nc_solid<Q><<<gs, BLOCK, 0, s>>>(d);
 }
 
