@@ -93,8 +93,10 @@ def pass_bytes(Q: int, bpp: int, cells_per_node: float = 3.66) -> dict:
         # wall normal 16 B (fluid-boundary nodes, about 45 %: 7 B); write
         # (n_c, |C|) 16 B
         "gradient": 4 + 4 + 1 + 7 + 16,
-        # links + offsets, neighbour n_c 16 B; write 16 B
-        "nc_solid": 5 * 4 + 8 + 16 + 16,
+        # the mark 1 B: the bytes every solid-boundary node needs (a node
+        # marked by the gradient pass adds its links + offsets, the
+        # neighbours' n_c 16 B and the write of 16 B)
+        "nc_solid": 1,
         # the node's own (n_c, |C|) 16 B: the bytes every node needs (a
         # node with an interface adds its padded index 4 B, the entries, the
         # neighbours' (n_c, |C|) 16 B and the curvature write 4 B; a node
@@ -114,7 +116,7 @@ NOMINAL_HBM_GBS = 7900.0
 # the kernel of each pass (names as ncu lists them)
 PASS_KERNEL = {"stream": "k_stream", "zh_fix": "k_zh_fix",
                "phi_solid": "k_phi_solid", "gradient": "k_gradient",
-               "nc_solid": "k_nc_solid", "curvature": "k_curvature",
+               "nc_solid": "k_nc_solid_marked", "curvature": "k_curvature",
                "collide": "k_collide"}
 
 
