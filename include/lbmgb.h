@@ -194,6 +194,21 @@ lbm_status lbm_macros(lbm_handle h, float *rho, float *phi, float *u,
  * sum is not finite. */
 lbm_status lbm_reduce(lbm_handle h, int kind, double *out_host, void *stream);
 
+/* lbm_reduce() without the wait, for a quantity read back every step
+ * while the GPU runs on: enqueues the same FP64 reduction on `stream` and
+ * the copy of its four raw sums to raw4_host[0..3] (host memory owned by
+ * the caller; page-locked for the copy to overlap the following work), and
+ * returns. Once the stream has passed that point, lbm_reduce_value() turns
+ * the raw sums into the quantity lbm_reduce() would have returned. The
+ * reduction's device scratch belongs to the handle, so reductions of one
+ * handle must stay on one stream. */
+lbm_status lbm_reduce_async(lbm_handle h, int kind, double *raw4_host,
+                            void *stream);
+/* The quantity of `kind` from four raw sums of lbm_reduce_async() (host
+ * arithmetic only). LBM_ERR_NONFINITE if it is not finite. */
+lbm_status lbm_reduce_value(lbm_handle h, int kind, const double *raw4_host,
+                            double *out_host);
+
 /* The stored (post-recolouring) populations as float32 [2][Q][N] in the
  * caller's device buffer (solid nodes 0), and back. */
 lbm_status lbm_get_populations(lbm_handle h, float *dst_dev, void *stream);

@@ -480,17 +480,33 @@ lbm_status lbm_macros(lbm_handle c, float *rho, float *phi, float *u,
   return LBM_OK;
 }
 
-lbm_status lbm_reduce(lbm_handle c, int kind, double *out, void *stream) {
-  if (!c || !out || kind < 0 || kind > LBM_CA_B) return LBM_ERR_ARG;
+lbm_status lbm_reduce_async(lbm_handle c, int kind, double *raw4,
+                            void *stream) {
+  if (!c || !raw4 || kind < 0 || kind > LBM_CA_B) return LBM_ERR_ARG;
   if (!c->state_set) return fail(c, LBM_ERR_STATE, "init the state first");
   cudaStream_t s = (cudaStream_t)stream;
-  double *dev_out = c->red_out;
   lbm::launch_reduce(c->Q, c->storage, c->d, kind, c->red, c->red_slots,
-                     dev_out, s);
-  double h[4];
-  cudaError_t e = cudaMemcpyAsync(h, dev_out, sizeof(h), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+                     c->red_out, s);
+  cudaError_t e = cudaMemcpyAsync(raw4, c->red_out, 4 * sizeof(double),
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(c, e, "reduce");
+  return LBM_OK;
+}
+
+lbm_status lbm_reduce(lbm_handle c, int kind, double *out, void *stream) {
+  if (!c || !out || kind < 0 || kind > LBM_CA_B) return LBM_ERR_ARG;
+  double h[4];
+  const lbm_status st = lbm_reduce_async(c, kind, h, stream);
+  if (st != LBM_OK) return st;
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reduce");
+  return lbm_reduce_value(c, kind, h, out);
+}
+
+lbm_status lbm_reduce_value(lbm_handle c, int kind, const double *h,
+                            double *out) {
+  if (!c || !h || !out || kind < 0 || kind > LBM_CA_B) return LBM_ERR_ARG;
   double v = 0.0;
   const double nf = (double)c->n_fluid;
   switch (kind) {

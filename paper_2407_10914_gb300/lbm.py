@@ -31,7 +31,7 @@ EXPORTS = ("lbm_workspace_bytes", "lbm_init_geometry",
            "lbm_workspace_bytes_tiled", "lbm_init_geometry_tiled",
            "lbm_set_params",
            "lbm_init_state", "lbm_step", "lbm_step_timed", "lbm_macros",
-           "lbm_reduce",
+           "lbm_reduce", "lbm_reduce_async", "lbm_reduce_value",
            "lbm_get_populations", "lbm_set_populations", "lbm_swap_inlet",
            "lbm_debug_flags",
            "lbm_get_geometry",
@@ -101,6 +101,10 @@ def load_library(path: str = LIB_PATH):
     L.lbm_macros.argtypes = [vp, vp, vp, vp, vp]
     L.lbm_reduce.restype = C.c_int
     L.lbm_reduce.argtypes = [vp, C.c_int, C.POINTER(C.c_double), vp]
+    L.lbm_reduce_async.restype = C.c_int
+    L.lbm_reduce_async.argtypes = [vp, C.c_int, vp, vp]
+    L.lbm_reduce_value.restype = C.c_int
+    L.lbm_reduce_value.argtypes = [vp, C.c_int, vp, C.POINTER(C.c_double)]
     L.lbm_get_populations.restype = C.c_int
     L.lbm_get_populations.argtypes = [vp, vp, vp]
     L.lbm_set_populations.restype = C.c_int
@@ -287,6 +291,21 @@ def lbm_reduce(h, kind, stream) -> float:
     out = C.c_double()
     _check(load_library().lbm_reduce(h, int(kind), C.byref(out), stream), h,
            "lbm_reduce")
+    return out.value
+
+
+def lbm_reduce_async(h, kind, raw4_ptr, stream):
+    """Enqueue a reduction and the copy of its four raw FP64 sums to the host
+    address raw4_ptr (an int; page-locked memory for the copy to overlap)."""
+    _check(load_library().lbm_reduce_async(h, int(kind), C.c_void_p(raw4_ptr),
+                                           stream), h, "lbm_reduce_async")
+
+
+def lbm_reduce_value(h, kind, raw4_ptr) -> float:
+    """The quantity of `kind` from four raw sums at host address raw4_ptr."""
+    out = C.c_double()
+    _check(load_library().lbm_reduce_value(h, int(kind), C.c_void_p(raw4_ptr),
+                                           C.byref(out)), h, "lbm_reduce_value")
     return out.value
 
 
