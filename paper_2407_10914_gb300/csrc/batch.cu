@@ -184,9 +184,12 @@ __device__ bool wait_count(const unsigned long long *cnt,
 }
 
 // All passes in one kernel: the registers of the heaviest (the collision
-// with the curvature), bounded to 3 resident blocks of 256 threads.
+// with the curvature), bounded to 4 resident blocks of 256 threads (64
+// registers, 204 B of spills: 8.75-9.04 ms per step on the 96 drops,
+// against 9.61-9.92 at 3 blocks and 80 registers and 11.35-11.58 at 2;
+// 5 blocks would spill 848 B).
 template <int Q, int ST, int BT>
-__global__ void __launch_bounds__(BT, BT == 256 ? 3 : 6) k_batch_persistent(
+__global__ void __launch_bounds__(BT, BT == 256 ? 4 : 8) k_batch_persistent(
     const Dom *__restrict__ table, Plan pl, BatchCtl *ctl,
     unsigned long long *done, int nsteps, unsigned long long limit_ns) {
   __shared__ __align__(16) Dom sd;
