@@ -21,7 +21,8 @@
 //    end whatever the grid size. Each wait is bounded by the GPU's global
 //    timer: past the limit the block sets the error flag and every block
 //    leaves; lbm_batch_status() reports LBM_ERR_TIMEOUT. Values written in
-//    the launch are read from L2 (passes.cuh, COH = true).
+//    the launch are read with plain coherent loads, after the item's
+//    acquire, fence and block barrier (passes.cuh, COH = true).
 //
 // Both modes are recorded once per (nsteps, configuration) into a CUDA
 // graph on a stream the batch owns and replayed on the caller's stream.

@@ -152,12 +152,14 @@ __device__ __forceinline__ float weight_of(int p) {
 // Loads of values that change from step to step. A kernel that never
 // writes what it reads takes them through the read-only path (__ldg). The
 // persistent batch kernel runs several passes in one launch, so it reads
-// values that other blocks wrote earlier in the same launch; it loads them
-// from L2, bypassing L1 (__ldcg): COH = true.
+// values that other blocks wrote earlier in the same launch: COH = true,
+// plain coherent loads (ld.global.ca), never the read-only path. Each of
+// its work items starts after an acquire (and a fence) by one thread and a
+// block barrier, which order these loads after the writes they depend on.
 template <bool COH, class T>
 __device__ __forceinline__ T ldv(const T *p) {
   if constexpr (COH)
-    return __ldcg(p);
+    return __ldca(p);
   else
     return __ldg(p);
 }
