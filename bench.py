@@ -473,7 +473,7 @@ def run_ours(args):
                          "dram_GBps": (round(tr / (t1 * 1e-3) / 1e9, 1)
                                        if tr else None)}
     dom = max(passes_out, key=lambda p: passes_out[p]["ms"])
-    # the step against the survey's 308 B per fluid-node update (38 pops
+    # the step against the algorithmic 308 B per fluid-node update (38 pops
     # read and written, 4 B link mask)
     upd_bytes = 2 * 2 * Q * bpp + 4
     step_alg = upd_bytes * nf
