@@ -148,7 +148,7 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the gradient (adjoint) object")
     ap.add_argument("--repeats", type=int, default=5,
-                    help="repeats of the timed region (median reported)")
+                    help="repeats of the timed region, at least (more when a repeat is short: about 0.5 s in all; median reported)")
     ap.add_argument("--oracle-sample", nargs=3, type=int, default=None,
                     metavar=("PLANES", "STEPS", "SIZE"),
                     help=argparse.SUPPRESS)
@@ -422,14 +422,25 @@ def run_ours(args):
     n_sbnd = s.counts[2]
     stream = torch.cuda.current_stream()
 
-    s.step(args.warmup)
     torch.cuda.synchronize()
+    w0 = torch.cuda.Event(enable_timing=True)
+    w1 = torch.cuda.Event(enable_timing=True)
+    w0.record(stream)
+    s.step(args.warmup)
+    w1.record(stream)
+    torch.cuda.synchronize()
+    # repeats: at least --repeats, and enough for about 0.5 s of timed work
+    # (so that the clock sampler sees the timed region), at most 200
+    est_ms = w0.elapsed_time(w1) / max(1, args.warmup)
+    n_rep = max(1, args.repeats)
+    if est_ms > 0:
+        n_rep = min(200, max(n_rep, int(math.ceil(500.0 / (est_ms * args.steps)))))
     clocks = ClockSampler(local)
     # the timed region, repeated: each repeat is `steps` steps between a
     # barrier and CUDA events on the launching stream; the population
-    # buffers (2 x 0.42 GB on the rock) exceed the 129 MB L2 every step
+    # buffers (2 x 0.35 GB on the rock) exceed the 129 MB L2 every step
     rep_ms = []
-    for _ in range(max(1, args.repeats)):
+    for _ in range(n_rep):
         barrier(ws)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
