@@ -29,3 +29,34 @@ def test_cache_round_trip(tmp_path):
     assert d["k1"]["config"] == [1, 256, 4] and d["k2"]["ms_per_step"] == 3.0
     open(p, "w").write("not json")
     assert A.load_cache(p) == {}
+
+
+def test_tile_class_and_cached_tile(tmp_path):
+    """The tile search's key and its cache: a cached shape among the
+    candidates is returned without building or timing anything; one that
+    is not a candidate is ignored."""
+    key = A.tile_class(19, "fp32", (256, 256, 256), [(4588847, 2561392)])
+    assert key == "tile-Q19-fp32-256x256x256-n1-F4600000-S2600000"
+    p = str(tmp_path / "t.json")
+    A.store_cache(p, key, {"tile": [64, 8, 8], "ms_per_step": 0.5,
+                           "trials": {"64x8x8": 0.5}})
+
+    def make(tile):
+        raise AssertionError("a cached shape needs no trial")
+
+    r = A.tune_tile(make, 19, key=key, cache_path=p)
+    assert r["cached"] and r["tile"] == (64, 8, 8)
+    A.store_cache(p, key, {"tile": [16, 4, 4], "ms_per_step": 0.5})
+    built = []
+
+    def make2(tile):
+        built.append(tile)
+        raise RuntimeError("stop")
+
+    try:
+        A.tune_tile(make2, 19, key=key, cache_path=p)
+    except RuntimeError:
+        pass
+    assert built == [A.TILE_CANDIDATES[19][0]]
+    assert all(t[0] >= 32 for q in A.TILE_CANDIDATES
+               for t in A.TILE_CANDIDATES[q])
