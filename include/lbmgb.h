@@ -128,7 +128,8 @@ lbm_status lbm_init_geometry(lbm_handle *out, int lattice, int nx, int ny,
                              void *dev_workspace, size_t ws_bytes,
                              void *stream);
 
-/* The two calls above with a chosen tile shape. The fluid nodes are
+/* The two calls above with a chosen tile shape (a memory-layout choice;
+ * the paper has no counterpart). The fluid nodes are
  * numbered tile by tile, tiles of tile[0] x tile[1] x tile[2] nodes (x, y,
  * z; host array of 3 ints). NULL gives the default the calls above use:
  * 32 x 8 x 8 (D3Q19), 64 x 32 x 1 (D2Q9). Each extent a power of two,
@@ -194,7 +195,8 @@ lbm_status lbm_macros(lbm_handle h, float *rho, float *phi, float *u,
  * sum is not finite. */
 lbm_status lbm_reduce(lbm_handle h, int kind, double *out_host, void *stream);
 
-/* lbm_reduce() without the wait, for a quantity read back every step
+/* lbm_reduce() without the wait (the same diagnostics; how they reach the
+ * host has no counterpart in the paper), for a quantity read back every step
  * while the GPU runs on: enqueues the same FP64 reduction on `stream` and
  * the copy of its four raw sums to raw4_host[0..3] (host memory owned by
  * the caller; page-locked for the copy to overlap the following work), and
