@@ -96,23 +96,29 @@ __global__ void __launch_bounds__(ABLOCK) k_adj_collide(Dom d, Adj a) {
   float lg[3] = {0.f, 0.f, 0.f};
   if (live) {
     using IO = TIO<Q, LBM_STORAGE_FP32>;
-    // forward values of the step
+    // forward values of the step. The curvature stencil only where the
+    // node has an interface: elsewhere |C| = 0, so kappa enters neither F
+    // nor, through lambda kappa = gamma |C| lambda_hk / 2, any neighbour;
+    // its lambda |C| is read only at nodes with an interface
+    // (k_adj_gradient)
+    const float4 c4 = d.ncf[k];
     float dn[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    if (c4.w != 0.f) {
 #pragma unroll
-    for (int i = 1; i < Q; ++i) {
-      const uint32_t e = nb_f<Q>(d, i, k);
-      const int idx = entry_idx(e);
-      const float4 v = (entry_cls(e) & 2) ? d.ncf[idx] : d.ncs[idx];
-      const float w3 = 3.f * Lattice<Q>::w(i);
+      for (int i = 1; i < Q; ++i) {
+        const uint32_t e = nb_f<Q>(d, i, k);
+        const int idx = entry_idx(e);
+        const float4 v = (entry_cls(e) & 2) ? d.ncf[idx] : d.ncs[idx];
+        const float w3 = 3.f * Lattice<Q>::w(i);
 #pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const float eb = (float)Lattice<Q>::e(i, b);
-        dn[0][b] += w3 * eb * v.x;
-        dn[1][b] += w3 * eb * v.y;
-        dn[2][b] += w3 * eb * v.z;
+        for (int b = 0; b < 3; ++b) {
+          const float eb = (float)Lattice<Q>::e(i, b);
+          dn[0][b] += w3 * eb * v.x;
+          dn[1][b] += w3 * eb * v.y;
+          dn[2][b] += w3 * eb * v.z;
+        }
       }
     }
-    const float4 c4 = d.ncf[k];
     const float n[3] = {c4.x, c4.y, c4.z};
     const float Cm = c4.w;
     float kappa = 0.f;
