@@ -272,6 +272,8 @@ __global__ void __launch_bounds__(ABLOCK) k_adj_nc_solid(Dom d, Adj a) {
   const int j = blockIdx.x * ABLOCK + threadIdx.x;
   if (j >= d.NS) return;
   const float4 l = a.lns[j];
+  // nothing read this node's n_c (no fluid neighbour with an interface)
+  if (l.x == 0.f && l.y == 0.f && l.z == 0.f) return;
   const int e = d.soff[j + 1];
   float W = 0.f;
   for (int p = d.soff[j]; p < e; ++p) W += link_w<Q>(d.slink[p]);
@@ -330,7 +332,9 @@ template <int Q>
 __global__ void __launch_bounds__(ABLOCK) k_adj_gradient(Dom d, Adj a) {
   const int k = blockIdx.x * ABLOCK + threadIdx.x;
   float lth = 0.f;
-  if (k < d.NF) {
+  // where the forward step found no interface (stored |C| = 0) n_c was held
+  // at zero, so nothing flows back through the stencil
+  if (k < d.NF && d.ncf[k].w != 0.f) {
     const bool own_blue = m_blue(d.mf[k]);
     float G[3] = {0.f, 0.f, 0.f};
 #pragma unroll
