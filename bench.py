@@ -575,7 +575,10 @@ def run_ours(args):
                                          "ncu dram__bytes_read.sum + "
                                          "dram__bytes_write.sum per launch "
                                          "(profiles/dram_traffic.txt, current "
-                                         "kernel source only)"},
+                                         "kernel source only), captured with "
+                                         "the default tile shape "
+                                         f"{tile_name(None, Q)}; this run's "
+                                         f"tile: {tile_name(tile, Q)}"},
             "dominant_pass": dict(passes_out[dom], name=dom),
             "passes": passes_out,
             "repeats_ms_per_step": [round(x / args.steps, 5) for x in rep_ms],
