@@ -153,3 +153,45 @@ def test_noalloc_refuses_host_tensor_before_any_launch():
         lbm.lbm_colour_mass_noalloc(19, pops, None)
     with pytest.raises(lbm.LbmError, match="lattice"):
         lbm.lbm_colour_mass_noalloc(7, pops, None)
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "bench_traffic", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    return bench
+
+
+def test_recorded_traffic_needs_kernel_workload_and_source(tmp_path,
+                                                           monkeypatch):
+    """bench.py reports a kernel's DRAM bytes only from a line taken on the
+    running kernel source: the kernel, the workload and the source hash must
+    all match, and comment lines are skipped."""
+    bench = _bench_module()
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "dram_traffic.txt").write_text(
+        "# k_stream w1 1 abc\n"
+        "k_stream  w1 100 abc\n"
+        "k_stream  w1 200 def\n"
+        "k_collide w1 300 abc\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "abc")
+    assert bench.recorded_traffic("k_stream", "w1") == 100
+    assert bench.recorded_traffic("k_collide", "w1") == 300
+    assert bench.recorded_traffic("k_stream", "w2") is None
+    assert bench.recorded_traffic("k_gradient", "w1") is None
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "def")
+    assert bench.recorded_traffic("k_stream", "w1") == 200
+    assert bench.recorded_traffic("k_collide", "w1") is None
+
+
+def test_committed_traffic_covers_every_pass_of_the_step():
+    """The committed DRAM summary has a line for every kernel of the FP32
+    step on the 256^3 rock at the current kernel source (a kernel change
+    that was not captured again would leave the roofline's traffic null)."""
+    bench = _bench_module()
+    for kern in bench.PASS_KERNEL.values():
+        t = bench.recorded_traffic(kern, "porous256_drainage_typeI_fp32")
+        assert t is not None and t > 0, kern
